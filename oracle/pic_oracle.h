@@ -1,0 +1,71 @@
+/*
+ * pic_oracle.h -- plain, slow FP64 CPU reference of the explicit electromagnetic
+ * particle-in-cell step run in a Lorentz-boosted frame (Vay et al., "Speeding up
+ * simulations of relativistic systems using an optimal boosted frame", Sec. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA path.  Only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may load it.  It
+ * shares no code, header, table or helper with the CUDA library and includes nothing
+ * from it.
+ *
+ * Units: c = eps0 = 1.  Grid index conventions (staggered Yee grid):
+ *   Ex[i,j,k] sits at (i+1/2, j, k), Ey at (i, j+1/2, k), Ez at (i, j, k+1/2),
+ *   Bx at (i, j+1/2, k+1/2), By at (i+1/2, j, k+1/2), Bz at (i+1/2, j+1/2, k);
+ *   J like E; rho on nodes (i, j, k).  Arrays are n0*n1*n2, x fastest.
+ *   In 2D3V (ndim = 2) n2 = 1 and d/dz = 0.
+ * Particles: int32 linear cell index (x fastest) + FP64 in-cell offsets in [0,1)
+ * per axis, momenta u = gamma*v (per unit mass), weight w (physical particles per
+ * macro-particle), int32 id.
+ */
+#ifndef PIC_ORACLE_H
+#define PIC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_EX, ORC_EY, ORC_EZ, ORC_BX, ORC_BY, ORC_BZ, ORC_JX, ORC_JY, ORC_JZ, ORC_NCOMP };
+enum { ORC_PERIODIC = 0, ORC_ABSORBING = 1 };
+enum { ORC_VAY = 0, ORC_BORIS = 1 };
+
+typedef struct orc_sim orc_sim;
+
+/* --- single-particle and single-point building blocks (for pins) --- */
+double orc_shape(int order, double x);
+void orc_push_vay(double u[3], const double E[3], const double B[3], double q_over_m, double dt);
+void orc_push_boris(double u[3], const double E[3], const double B[3], double q_over_m, double dt);
+void orc_boost_fields(double gamma_b, const double E[3], const double B[3], double Ep[3], double Bp[3]);
+void orc_boost_event(double gamma_b, const double tx[4], const double u[3], double txp[4], double up[3]);
+uint64_t orc_splitmix64(uint64_t seed, uint64_t stream, uint64_t counter);
+double orc_uniform(uint64_t seed, uint64_t stream, uint64_t counter);
+double orc_normal(uint64_t seed, uint64_t stream, uint64_t counter);
+
+/* --- simulation --- */
+orc_sim *orc_create(int ndim, const int n[3], const int bc[3], const double dx[3], double dt,
+                    int order, int pusher, int filter_passes, const int tile[3], double q,
+                    double m, int absorb_cells, double absorb_strength);
+void orc_destroy(orc_sim *s);
+void orc_set_field(orc_sim *s, int comp, const double *data);
+void orc_get_field(const orc_sim *s, int comp, double *out);
+int orc_set_particles(orc_sim *s, int64_t np, const int32_t *cell, const double *off,
+                      const double *u, const double *w, const int32_t *id);
+int64_t orc_num_particles(const orc_sim *s);
+void orc_get_particles(const orc_sim *s, int32_t *cell, double *off, double *u, double *w,
+                       int32_t *id);
+void orc_sort(orc_sim *s);
+void orc_gather(const orc_sim *s, int32_t cell, const double off[3], double E[3], double B[3]);
+void orc_particle_phase(orc_sim *s);
+void orc_filter(orc_sim *s);
+void orc_maxwell(orc_sim *s);
+void orc_step(orc_sim *s, int nsteps);
+void orc_rho(const orc_sim *s, double *out);
+void orc_div_e(const orc_sim *s, double *out);
+void orc_diagnostics(const orc_sim *s, double out[8]);
+int orc_load_lab_frame(orc_sim *s, double gamma_b, const double *laser, const double *plasma,
+                       const double *beam);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
