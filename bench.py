@@ -1,0 +1,358 @@
+"""Benchmark: boosted-frame LWFA stage (3D, 128 x 128 x 1024 cells, 2 electrons per cell
+= 33,554,432 particles, quadratic shape, 3-pass binomial filter, Vay pusher, FP32 storage
+with the FP64 gamma solve), synthetic lab-frame inputs transformed to gamma_boost = 13.
+
+Prints one JSON line: particle-steps/s of the whole step (gather + push + deposit +
+filter + Maxwell), the fused particle kernel against the HBM roofline, the FP64 CPU
+oracle on a bounded sample of the same workload, and an end-to-end figure through the C
+ABI with host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload (the step
+has no exchange in this build); rank 0 prints the aggregate over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+Vay push+deposit) & % HBM roofline, FP32 vs FP64"
+
+# ---- workload: lab-frame inputs of the boosted LWFA stage (normalised units, lambda0 = 1)
+GAMMA_B = 13.0
+LAMBDA0 = 1.0
+N_GRID = (128, 128, 1024)
+PPC = 2
+
+
+def workload(nz=N_GRID[2]):
+    b = math.sqrt(1.0 - 1.0 / GAMMA_B ** 2)
+    doppler = GAMMA_B * (1.0 + b)
+    dz = doppler * LAMBDA0 / 16.0          # 16 cells per boosted laser wavelength
+    dx = 2.0 * LAMBDA0                     # 10 cells across the waist
+    dt = 0.5 * dz
+    k0 = 2.0 * math.pi / LAMBDA0
+    n_c = k0 * k0                          # critical density (q = m = eps0 = c = 1)
+    duration = 10.0 * LAMBDA0              # 10 lab periods
+    laser = (2.0, LAMBDA0, 20.0 * LAMBDA0, duration, 2.0 * duration)
+    plasma = (n_c / 900.0, 0.0, 2.0 * dz * GAMMA_B, PPC, (0.0, 0.0, 0.0), 3)
+    return dict(n=(N_GRID[0], N_GRID[1], nz), dx=(dx, dx, dz), dt=dt, laser=laser, plasma=plasma)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("PIC_BENCH_GLOO") is None else "gloo"
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------ oracle (CPU)
+def oracle_sample(steps, nz_sample=16, warmup=0):
+    """The FP64 oracle on a bounded sample of the workload: the same lab-frame plasma and
+    grid spacing on a 128 x 128 x nz_sample slab; returns (particle-steps/s, sample, cores)."""
+    import oracle
+
+    oracle.build()
+    w = workload(nz_sample)
+    s = oracle.Sim(3, w["n"], (1, 1, 1), w["dx"], w["dt"], order=2, filter_passes=3, tile=(8, 8, 8))
+    p = w["plasma"]
+    s.load_lab_frame(GAMMA_B, plasma=[p[0], p[1], p[2], p[3], *p[4], p[5]])
+    np0 = s.num_particles()
+    s.step(warmup)
+    t0 = time.perf_counter()
+    done = 0.0
+    for _ in range(steps):
+        before = s.num_particles()
+        s.step(1)
+        done += 0.5 * (before + s.num_particles())
+    dt = time.perf_counter() - t0
+    sample = (f"128x128x{nz_sample} slab of the same lab-frame plasma and spacing ({np0} particles), "
+              f"{steps} timed steps, single thread")
+    return done / dt, sample, 1
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle as it stands, each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    v, sample, cores = oracle_sample(steps=args.steps, nz_sample=4, warmup=args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "boosted LWFA stage (3D laser wakefield), gamma_boost 13, 128x128x1024 cells, "
+                                   "2 ppc, order-2 shape, 3-pass 1-2-1 filter, Vay",
+                       "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_0909_5603_gb300 as pic
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    pic.build()
+    w = workload()
+    ncell = w["n"][0] * w["n"][1] * w["n"][2]
+    sim = pic.Simulation(3, w["n"], (1, 1, 1), w["dx"], w["dt"], gamma_boost=GAMMA_B, order=2,
+                         precision=pic.PIC_PREC_FP32, pusher=pic.PIC_PUSHER_VAY, filter_passes=3, tile=(8, 8, 8),
+                         track_ids=False)
+    sim.load_lab_frame(laser=w["laser"], plasma=w["plasma"])
+    n0 = sim.num_particles()
+    stream = sim.stream
+    sim.step(args.warmup)
+    sim.synchronize()
+
+    # ---- timed region: K steps, per-kernel events on the library's stream
+    sim.set_profiling(True, reset=True)
+    nb = sim.num_particles()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    tm = sim.timings()
+    sim.set_profiling(False)
+    na = sim.num_particles()
+    psteps = 0.5 * (nb + na) * args.steps
+    ms_max = allreduce_max(ms, world)
+    psteps_all = allreduce_sum(psteps, world)
+    value = psteps_all / (ms_max * 1e-3)
+
+    # ---- roofline of the fused particle kernel
+    peaks, peak_kind = measured_peaks()
+    bytes_particle = 32 + 32     # read cell + 3 off + 3 u + w (FP32), write the same
+    bytes_cell = 24 + 12         # E, B tile read; J tile flush
+    kern_ms = tm["ms_particles"] / max(tm["steps"], 1)
+    algo_bytes = 0.5 * (nb + na) * bytes_particle + ncell * bytes_cell
+    achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_kind": peak_kind,
+            "kernel": "k_particles<3,2,float,Vay>", "kernel_ms": kern_ms,
+            "bytes_per_launch": algo_bytes}
+
+    # ---- FP64 path (the plain FP64 one-instance baseline at the same accuracy)
+    fp64 = None
+    if not args.skip_fp64:
+        del sim
+        torch.cuda.empty_cache()
+        s64 = pic.Simulation(3, w["n"], (1, 1, 1), w["dx"], w["dt"], gamma_boost=GAMMA_B, order=2,
+                             precision=pic.PIC_PREC_FP64, filter_passes=3, tile=(8, 8, 8), track_ids=False)
+        s64.load_lab_frame(laser=w["laser"], plasma=w["plasma"])
+        s64.step(2)
+        s64.synchronize()
+        s64.set_profiling(True, reset=True)
+        k64 = max(2, args.steps // 4)
+        nb64 = s64.num_particles()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(s64.stream)
+        s64.step(k64)
+        f1.record(s64.stream)
+        torch.cuda.synchronize()
+        t64 = s64.timings()
+        na64 = s64.num_particles()
+        fp64 = {"value": 0.5 * (nb64 + na64) * k64 / (f0.elapsed_time(f1) * 1e-3), "unit": "particle-steps/s",
+                "steps": k64, "particle_kernel_ms": t64["ms_particles"] / max(t64["steps"], 1)}
+        del s64
+        torch.cuda.empty_cache()
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = end_to_end(pic, w, args, torch)
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        v, sample, cores = oracle_sample(steps=2)
+        cpu = {"value": v, "unit": "particle-steps/s", "cores": cores, "kind": "oracle", "sample": sample}
+    line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "boosted LWFA stage (3D laser wakefield), gamma_boost 13, 128x128x1024 cells, "
+                                   "2 ppc = 33,554,432 particles, order-2 shape, 3-pass 1-2-1 filter, Vay, "
+                                   "FP32 + FP64 gamma solve",
+                       "particles": n0, "cells": ncell, "l2": "inputs larger than L2 (1.07 GB of particles)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "cell_updates_per_s": ncell * args.steps * world / (ms_max * 1e-3),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
+            "gpu_launches": int(tm["launches"]),
+            "phase_ms_per_step": {k: tm[k] / max(tm["steps"], 1) for k in
+                                  ("ms_particles", "ms_scan", "ms_filter", "ms_maxwell", "ms_other")},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def end_to_end(pic, w, args, torch):
+    """Same metric through the public API with host buffers: the particle state is
+    uploaded from pinned host memory, K steps run, each step's diagnostics are read back
+    and the final particles are copied to the host, all inside the timed region."""
+    src = pic.Simulation(3, w["n"], (1, 1, 1), w["dx"], w["dt"], gamma_boost=GAMMA_B, order=2,
+                         precision=pic.PIC_PREC_FP32, filter_passes=3, tile=(8, 8, 8), track_ids=False)
+    src.load_lab_frame(laser=w["laser"], plasma=w["plasma"])
+    p = src.get_particles()
+    ex, by = src.get_field(pic.PIC_EX), src.get_field(pic.PIC_BY)
+    del src
+    torch.cuda.empty_cache()
+    # pinned host copies of the inputs
+    hp = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in p.items()}
+    hex_, hby = torch.from_numpy(ex).pin_memory().numpy(), torch.from_numpy(by).pin_memory().numpy()
+    sim = pic.Simulation(3, w["n"], (1, 1, 1), w["dx"], w["dt"], gamma_boost=GAMMA_B, order=2,
+                         precision=pic.PIC_PREC_FP32, filter_passes=3, tile=(8, 8, 8), track_ids=False)
+    k = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.load_particles(hp["cell"], hp["off"], hp["u"], hp["w"])
+    sim.set_field(pic.PIC_EX, hex_)
+    sim.set_field(pic.PIC_BY, hby)
+    nb = sim.num_particles()
+    for _ in range(k):
+        sim.step(1)
+        sim.diagnostics()
+    out = sim.get_particles()
+    t1 = time.perf_counter()
+    na = out["cell"].size
+    npart = hp["cell"].size
+    h2d = npart * (4 + 24 + 24 + 8) + 2 * hex_.size * 8
+    d2h = k * 64 + na * (4 + 24 + 24 + 8 + 4)
+    del sim
+    torch.cuda.empty_cache()
+    return {"value": 0.5 * (nb + na) * k / (t1 - t0), "unit": "particle-steps/s",
+            "h2d_bytes_per_step": int(h2d / k), "d2h_bytes_per_step": int(d2h / k),
+            "seconds": t1 - t0, "includes": "host sort+upload of 33.5M particles, K steps with per-step "
+                                            "diagnostics read-back, final particle read-back"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) explicit electromagnetic particle-in-cell step in
+ * a Lorentz-boosted frame (Vay, Fawley, Geddes, Cormier-Michel, Grote, "Speeding up
+ * simulations of relativistic systems using an optimal boosted frame", arXiv:0909.5603).
+ *
+ * The calls follow the paper's statement of the problem (Sec. 2): inputs are given in
+ * the laboratory frame and transformed into the boosted frame (pic_load_lab_frame); the
+ * relativistic PIC loop -- field gather, Vay (or Boris) push, charge-conserving current
+ * deposit, low-pass binomial filtering of the current, Yee Maxwell update -- evolves the
+ * system in the boosted frame (pic_step); results are read back (pic_get_*).
+ *
+ * Conventions, for every call:
+ *  - Normalised units: c = eps0 = 1.  The species charge q and mass m are options
+ *    (default electrons, q = -1, m = 1).  Boost along +z.
+ *  - Every call returns pic_status; no C++ exception crosses the ABI.  After a non-OK
+ *    status, pic_last_error() describes it.
+ *  - The library owns all device memory of a context (obtained through the allocator
+ *    given in pic_options, or cudaMalloc).  The caller owns every host buffer passed in;
+ *    getters copy into it and check its size (count / cap) first (PIC_ERR_ARG if short).
+ *  - Getters return FP64 whatever the storage precision (widening is exact).
+ *  - Work is issued on the context's stream (pic_options.stream).  pic_step is
+ *    asynchronous; getters synchronise the stream.  A device-side error word (e.g. a
+ *    bounded wait that timed out, a particle faster than one cell per step) is sticky and
+ *    reported by the next synchronising call.
+ *  - A context is thread-compatible, not thread-safe.
+ *  - Grid arrays exchanged with the host are n0 * n1 * n2 doubles, x fastest, with the
+ *    Yee staggering: Ex[i,j,k] at (i+1/2, j, k), Ey at (i, j+1/2, k), Ez at (i, j, k+1/2),
+ *    Bx at (i, j+1/2, k+1/2), By at (i+1/2, j, k+1/2), Bz at (i+1/2, j+1/2, k), J like E,
+ *    rho and div E on nodes (i, j, k).
+ *  - 2D3V (ndim = 2) is the x-z plane: n[1] must be 1, y is invariant, all three field
+ *    and momentum components are kept.
+ *  - Particles: int32 linear cell index c = i + n0 (j + n1 k) and in-cell offsets in
+ *    [0, 1) per axis (3 doubles per particle, the y offset is 0 in 2D), momenta
+ *    u = gamma v (3 doubles), weight w (physical particles per macro-particle), optional
+ *    int32 id carried along unchanged.
+ *  - Particle order: after every load and every step the particles are kept in the
+ *    canonical order -- a stable sort by tile id (tile coordinates lexicographic, z
+ *    slowest) of the previous order; getters return them in that order.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,            /* invalid argument, size or pointer */
+    PIC_ERR_CFL = 2,            /* dt above the Yee Courant limit */
+    PIC_ERR_CUDA = 3,           /* a CUDA runtime or driver call failed */
+    PIC_ERR_OOM = 4,            /* the allocator returned no memory */
+    PIC_ERR_STATE = 5,          /* call not valid in this state (e.g. step before load) */
+    PIC_ERR_PARTICLE_SPEED = 6, /* device: a particle moved a cell or more, or became NaN */
+    PIC_ERR_TIMEOUT = 7,        /* device: a bounded wait gave up */
+    PIC_ERR_NAN = 8,            /* non-finite value in a host input */
+    PIC_ERR_UNSUPPORTED = 9,    /* valid request this build does not implement */
+    PIC_ERR_INTERNAL = 10       /* device: an internal consistency check failed */
+} pic_status;
+
+enum { PIC_PERIODIC = 0, PIC_ABSORBING = 1 };
+enum { PIC_PREC_FP32 = 0, PIC_PREC_FP64 = 1 };
+enum { PIC_PUSHER_VAY = 0, PIC_PUSHER_BORIS = 1 };
+enum {
+    PIC_EX = 0, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ,
+    PIC_RHO = 9, /* charge density deposited from the particles (getter only) */
+    PIC_DIVE = 10 /* discrete divergence of E on nodes (getter only) */
+};
+enum { PIC_PHASE_PARTICLES = 1, PIC_PHASE_FILTER = 2, PIC_PHASE_MAXWELL = 4, PIC_PHASE_ALL = 7 };
+
+typedef struct {
+    int ndim;  /* 2 (x-z plane, n[1] = 1) or 3 */
+    int n[3];  /* cells per axis */
+    int bc[3]; /* PIC_PERIODIC or PIC_ABSORBING per axis (fields and particles) */
+} pic_grid;
+
+/* Device allocator hooks: return a device pointer of at least `bytes` bytes aligned to
+ * 256 bytes, or NULL; free it.  Both are called only from pic_create, pic_load_* and
+ * pic_destroy / pic_batch_*. */
+typedef void *(*pic_alloc_fn)(size_t bytes, void *user);
+typedef void (*pic_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    int precision;          /* PIC_PREC_FP32: FP32 particles, fields and deposits, FP64
+                               only in the Vay gamma solve and the diagnostics sums;
+                               PIC_PREC_FP64: everything FP64 */
+    int pusher;             /* PIC_PUSHER_VAY (default) or PIC_PUSHER_BORIS */
+    int filter_passes;      /* binomial 1-2-1 passes on J per step (0 = none) */
+    int tile[3];            /* particle tile in cells; 0 = default (8^3 in 3D, 16x1x16 in
+                               2D); tile[0] must be a multiple of 4 */
+    int threads;            /* threads per particle CTA: 128 or 256 (0 = 256) */
+    int absorb_cells;       /* width L of the absorbing layer (default 16) */
+    double absorb_strength; /* per-step damping 1 - s (d/L)^2 at depth d (default 0.1) */
+    double charge, mass;    /* species charge and mass (default -1, 1) */
+    int track_ids;          /* carry an int32 id per particle (default 1) */
+    pic_alloc_fn alloc;     /* NULL: cudaMalloc */
+    pic_free_fn free;       /* NULL: cudaFree */
+    void *alloc_user;
+    void *stream;           /* cudaStream_t used for all work; NULL = legacy stream */
+    int device;             /* CUDA device ordinal (default: the current device) */
+} pic_options;
+
+typedef struct {
+    int64_t step;          /* steps taken since the last load */
+    double t;              /* boosted-frame time step * dt */
+    double field_energy;   /* (1/2) sum (E^2 + B^2) dV over the cells, FP64 sum */
+    double kinetic_energy; /* sum w m (gamma - 1) over particles, FP64 sum */
+    double total_charge;   /* sum q w over particles, FP64 sum */
+    int64_t n_particles;   /* live macro-particles */
+    int64_t n_lost;        /* macro-particles removed at absorbing boundaries */
+    int32_t error_flags;   /* sticky device error word (0 = none) */
+} pic_diag;
+
+/* Per-phase device time accumulated while profiling is on (CUDA events on the
+ * context's stream around each kernel; see pic_set_profiling). */
+typedef struct {
+    int64_t steps;
+    double ms_particles; /* fused gather + push + deposit + reorder kernel */
+    double ms_scan;      /* tile population scan */
+    double ms_filter;    /* current filter */
+    double ms_maxwell;   /* Yee B/E/B (+ absorbing layer, ghost exchange) */
+    double ms_other;     /* J clear and step bookkeeping */
+    int64_t launches;    /* kernels launched by the profiled steps */
+} pic_timings;
+
+/* Fills *o with the defaults listed above. */
+void pic_default_options(pic_options *o);
+
+/* Creates a simulation instance on a boosted-frame grid.
+ *  grid: dimensions and boundaries; dx: cell sizes (> 0); dt: time step, at most the
+ *  Yee Courant limit 1 / sqrt(sum_a 1/dx_a^2) over the active axes (else PIC_ERR_CFL);
+ *  gamma_boost >= 1: Lorentz factor of the boosted frame relative to the lab (Sec. 2),
+ *  used by pic_load_lab_frame; shape_order: 1 (linear) or 2 (quadratic) particle shape
+ *  for gather and deposit; opt: NULL for defaults.  Periodic axes need at least 3 tiles
+ *  unless they hold a single tile.  On success *out owns the instance (free with
+ *  pic_destroy).  Fields start at zero, no particles. */
+pic_status pic_create(const pic_grid *grid, const double dx[3], double dt, double gamma_boost,
+                      int shape_order, const pic_options *opt, pic_ctx **out);
+
+/* Frees the instance (or a batch, which does not free its members).  NULL is a no-op. */
+void pic_destroy(pic_ctx *ctx);
+
+/* Human-readable description of the last non-OK status on ctx (or of the last failed
+ * pic_create when ctx is NULL).  Valid until the next call on ctx. */
+const char *pic_last_error(const pic_ctx *ctx);
+
+/* Laboratory-frame inputs (Sec. 2).  Box coordinates: x in [0, n0 dx0), y in [0, n1 dx1),
+ * z' in [0, n2 dx2) at boosted time t' = 0; lab z = 0 coincides with z' = 0 at t = t' = 0. */
+typedef struct {
+    double a0;       /* normalised peak vector potential (invariant) */
+    double lambda0;  /* lab wavelength */
+    double waist;    /* 1/e field radius (invariant), centred on the box axis */
+    double duration; /* 1/e half-length of the field envelope, lab (c tau) */
+    double z_center; /* lab position of the envelope centre at lab time 0 */
+} pic_laser_lab;     /* linearly polarised along x, propagating along +z, no curvature */
+
+typedef struct {
+    double n0;       /* lab electron density for z >= z_start + ramp_len */
+    double z_start;  /* lab position where the density starts */
+    double ramp_len; /* lab length of the linear up-ramp (0 = step) */
+    int ppc;         /* macro-particles per cell */
+    double u_th[3];  /* lab thermal momentum spread per axis (0 = cold) */
+    uint64_t seed;
+} pic_plasma_lab;
+
+typedef struct {
+    int64_t n;           /* macro-particles */
+    double gamma;        /* lab Lorentz factor of the beam centroid (> 1) */
+    double rel_spread;   /* isotropic momentum spread / (gamma beta) */
+    double sigma_r;      /* lab rms transverse size, centred on the box axis */
+    double sigma_z;      /* lab rms length */
+    double z0;           /* lab centroid position at lab time 0 */
+    double total_weight; /* physical particles in the beam */
+    uint64_t seed;
+} pic_beam_lab;
+
+/* Replaces the state with lab-frame inputs transformed to the boosted frame (Sec. 2):
+ * laser Doppler-shifted (wavelength and length x gamma(1+beta), a0 and waist invariant,
+ * E'x = B'y), plasma at lab rest drifting at -beta with density gamma n0, beam
+ * particles boosted then drifted ballistically to t' = 0.  Host FP64, seeded with
+ * SplitMix64 (counter-based); particles falling outside the box are dropped.  Any of
+ * the three may be NULL.  Resets step count, J and the lost counter. */
+pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *laser, const pic_plasma_lab *plasma,
+                              const pic_beam_lab *beam);
+
+/* Replaces the particles with n host particles (exact-input path).  cell[n]; off3[3n]
+ * in [0,1) (PIC_ERR_ARG otherwise); u3[3n]; w[n]; id[n] or NULL (ids 0..n-1).  The
+ * library sorts them into the canonical order. */
+pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3,
+                              const double *u3, const double *w, const int32_t *id);
+
+/* Overwrites one field component (PIC_EX .. PIC_JZ) with count = n0 n1 n2 host values. */
+pic_status pic_set_field(pic_ctx *ctx, int comp, const double *host, size_t count);
+
+/* Advances n >= 0 steps (all phases).  Asynchronous; the step is replayed from a CUDA
+ * graph captured on first use unless profiling is on.  PIC_ERR_STATE before any load. */
+pic_status pic_step(pic_ctx *ctx, int n);
+
+/* Runs the selected phases (PIC_PHASE_* mask) of one step, for unit testing a phase in
+ * isolation; a full step is PIC_PHASE_ALL. */
+pic_status pic_run_phases(pic_ctx *ctx, int phase_mask);
+
+/* Copies one component (PIC_EX .. PIC_JZ, PIC_RHO, PIC_DIVE) into host_out[count],
+ * count >= n0 n1 n2.  J is the current used by the last Maxwell update (after filter). */
+pic_status pic_get_field(pic_ctx *ctx, int comp, double *host_out, size_t count);
+
+/* Number of live particles (synchronises). */
+pic_status pic_num_particles(pic_ctx *ctx, int64_t *n_out);
+
+/* Copies the live particles, in canonical order, into host arrays with room for cap
+ * particles (any pointer may be NULL to skip that array); *n_out = count. */
+pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off3, double *u3, double *w,
+                             int32_t *id, int64_t cap, int64_t *n_out);
+
+/* FP64 global diagnostics (computed on the device, then copied). */
+pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out);
+
+/* Profiling: when on, pic_step launches each kernel directly (no graph) between CUDA
+ * events on the context's stream and accumulates per-phase device time; reset clears the
+ * sums.  pic_get_timings synchronises and returns the sums. */
+pic_status pic_set_profiling(pic_ctx *ctx, int on, int reset);
+pic_status pic_get_timings(pic_ctx *ctx, pic_timings *out);
+
+/* Waits for all work of ctx; reports a sticky device error. */
+pic_status pic_synchronize(pic_ctx *ctx);
+
+/* Groups n >= 1 instances created with identical ndim, shape order, precision, pusher,
+ * tile, threads and device into a batch whose pic_step advances all of them in one
+ * launch per phase (one flattened tile list over all instances), captured in one graph.
+ * The members keep their own memory and stay readable with the getters; destroy the
+ * batch before its members.  Only pic_step, pic_run_phases, pic_synchronize,
+ * pic_set_profiling, pic_get_timings and pic_destroy accept a batch. */
+pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx **batch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

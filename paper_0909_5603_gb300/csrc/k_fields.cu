@@ -1,0 +1,350 @@
+// k_fields.cu -- grid kernels of the boosted-frame PIC step on sm_103a: Yee FDTD
+// half/whole updates with the absorbing layer, binomial current filter sweeps, periodic
+// ghost exchange for the TMA gather boxes, and the FP64 field reductions / read-outs.
+//
+// All stencil kernels run one thread per interior cell of a flattened cell space over
+// every instance of the launch (x fastest, so loads and stores coalesce along rows).
+// Neighbours along periodic axes wrap by index; along absorbing axes they read the
+// zero ghost layers.
+#include "pic_internal.h"
+
+namespace pic {
+
+struct CellPos {
+    int ii;       // instance
+    int i, j, k;  // interior cell
+    long long p;  // padded linear index
+};
+
+__device__ __forceinline__ bool cell_of(const Launch &L, long long g, CellPos &c, const InstDev *&I)
+{
+    if (g >= L.total_cells) return false;
+    c.ii = find_instance_ll(L.cell_start, L.ninst, g);
+    I = L.inst + c.ii;
+    long long r = g - L.cell_start[c.ii];
+    c.i = (int)(r % I->n[0]);
+    r /= I->n[0];
+    c.j = (int)(r % I->n[1]);
+    c.k = (int)(r / I->n[1]);
+    c.p = (c.i + I->gh[0]) + I->sy * (c.j + I->gh[1]) + I->sz * (c.k + I->gh[2]);
+    return true;
+}
+
+// Offsets to the +1 / -1 neighbour along each axis (0 on an inactive axis).
+__device__ __forceinline__ void neighbour_offsets(const InstDev &I, const CellPos &c, long long up[3], long long dn[3])
+{
+    const long long st[3] = {1, I.sy, I.sz};
+    const int idx[3] = {c.i, c.j, c.k};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (I.ndim == 2 && a == 1) {
+            up[a] = dn[a] = 0;
+            continue;
+        }
+        const bool per = I.bc[a] == 0;
+        up[a] = (per && idx[a] == I.n[a] - 1) ? -(long long)(I.n[a] - 1) * st[a] : st[a];
+        dn[a] = (per && idx[a] == 0) ? (long long)(I.n[a] - 1) * st[a] : -st[a];
+    }
+}
+
+// Absorbing-layer factor prod_a (1 - s (d_a / L)^2), d_a = depth into the layer.
+__device__ __forceinline__ double damp_factor(const InstDev &I, const CellPos &c)
+{
+    const int L = I.absorb_cells;
+    if (L <= 0) return 1.0;
+    double f = 1.0;
+    const int idx[3] = {c.i, c.j, c.k};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if ((I.ndim == 2 && a == 1) || I.bc[a] == 0) continue;
+        int d = 0;
+        if (L - idx[a] > d) d = L - idx[a];
+        if (idx[a] - (I.n[a] - 1 - L) > d) d = idx[a] - (I.n[a] - 1 - L);
+        const double r = (double)d / (double)L;
+        f *= 1.0 - I.absorb_strength * r * r;
+    }
+    return f;
+}
+
+// B <- B - (dt/2) curl E  [then x damping on the second half of the step]
+template <typename R>
+__global__ void __launch_bounds__(256) k_bhalf(Launch L, int damp)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    CellPos c;
+    const InstDev *Ip;
+    if (!cell_of(L, g, c, Ip)) return;
+    const InstDev &I = *Ip;
+    long long up[3], dn[3];
+    neighbour_offsets(I, c, up, dn);
+    const R *Ex = (const R *)I.E[0], *Ey = (const R *)I.E[1], *Ez = (const R *)I.E[2];
+    R *Bx = (R *)I.B[0], *By = (R *)I.B[1], *Bz = (R *)I.B[2];
+    const R h = R(0.5 * I.dt);
+    const R ix = R(1.0 / I.dx[0]), iy = R(1.0 / I.dx[1]), iz = R(1.0 / I.dx[2]);
+    const long long p = c.p;
+    const R ex = Ex[p], ey = Ey[p], ez = Ez[p];
+    R dEz_dy = R(0), dEy_dz = (Ey[p + up[2]] - ey) * iz, dEx_dz = (Ex[p + up[2]] - ex) * iz;
+    R dEz_dx = (Ez[p + up[0]] - ez) * ix, dEy_dx = (Ey[p + up[0]] - ey) * ix, dEx_dy = R(0);
+    if (I.ndim == 3) {
+        dEz_dy = (Ez[p + up[1]] - ez) * iy;
+        dEx_dy = (Ex[p + up[1]] - ex) * iy;
+    }
+    R bx = Bx[p] - h * (dEz_dy - dEy_dz);
+    R by = By[p] - h * (dEx_dz - dEz_dx);
+    R bz = Bz[p] - h * (dEy_dx - dEx_dy);
+    if (damp) {
+        const R f = R(damp_factor(I, c));
+        bx *= f;
+        by *= f;
+        bz *= f;
+    }
+    Bx[p] = bx;
+    By[p] = by;
+    Bz[p] = bz;
+}
+
+// E <- damping x (E + dt (curl B - J)), J = the filtered current of this step.
+template <typename R>
+__global__ void __launch_bounds__(256) k_efull(Launch L, int filtered)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    CellPos c;
+    const InstDev *Ip;
+    if (!cell_of(L, g, c, Ip)) return;
+    const InstDev &I = *Ip;
+    long long up[3], dn[3];
+    neighbour_offsets(I, c, up, dn);
+    const R *Bx = (const R *)I.B[0], *By = (const R *)I.B[1], *Bz = (const R *)I.B[2];
+    R *Ex = (R *)I.E[0], *Ey = (R *)I.E[1], *Ez = (R *)I.E[2];
+    const int nsweeps = I.filter_passes * (I.ndim == 3 ? 3 : 2);
+    void *const *Jsrc = (filtered && (nsweeps & 1)) ? I.Jt : I.J;
+    const R *Jx = (const R *)Jsrc[0], *Jy = (const R *)Jsrc[1], *Jz = (const R *)Jsrc[2];
+    const R dt = R(I.dt);
+    const R ix = R(1.0 / I.dx[0]), iy = R(1.0 / I.dx[1]), iz = R(1.0 / I.dx[2]);
+    const long long p = c.p;
+    const R bx = Bx[p], by = By[p], bz = Bz[p];
+    R dBz_dy = R(0), dBy_dz = (by - By[p + dn[2]]) * iz, dBx_dz = (bx - Bx[p + dn[2]]) * iz;
+    R dBz_dx = (bz - Bz[p + dn[0]]) * ix, dBy_dx = (by - By[p + dn[0]]) * ix, dBx_dy = R(0);
+    if (I.ndim == 3) {
+        dBz_dy = (bz - Bz[p + dn[1]]) * iy;
+        dBx_dy = (bx - Bx[p + dn[1]]) * iy;
+    }
+    const R f = R(damp_factor(I, c));
+    Ex[p] = f * (Ex[p] + dt * ((dBz_dy - dBy_dz) - Jx[p]));
+    Ey[p] = f * (Ey[p] + dt * ((dBx_dz - dBz_dx) - Jy[p]));
+    Ez[p] = f * (Ez[p] + dt * ((dBy_dx - dBx_dy) - Jz[p]));
+}
+
+// One binomial sweep J <- J(i-1)/4 + J(i)/2 + J(i+1)/4 along one axis for the three
+// components; sweep s of an instance reads J (s even) or Jt (s odd) and writes the
+// other.  Sweeps cycle x, (y,) z within each pass.  Instances with fewer sweeps skip.
+template <typename R>
+__global__ void __launch_bounds__(256) k_filter(Launch L, int s)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    CellPos c;
+    const InstDev *Ip;
+    if (!cell_of(L, g, c, Ip)) return;
+    const InstDev &I = *Ip;
+    const int naxes = I.ndim == 3 ? 3 : 2;
+    if (s >= I.filter_passes * naxes) return;
+    const int ai = s % naxes;
+    const int axis = I.ndim == 3 ? ai : (ai == 0 ? 0 : 2);
+    long long up[3], dn[3];
+    neighbour_offsets(I, c, up, dn);
+    void *const *src = (s & 1) ? I.Jt : I.J;
+    void *const *dst = (s & 1) ? I.J : I.Jt;
+    const long long p = c.p;
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+        const R *a = (const R *)src[comp];
+        R *b = (R *)dst[comp];
+        b[p] = R(0.25) * a[p + dn[axis]] + R(0.5) * a[p] + R(0.25) * a[p + up[axis]];
+    }
+}
+
+// Periodic ghost exchange of the six E/B components along one axis (after the whole
+// step); ghosts of earlier axes are included so corners come out right.
+template <typename R>
+__global__ void __launch_bounds__(256) k_ghost(Launch L, int axis, long long per_inst_max)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ii = (int)(g / per_inst_max);
+    if (ii >= L.ninst) return;
+    const InstDev &I = L.inst[ii];
+    if (I.bc[axis] != 0 || (I.ndim == 2 && axis == 1)) return;
+    // ghost slab: 2*gh layers along `axis` x padded extents of the other two axes
+    const int gh = I.gh[axis];
+    long long r = g - (long long)ii * per_inst_max;
+    const int o1 = axis == 0 ? 1 : 0, o2 = axis == 2 ? 1 : 2;
+    const long long e1 = I.P[o1], e2 = I.P[o2];
+    const long long slab = 2LL * gh * e1 * e2;
+    if (r >= 6 * slab) return;
+    const int comp = (int)(r / slab);
+    r -= comp * slab;
+    const int layer = (int)(r % (2 * gh));
+    r /= 2 * gh;
+    const long long a1 = r % e1, a2 = r / e1;
+    const int n = I.n[axis];
+    // destination padded coordinate along axis and its periodic source
+    const int dpos = layer < gh ? layer : gh + n + (layer - gh);
+    const int spos = layer < gh ? dpos + n : dpos - n;
+    long long st[3] = {1, I.sy, I.sz};
+    const long long base = a1 * st[o1] + a2 * st[o2];
+    R *f = (R *)(comp < 3 ? I.E[comp] : I.B[comp - 3]);
+    f[base + dpos * st[axis]] = f[base + spos * st[axis]];
+}
+
+// FP64 field energy sums (1/2) sum (E^2 + B^2) dV per instance.
+template <typename R>
+__global__ void __launch_bounds__(256) k_field_energy(Launch L, double *sums)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    CellPos c;
+    const InstDev *Ip;
+    double e = 0.0;
+    int ii = -1;
+    if (cell_of(L, g, c, Ip)) {
+        const InstDev &I = *Ip;
+        ii = c.ii;
+        for (int a = 0; a < 3; ++a) {
+            const double x = ((const R *)I.E[a])[c.p], y = ((const R *)I.B[a])[c.p];
+            e += x * x + y * y;
+        }
+        e *= 0.5 * I.dx[0] * I.dx[1] * I.dx[2];
+    }
+    // instances are contiguous in g: reduce per warp when the whole warp shares one
+    const int ii0 = __shfl_sync(0xffffffffu, ii, 0);
+    const bool same = __all_sync(0xffffffffu, ii == ii0 || ii < 0);
+    if (same) {
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+        if ((threadIdx.x & 31) == 0 && ii0 >= 0) atomicAdd(sums + 2 * L.ninst + ii0, e);
+    } else if (ii >= 0) {
+        atomicAdd(sums + 2 * L.ninst + ii, e);
+    }
+}
+
+template <typename R>
+__global__ void k_pack(InstDev I, int comp, int filtered, double *dense, long long ncell)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ncell) return;
+    const int i = (int)(g % I.n[0]);
+    const int j = (int)((g / I.n[0]) % I.n[1]);
+    const int k = (int)(g / ((long long)I.n[0] * I.n[1]));
+    const long long p = (i + I.gh[0]) + I.sy * (j + I.gh[1]) + I.sz * (k + I.gh[2]);
+    const void *src;
+    if (comp < 3) src = I.E[comp];
+    else if (comp < 6) src = I.B[comp - 3];
+    else {
+        const int nsweeps = I.filter_passes * (I.ndim == 3 ? 3 : 2);
+        src = (filtered && (nsweeps & 1)) ? I.Jt[comp - 6] : I.J[comp - 6];
+    }
+    dense[g] = (double)((const R *)src)[p];
+}
+
+template <typename R>
+__global__ void k_unpack(InstDev I, int comp, const double *dense, long long ncell)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ncell) return;
+    const int i = (int)(g % I.n[0]);
+    const int j = (int)((g / I.n[0]) % I.n[1]);
+    const int k = (int)(g / ((long long)I.n[0] * I.n[1]));
+    const long long p = (i + I.gh[0]) + I.sy * (j + I.gh[1]) + I.sz * (k + I.gh[2]);
+    void *dst = comp < 3 ? I.E[comp] : (comp < 6 ? I.B[comp - 3] : I.J[comp - 6]);
+    ((R *)dst)[p] = (R)dense[g];
+}
+
+// div E on nodes: sum_a (E_a[i] - E_a[i - e_a]) / dx_a
+template <typename R>
+__global__ void k_dive(InstDev I, double *dense, long long ncell)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ncell) return;
+    CellPos c;
+    c.i = (int)(g % I.n[0]);
+    c.j = (int)((g / I.n[0]) % I.n[1]);
+    c.k = (int)(g / ((long long)I.n[0] * I.n[1]));
+    c.p = (c.i + I.gh[0]) + I.sy * (c.j + I.gh[1]) + I.sz * (c.k + I.gh[2]);
+    long long up[3], dn[3];
+    neighbour_offsets(I, c, up, dn);
+    double d = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (I.ndim == 2 && a == 1) continue;
+        const R *E = (const R *)I.E[a];
+        d += ((double)E[c.p] - (double)E[c.p + dn[a]]) / I.dx[a];
+    }
+    dense[g] = d;
+}
+
+// ------------------------------------------------------------------------------------
+static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_filter(int fp64, const Launch &L, int max_sweeps, cudaStream_t s)
+{
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        if (fp64)
+            k_filter<double><<<blocks_for(L.total_cells, 256), 256, 0, s>>>(L, sw);
+        else
+            k_filter<float><<<blocks_for(L.total_cells, 256), 256, 0, s>>>(L, sw);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxwell(int fp64, const Launch &L, int filtered, cudaStream_t s)
+{
+    const unsigned nb = blocks_for(L.total_cells, 256);
+    if (fp64) {
+        k_bhalf<double><<<nb, 256, 0, s>>>(L, 0);
+        k_efull<double><<<nb, 256, 0, s>>>(L, filtered);
+        k_bhalf<double><<<nb, 256, 0, s>>>(L, 1);
+    } else {
+        k_bhalf<float><<<nb, 256, 0, s>>>(L, 0);
+        k_efull<float><<<nb, 256, 0, s>>>(L, filtered);
+        k_bhalf<float><<<nb, 256, 0, s>>>(L, 1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ghost(int fp64, const Launch &L, int axis, long long per_inst_max, cudaStream_t s)
+{
+    const long long n = per_inst_max * L.ninst;
+    if (fp64)
+        k_ghost<double><<<blocks_for(n, 256), 256, 0, s>>>(L, axis, per_inst_max);
+    else
+        k_ghost<float><<<blocks_for(n, 256), 256, 0, s>>>(L, axis, per_inst_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_energy(int fp64, const Launch &L, double *sums, cudaStream_t s)
+{
+    if (fp64)
+        k_field_energy<double><<<blocks_for(L.total_cells, 256), 256, 0, s>>>(L, sums);
+    else
+        k_field_energy<float><<<blocks_for(L.total_cells, 256), 256, 0, s>>>(L, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int fp64, const InstDev &I, int comp, int filtered, double *dense, long long ncell, cudaStream_t s)
+{
+    if (fp64) k_pack<double><<<blocks_for(ncell, 256), 256, 0, s>>>(I, comp, filtered, dense, ncell);
+    else k_pack<float><<<blocks_for(ncell, 256), 256, 0, s>>>(I, comp, filtered, dense, ncell);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int fp64, const InstDev &I, int comp, const double *dense, long long ncell, cudaStream_t s)
+{
+    if (fp64) k_unpack<double><<<blocks_for(ncell, 256), 256, 0, s>>>(I, comp, dense, ncell);
+    else k_unpack<float><<<blocks_for(ncell, 256), 256, 0, s>>>(I, comp, dense, ncell);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dive(int fp64, const InstDev &I, double *dense, long long ncell, cudaStream_t s)
+{
+    if (fp64) k_dive<double><<<blocks_for(ncell, 256), 256, 0, s>>>(I, dense, ncell);
+    else k_dive<float><<<blocks_for(ncell, 256), 256, 0, s>>>(I, dense, ncell);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

@@ -1,0 +1,604 @@
+// k_particles.cuh -- the particle half of the boosted-frame PIC step on sm_103a.
+//
+// One CTA per particle tile.  It stages the tile's E and B plus guard cells into shared
+// memory with TMA bulk-tensor copies, loads the tile's particles from the previous
+// step's layout (the moved-in sub-ranges of the 27 neighbouring tiles), and for each
+// particle: gathers E, B (shape order 1 or 2, each component at its Yee position), pushes
+// u with the Vay (or Boris) pusher (Sec. 2 of the paper), moves it, and deposits the
+// charge-conserving Esirkepov current into a shared-memory J tile.  Each chunk of
+// particles is written out stably partitioned by the tile it moved to, so the next
+// step finds every tile's particles in contiguous sub-ranges: the array stays sorted
+// by tile at every step with no separate sort pass.  The J tile is flushed to global
+// memory once, with wrap-around (periodic) or clipping (absorbing) of its guard cells.
+#pragma once
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+constexpr int kNT = 256;          // threads per particle CTA
+constexpr int kPPT = 4;           // particles per thread per chunk
+constexpr int kNW = kNT / 32;
+constexpr int kChunk = kNT * kPPT;  // particles per chunk
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
+
+// -------------------------------------------------------------------------------------
+// Source table of one destination tile: the (tile, direction) pairs whose particles
+// move into it, in ascending source-tile order (so the concatenation is the stable
+// order of the previous array).
+// -------------------------------------------------------------------------------------
+struct SrcTable {
+    int n;
+    int count;         // sum of the sources
+    int tile[kDirs];
+    int dir[kDirs];
+    int pre[kDirs + 1];
+    int seg[kDirs];    // segment start of the source tile
+    int c0[kDirs];     // first chunk record of the source tile
+    int nch[kDirs];    // chunks of the source tile
+    int pos0[kDirs];   // direct start position when the source has one chunk
+};
+
+// Valid (direction, source coordinate) pairs along one axis for destination coordinate
+// T, sorted by source coordinate.  Returns how many.
+__device__ __forceinline__ int axis_sources(int T, int nt, int bc, int dirs[3], int src[3])
+{
+    int m = 0;
+    int cd[3], cs[3];
+    if (bc == 0) {
+        if (nt >= 3) {
+            for (int d = -1; d <= 1; ++d) {
+                cd[m] = d;
+                cs[m] = ((T - d) % nt + nt) % nt;
+                ++m;
+            }
+        } else if (nt == 2) {
+            cd[0] = 0; cs[0] = T;
+            cd[1] = 1; cs[1] = (T + 1) % 2;
+            m = 2;
+        } else {
+            cd[0] = 0; cs[0] = T;
+            m = 1;
+        }
+    } else {
+        for (int d = -1; d <= 1; ++d) {
+            const int s = T - d;
+            if (s >= 0 && s < nt) {
+                cd[m] = d;
+                cs[m] = s;
+                ++m;
+            }
+        }
+    }
+    // sort by source coordinate (m <= 3)
+    for (int i = 0; i < m; ++i)
+        for (int j = i + 1; j < m; ++j)
+            if (cs[j] < cs[i]) {
+                int a = cs[i]; cs[i] = cs[j]; cs[j] = a;
+                a = cd[i]; cd[i] = cd[j]; cd[j] = a;
+            }
+    for (int i = 0; i < m; ++i) {
+        dirs[i] = cd[i];
+        src[i] = cs[i];
+    }
+    return m;
+}
+
+// Canonical direction along one axis from old tile coordinate to new one.
+__device__ __forceinline__ int axis_dir(int told, int tnew, int nt, int bc)
+{
+    if (bc != 0) return tnew - told;
+    int d = tnew - told;
+    if (d < 0) d += nt;  // d in [0, nt)
+    if (d == 0) return 0;
+    if (d == 1) return 1;
+    return -1;           // d == nt - 1 with nt >= 3
+}
+
+// Built by one thread (thread 0) of the CTA.  `lay` = layout holding the source tiles.
+static __device__ void build_sources(const InstDev &I, int lay, int tx, int ty, int tz, SrcTable &S)
+{
+    int dx[3], sx[3], dy[3], sy[3], dz[3], sz[3];
+    const int mx = axis_sources(tx, I.nt[0], I.bc[0], dx, sx);
+    const int my = I.ndim == 3 ? axis_sources(ty, I.nt[1], I.bc[1], dy, sy) : 1;
+    if (I.ndim != 3) { dy[0] = 0; sy[0] = 0; }
+    const int mz = axis_sources(tz, I.nt[2], I.bc[2], dz, sz);
+    int n = 0, acc = 0;
+    const int *seg = I.seg[lay];
+    const int *cbase = I.chunk_base[lay];
+    const int *tot = I.tot[lay];
+    const int *pre = I.chunk_pre[lay];
+    for (int a = 0; a < mz; ++a)
+        for (int b = 0; b < my; ++b)
+            for (int c = 0; c < mx; ++c) {
+                const int st = sx[c] + I.nt[0] * (sy[b] + I.nt[1] * sz[a]);
+                const int d = (dz[a] + 1) * 9 + (dy[b] + 1) * 3 + (dx[c] + 1);
+                const int cnt = tot[st * kBuckets + d];
+                S.tile[n] = st;
+                S.dir[n] = d;
+                S.pre[n] = acc;
+                S.seg[n] = seg[st];
+                S.c0[n] = cbase[st];
+                S.nch[n] = cbase[st + 1] - cbase[st];
+                S.pos0[n] = S.nch[n] == 1 ? seg[st] + pre[cbase[st] * kPre + d] : -1;
+                acc += cnt;
+                ++n;
+            }
+    S.n = n;
+    S.pre[n] = acc;
+    S.count = acc;
+}
+
+// Buffer position of slot p (0 <= p < S.count) of the destination tile.
+__device__ __forceinline__ int slot_position(const InstDev &I, int lay, const SrcTable &S, int p)
+{
+    int s = 0;
+    while (s + 1 < S.n && S.pre[s + 1] <= p) ++s;
+    const int j = p - S.pre[s];
+    if (S.pos0[s] >= 0) return S.pos0[s] + j;
+    // several chunks: the last chunk whose earlier-chunks count of this bucket is <= j
+    const int d = S.dir[s];
+    const int *cb = I.chunk_cb[lay];
+    int lo = 0, hi = S.nch[s] - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cb[(S.c0[s] + mid) * kBuckets + d] <= j) lo = mid; else hi = mid - 1;
+    }
+    const int c = S.c0[s] + lo;
+    return S.seg[s] + lo * I.R + I.chunk_pre[lay][c * kPre + d] + (j - cb[c * kBuckets + d]);
+}
+
+// -------------------------------------------------------------------------------------
+// Gather helpers: separable interpolation from a shared-memory box.
+// -------------------------------------------------------------------------------------
+template <int ND, int ORD, typename R>
+__device__ __forceinline__ R interp(const R *f, int bx, int bxy, int i0, int j0, int k0, const R *wx, const R *wy,
+                                    const R *wz)
+{
+    constexpr int NP = ORD + 1;
+    R acc = R(0);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        R ay = R(0);
+        if (ND == 3) {
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const R *row = f + i0 + bx * (j0 + j) + bxy * (k0 + k);
+                R ax = R(0);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) ax += wx[i] * row[i];
+                ay += wy[j] * ax;
+            }
+        } else {
+            const R *row = f + i0 + bxy * (k0 + k);
+            R ax = R(0);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) ax += wx[i] * row[i];
+            ay = ax;
+        }
+        acc += wz[k] * ay;
+    }
+    return acc;
+}
+
+struct PState {
+    int cell;
+    int id;
+    int bucket;  // 0..26 direction, 27 dead, 28 no particle
+};
+
+template <typename R>
+struct Kin {
+    R o[3], u[3], w;
+};
+
+template <int ND, int ORD, typename R, int PUSHER>
+__global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launch L)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ SrcTable S;
+    __shared__ uint64_t bar;
+    __shared__ int s_base[kBuckets], s_run[kBuckets], s_round[kBuckets];
+    __shared__ int s_cnt[kPPT][kNW][kBuckets];
+
+    const int g = blockIdx.x;
+    const int ii = find_instance(L.tile_start, L.ninst, g);
+    const InstDev &I = L.inst[ii];
+    const int t = g - L.tile_start[ii];
+    const int out = *I.cur;  // the scan of this step already flipped the parity
+    const int in = 1 - out;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    const int tx = t % I.nt[0];
+    const int ty = (t / I.nt[0]) % I.nt[1];
+    const int tz = t / (I.nt[0] * I.nt[1]);
+    const int T0[3] = {tx * I.ts[0], ty * I.ts[1], tz * I.ts[2]};
+    const int seg_out = I.seg[out][t];
+    const int count = I.seg[out][t + 1] - seg_out;
+    const int chunk_out = I.chunk_base[out][t];
+
+    if (count == 0) {
+        if (tid < kBuckets) I.tot[out][t * kBuckets + tid] = 0;
+        return;
+    }
+    // the output layout must fit the buffers (it always does unless memory is corrupt)
+    if (seg_out + count > I.cap || chunk_out + (count + kChunk - 1) / kChunk > I.chunk_cap) {
+        if (tid == 0) atomicOr(I.err, kErrCapacity);
+        return;
+    }
+
+    // shared-memory carve-up (base rounded up to 128 bytes for TMA): 6 field boxes, then
+    // 3 J components
+    const int boxn = I.box[0] * I.box[1] * I.box[2];
+    const int box_bytes = boxn * (int)sizeof(R);
+    const int box_stride = (box_bytes + 127) & ~127;
+    unsigned char *sbase = smem + ((128u - (smem_addr(smem) & 127u)) & 127u);
+    R *sF = reinterpret_cast<R *>(sbase);
+    R *sJ = reinterpret_cast<R *>(sbase + 6 * box_stride);
+    const int jvol = I.jdim[0] * I.jdim[1] * I.jdim[2];
+
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        for (int c = 0; c < 6; ++c) tmap_acquire(I.tmap + c);
+        mbar_expect_tx(&bar, 6u * (uint32_t)box_bytes);
+        const int x = T0[0] + I.box_lo[0] + I.gh[0];
+        const int y = T0[1] + I.box_lo[1] + I.gh[1];
+        const int z = T0[2] + I.box_lo[2] + I.gh[2];
+        for (int c = 0; c < 6; ++c)
+            tma_load_3d(sbase + c * box_stride, I.tmap + c, x, y, z, &bar);
+        build_sources(I, in, tx, ty, tz, S);
+    }
+    for (int e = tid; e < 3 * jvol; e += kNT) sJ[e] = R(0);
+    if (tid < kBuckets) s_run[tid] = 0;
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, kWaitCycles);
+    if (!__syncthreads_and(ok ? 1 : 0)) {
+        if (tid == 0) {
+            atomicOr(I.err, kErrTimeout);
+            mbar_wait_bounded(&bar, 0, kWaitCycles);  // let copies in flight land
+        }
+        return;
+    }
+    if (tid == 0 && S.count != count) atomicOr(I.err, kErrInternal);
+
+    // per-instance constants in the working precision
+    const R dt = R(I.dt);
+    const R h = R(0.5 * I.q / I.m * I.dt);
+    const double dV = I.dx[0] * I.dx[1] * I.dx[2];
+    const R qdv = R(I.q / dV);
+    const R jfx = R(I.dx[0] / I.dt), jfy = R(I.dx[1] / I.dt), jfz = R(I.dx[2] / I.dt);
+    const R dtdx[3] = {R(I.dt / I.dx[0]), R(I.dt / I.dx[1]), R(I.dt / I.dx[2])};
+    const int bx = I.box[0], bxy = I.box[0] * I.box[1];
+    const int jd0 = I.jdim[0], jd01 = I.jdim[0] * I.jdim[1];
+    const int jlo_y = ND == 3 ? I.jlo : 0;
+    const int tsx = min(I.ts[0], I.n[0] - T0[0]);
+    const int tsy = min(I.ts[1], I.n[1] - T0[1]);
+    const int tsz = min(I.ts[2], I.n[2] - T0[2]);
+
+    const int *cell_in = I.cell[in];
+    const R *off_in[3] = {(const R *)I.off[in][0], (const R *)I.off[in][1], (const R *)I.off[in][2]};
+    const R *u_in[3] = {(const R *)I.u[in][0], (const R *)I.u[in][1], (const R *)I.u[in][2]};
+    const R *w_in = (const R *)I.w[in];
+    const int *id_in = I.id[in];
+
+    for (int base = 0, r = 0; base < count; base += kChunk, ++r) {
+        for (int e = tid; e < kPPT * kNW * kBuckets; e += kNT) (&s_cnt[0][0][0])[e] = 0;
+        __syncthreads();
+        PState st[kPPT];
+        Kin<R> kn[kPPT];
+#pragma unroll
+        for (int k = 0; k < kPPT; ++k) {
+            const int slot = base + k * kNT + tid;
+            st[k].bucket = 28;
+            if (slot >= count) continue;
+            const int pos = slot_position(I, in, S, slot);
+            if (pos < 0 || pos >= I.cap) {
+                atomicOr(I.err, kErrInternal);
+                continue;
+            }
+            const int c = __ldg(cell_in + pos);
+            const int cx = c % I.n[0];
+            const int cyz = c / I.n[0];
+            const int cy = cyz % I.n[1];
+            const int cz = cyz / I.n[1];
+            int l[3] = {cx - T0[0], cy - T0[1], cz - T0[2]};
+            if (l[0] < 0 || l[0] >= tsx || l[1] < 0 || l[1] >= tsy || l[2] < 0 || l[2] >= tsz) {
+                atomicOr(I.err, kErrInternal);
+                continue;
+            }
+            R o[3], u[3];
+            o[0] = __ldg(off_in[0] + pos);
+            o[1] = ND == 3 ? __ldg(off_in[1] + pos) : R(0);
+            o[2] = __ldg(off_in[2] + pos);
+            u[0] = __ldg(u_in[0] + pos);
+            u[1] = __ldg(u_in[1] + pos);
+            u[2] = __ldg(u_in[2] + pos);
+            const R w = __ldg(w_in + pos);
+            st[k].id = id_in ? __ldg(id_in + pos) : 0;
+
+            // ---- gather (Yee positions: E_a staggered along a, B_a along the other two)
+            R wn[3][ORD + 1], wsg[3][ORD + 1];
+            int bn[3], bsg[3];
+            bn[0] = shape_nodal<ORD>(l[0], o[0], wn[0]) - I.box_lo[0];
+            bsg[0] = shape_stag<ORD>(l[0], o[0], wsg[0]) - I.box_lo[0];
+            if (ND == 3) {
+                bn[1] = shape_nodal<ORD>(l[1], o[1], wn[1]) - I.box_lo[1];
+                bsg[1] = shape_stag<ORD>(l[1], o[1], wsg[1]) - I.box_lo[1];
+            } else {
+                bn[1] = bsg[1] = 0;
+#pragma unroll
+                for (int q = 0; q <= ORD; ++q) wn[1][q] = wsg[1][q] = R(0);
+                wn[1][0] = wsg[1][0] = R(1);
+            }
+            bn[2] = shape_nodal<ORD>(l[2], o[2], wn[2]) - I.box_lo[2];
+            bsg[2] = shape_stag<ORD>(l[2], o[2], wsg[2]) - I.box_lo[2];
+            R E[3], B[3];
+            E[0] = interp<ND, ORD, R>(sF + 0 * (box_stride / sizeof(R)), bx, bxy, bsg[0], bn[1], bn[2], wsg[0], wn[1], wn[2]);
+            E[1] = interp<ND, ORD, R>(sF + 1 * (box_stride / sizeof(R)), bx, bxy, bn[0], bsg[1], bn[2], wn[0], wsg[1], wn[2]);
+            E[2] = interp<ND, ORD, R>(sF + 2 * (box_stride / sizeof(R)), bx, bxy, bn[0], bn[1], bsg[2], wn[0], wn[1], wsg[2]);
+            B[0] = interp<ND, ORD, R>(sF + 3 * (box_stride / sizeof(R)), bx, bxy, bn[0], bsg[1], bsg[2], wn[0], wsg[1], wsg[2]);
+            B[1] = interp<ND, ORD, R>(sF + 4 * (box_stride / sizeof(R)), bx, bxy, bsg[0], bn[1], bsg[2], wsg[0], wn[1], wsg[2]);
+            B[2] = interp<ND, ORD, R>(sF + 5 * (box_stride / sizeof(R)), bx, bxy, bsg[0], bsg[1], bn[2], wsg[0], wsg[1], wn[2]);
+
+            // ---- push
+            if (PUSHER == 0)
+                push_vay(u, E, B, h);
+            else
+                push_boris(u, E, B, h);
+
+            // ---- move
+            bool bad = false;
+            R o1[3] = {o[0], o[1], o[2]};
+            int kstep[3] = {0, 0, 0};
+            R vy;
+            if (sizeof(R) == 4) {
+                const float gn = sqrtf(1.f + (float)u[0] * (float)u[0] + (float)u[1] * (float)u[1] + (float)u[2] * (float)u[2]);
+                const float ig = 1.f / gn;
+                float ox = (float)o1[0], oy = (float)o1[1], oz = (float)o1[2];
+                kstep[0] = move_axis(ox, (float)u[0], ig, (float)dtdx[0], bad);
+                if (ND == 3) kstep[1] = move_axis(oy, (float)u[1], ig, (float)dtdx[1], bad);
+                kstep[2] = move_axis(oz, (float)u[2], ig, (float)dtdx[2], bad);
+                o1[0] = R(ox); o1[1] = R(oy); o1[2] = R(oz);
+                vy = R((float)u[1] * ig);
+            } else {
+                const double gn = gamma_of((double)u[0], (double)u[1], (double)u[2]);
+                double ox = (double)o1[0], oy = (double)o1[1], oz = (double)o1[2];
+                kstep[0] = move_axis(ox, (double)u[0], gn, I.dt, I.dx[0], bad);
+                if (ND == 3) kstep[1] = move_axis(oy, (double)u[1], gn, I.dt, I.dx[1], bad);
+                kstep[2] = move_axis(oz, (double)u[2], gn, I.dt, I.dx[2], bad);
+                o1[0] = R(ox); o1[1] = R(oy); o1[2] = R(oz);
+                vy = R((double)u[1] / gn);
+            }
+            if (bad) {
+                atomicOr(I.err, kErrSpeed);
+                o1[0] = o[0]; o1[1] = o[1]; o1[2] = o[2];
+                kstep[0] = kstep[1] = kstep[2] = 0;
+            }
+            const int l1[3] = {l[0] + kstep[0], l[1] + kstep[1], l[2] + kstep[2]};
+
+            // ---- Esirkepov deposit into the shared J tile
+            {
+                constexpr int W = ORD + 2;
+                R S0x[W], S1x[W], S0y[W], S1y[W], S0z[W], S1z[W];
+                const int wsx = shape_window<ORD>(l[0], o[0], l1[0], o1[0], S0x, S1x) - I.jlo;
+                const int wsz = shape_window<ORD>(l[2], o[2], l1[2], o1[2], S0z, S1z) - I.jlo;
+                R DSx[W], DSz[W];
+#pragma unroll
+                for (int i = 0; i < W; ++i) { DSx[i] = S1x[i] - S0x[i]; DSz[i] = S1z[i] - S0z[i]; }
+                R *Jx = sJ, *Jy = sJ + jvol, *Jz = sJ + 2 * jvol;
+                const R qw = qdv * w;
+                if (ND == 3) {
+                    const int wsy = shape_window<ORD>(l[1], o[1], l1[1], o1[1], S0y, S1y) - jlo_y;
+                    R DSy[W];
+#pragma unroll
+                    for (int i = 0; i < W; ++i) DSy[i] = S1y[i] - S0y[i];
+                    const R fx = -qw * jfx, fy = -qw * jfy, fz = -qw * jfz;
+                    const R third = R(1.0 / 3.0);
+                    // Jx: running sum of DSx along x, times the transverse factor
+#pragma unroll
+                    for (int k = 0; k < W; ++k)
+#pragma unroll
+                        for (int j = 0; j < W; ++j) {
+                            const R Y = S0y[j] * S0z[k] + R(0.5) * (DSy[j] * S0z[k] + S0y[j] * DSz[k]) + third * DSy[j] * DSz[k];
+                            R acc = R(0);
+                            R *row = Jx + wsx + jd0 * (wsy + j) + jd01 * (wsz + k);
+#pragma unroll
+                            for (int i = 0; i < W - 1; ++i) {
+                                acc += DSx[i];
+                                const R v = fx * acc * Y;
+                                if (v != R(0)) atomicAdd(row + i, v);
+                            }
+                        }
+#pragma unroll
+                    for (int k = 0; k < W; ++k)
+#pragma unroll
+                        for (int i = 0; i < W; ++i) {
+                            const R X = S0x[i] * S0z[k] + R(0.5) * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) + third * DSx[i] * DSz[k];
+                            R acc = R(0);
+                            R *col = Jy + (wsx + i) + jd0 * wsy + jd01 * (wsz + k);
+#pragma unroll
+                            for (int j = 0; j < W - 1; ++j) {
+                                acc += DSy[j];
+                                const R v = fy * acc * X;
+                                if (v != R(0)) atomicAdd(col + jd0 * j, v);
+                            }
+                        }
+#pragma unroll
+                    for (int j = 0; j < W; ++j)
+#pragma unroll
+                        for (int i = 0; i < W; ++i) {
+                            const R X = S0x[i] * S0y[j] + R(0.5) * (DSx[i] * S0y[j] + S0x[i] * DSy[j]) + third * DSx[i] * DSy[j];
+                            R acc = R(0);
+                            R *col = Jz + (wsx + i) + jd0 * (wsy + j) + jd01 * wsz;
+#pragma unroll
+                            for (int k = 0; k < W - 1; ++k) {
+                                acc += DSz[k];
+                                const R v = fz * acc * X;
+                                if (v != R(0)) atomicAdd(col + jd01 * k, v);
+                            }
+                        }
+                } else {
+                    // 2D3V in the x-z plane (y invariant): in-plane currents by running sums,
+                    // the out-of-plane Jy from the averaged shape.
+                    const R fx = -qw * jfx, fz = -qw * jfz, fyo = qw * vy;
+                    const R third = R(1.0 / 3.0);
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        const R Y = S0z[k] + R(0.5) * DSz[k];
+                        R acc = R(0);
+                        R *row = Jx + wsx + jd01 * (wsz + k);
+#pragma unroll
+                        for (int i = 0; i < W - 1; ++i) {
+                            acc += DSx[i];
+                            const R v = fx * acc * Y;
+                            if (v != R(0)) atomicAdd(row + i, v);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        const R X = S0x[i] + R(0.5) * DSx[i];
+                        R acc = R(0);
+                        R *col = Jz + (wsx + i) + jd01 * wsz;
+#pragma unroll
+                        for (int k = 0; k < W - 1; ++k) {
+                            acc += DSz[k];
+                            const R v = fz * acc * X;
+                            if (v != R(0)) atomicAdd(col + jd01 * k, v);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < W; ++k)
+#pragma unroll
+                        for (int i = 0; i < W; ++i) {
+                            const R v = fyo * (S0x[i] * S0z[k] + R(0.5) * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) +
+                                               third * DSx[i] * DSz[k]);
+                            if (v != R(0)) atomicAdd(Jy + (wsx + i) + jd01 * (wsz + k), v);
+                        }
+                }
+            }
+
+            // ---- new cell, destination tile, bucket
+            int cn[3] = {cx + kstep[0], cy + kstep[1], cz + kstep[2]};
+            bool dead = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (ND == 2 && a == 1) continue;
+                if (cn[a] < 0 || cn[a] >= I.n[a]) {
+                    if (I.bc[a] == 0)
+                        cn[a] += cn[a] < 0 ? I.n[a] : -I.n[a];
+                    else
+                        dead = true;
+                }
+            }
+            if (dead) {
+                st[k].bucket = kDead;
+            } else {
+                const int ddx = axis_dir(tx, cn[0] / I.ts[0], I.nt[0], I.bc[0]);
+                const int ddy = ND == 3 ? axis_dir(ty, cn[1] / I.ts[1], I.nt[1], I.bc[1]) : 0;
+                const int ddz = axis_dir(tz, cn[2] / I.ts[2], I.nt[2], I.bc[2]);
+                st[k].bucket = (ddz + 1) * 9 + (ddy + 1) * 3 + (ddx + 1);
+            }
+            st[k].cell = cn[0] + I.n[0] * (cn[1] + I.n[1] * cn[2]);
+            kn[k].o[0] = o1[0]; kn[k].o[1] = o1[1]; kn[k].o[2] = o1[2];
+            kn[k].u[0] = u[0]; kn[k].u[1] = u[1]; kn[k].u[2] = u[2];
+            kn[k].w = w;
+        }
+
+        // ---- stable ranking of the chunk by bucket: order (k, warp, lane)
+        int rank[kPPT];
+#pragma unroll
+        for (int k = 0; k < kPPT; ++k) {
+            const unsigned peers = __match_any_sync(0xffffffffu, st[k].bucket);
+            rank[k] = __popc(peers & ((1u << lane) - 1u));
+            if (st[k].bucket < kBuckets && lane == __ffs(peers) - 1) s_cnt[k][warp][st[k].bucket] = __popc(peers);
+        }
+        __syncthreads();
+        if (tid < kBuckets) {
+            int run = 0;
+            for (int k = 0; k < kPPT; ++k)
+                for (int ww = 0; ww < kNW; ++ww) {
+                    const int v = s_cnt[k][ww][tid];
+                    s_cnt[k][ww][tid] = run;
+                    run += v;
+                }
+            s_round[tid] = run;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            const int c = chunk_out + r;
+            int *pre = I.chunk_pre[out] + (long long)c * kPre;
+            int *cb = I.chunk_cb[out] + (long long)c * kBuckets;
+            for (int d = 0; d < kBuckets; ++d) {
+                s_base[d] = acc;
+                pre[d] = acc;
+                cb[d] = s_run[d];
+                s_run[d] += s_round[d];
+                acc += s_round[d];
+            }
+            pre[kBuckets] = acc;
+        }
+        __syncthreads();
+        int *cell_out = I.cell[out];
+        R *off_out[3] = {(R *)I.off[out][0], (R *)I.off[out][1], (R *)I.off[out][2]};
+        R *u_out[3] = {(R *)I.u[out][0], (R *)I.u[out][1], (R *)I.u[out][2]};
+        R *w_out = (R *)I.w[out];
+        int *id_out = I.id[out];
+#pragma unroll
+        for (int k = 0; k < kPPT; ++k) {
+            const int b = st[k].bucket;
+            if (b >= kDead) continue;
+            const int pos = seg_out + base + s_base[b] + s_cnt[k][warp][b] + rank[k];
+            cell_out[pos] = st[k].cell;
+            off_out[0][pos] = kn[k].o[0];
+            if (ND == 3) off_out[1][pos] = kn[k].o[1];
+            off_out[2][pos] = kn[k].o[2];
+            u_out[0][pos] = kn[k].u[0];
+            u_out[1][pos] = kn[k].u[1];
+            u_out[2][pos] = kn[k].u[2];
+            w_out[pos] = kn[k].w;
+            if (id_out) id_out[pos] = st[k].id;
+        }
+        __syncthreads();
+    }
+
+    // ---- tile bookkeeping for the next step
+    if (tid < kBuckets) I.tot[out][t * kBuckets + tid] = s_run[tid];
+    if (tid < kDirs && s_run[tid] > 0) {
+        const int ddx = tid % 3 - 1, ddy = (tid / 3) % 3 - 1, ddz = tid / 9 - 1;
+        int nx = tx + ddx, ny = ty + ddy, nz = tz + ddz;
+        nx = (nx + I.nt[0]) % I.nt[0];
+        ny = (ny + I.nt[1]) % I.nt[1];
+        nz = (nz + I.nt[2]) % I.nt[2];
+        atomicAdd(I.pop + nx + I.nt[0] * (ny + I.nt[1] * nz), s_run[tid]);
+    }
+    if (tid == 0 && s_run[kDead] > 0) atomicAdd(I.lost, (unsigned long long)s_run[kDead]);
+
+    // ---- flush the J tile (guard cells wrap on periodic axes, clip on absorbing ones)
+    for (int e = tid; e < 3 * jvol; e += kNT) {
+        const R v = sJ[e];
+        if (v == R(0)) continue;
+        const int comp = e / jvol;
+        const int rem = e - comp * jvol;
+        const int lx = rem % I.jdim[0];
+        const int ly = (rem / I.jdim[0]) % I.jdim[1];
+        const int lz = rem / jd01;
+        int gidx[3] = {T0[0] + I.jlo + lx, ND == 3 ? T0[1] + I.jlo + ly : 0, T0[2] + I.jlo + lz};
+        bool keep = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (ND == 2 && a == 1) continue;
+            if (gidx[a] < 0 || gidx[a] >= I.n[a]) {
+                if (I.bc[a] == 0)
+                    gidx[a] += gidx[a] < 0 ? I.n[a] : -I.n[a];
+                else
+                    keep = false;
+            }
+        }
+        if (!keep) continue;
+        R *J = (R *)I.J[comp];
+        atomicAdd(J + (gidx[0] + I.gh[0]) + I.sy * (gidx[1] + I.gh[1]) + I.sz * (gidx[2] + I.gh[2]), v);
+    }
+}
+
+}  // namespace pic

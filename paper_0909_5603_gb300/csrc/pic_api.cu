@@ -1,0 +1,1078 @@
+// pic_api.cu -- host side of the C ABI declared in include/pic.h: instance set-up
+// (geometry, device memory through the caller's allocator, TMA descriptors), loaders,
+// the step sequence (graph-captured), getters, profiling and batching.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "lab_frame.h"
+#include "pic_internal.h"
+
+using namespace pic;
+
+namespace {
+
+struct Block {
+    void *p;
+    size_t bytes;
+};
+
+constexpr int kPhases = 5;  // particles, scan, filter, maxwell, other
+constexpr int kEventSteps = 1024;
+
+}  // namespace
+
+struct pic_ctx {
+    bool is_batch = false;
+    std::vector<pic_ctx *> members;
+    std::vector<uint64_t> member_versions;
+    // configuration
+    int ndim = 3, n[3] = {1, 1, 1}, bc[3] = {0, 0, 0}, order = 1;
+    double dx[3] = {1, 1, 1}, dt = 0, gamma_b = 1;
+    pic_options opt{};
+    int fp64 = 0;
+    size_t es = 4;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    // device views
+    InstDev h{};
+    InstDev *d_inst = nullptr;
+    int *d_tile_start = nullptr;
+    long long *d_cell_start = nullptr;
+    Launch L{};
+    size_t smem = 0;
+    long long ncell = 0;
+    long long ghost_max = 0;
+    bool any_periodic[3] = {false, false, false};
+    int max_sweeps = 0;
+    std::vector<Block> blocks;
+    uint64_t version = 1;  // bumps when device pointers of the instance change
+    // state
+    bool loaded = false;
+    int64_t step = 0;
+    int last_filtered = 0;
+    // scratch
+    double *d_dense = nullptr;   // ncell doubles (field exchange)
+    double *d_sums = nullptr;    // diagnostics sums
+    int *d_start = nullptr;      // ntiles + 1 read-out offsets
+    int **d_start_ptr = nullptr; // device array holding d_start
+    int stage_cap = 0;
+    int *st_cell = nullptr, *st_id = nullptr;
+    double *st_off = nullptr, *st_u = nullptr, *st_w = nullptr;
+    // graph
+    cudaGraphExec_t graph = nullptr;
+    // profiling
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+    std::vector<unsigned char> recorded;  // per (slot, phase): both events recorded
+    int ev_steps = 0;
+    pic_timings acc{};
+    std::string err;
+};
+
+static std::string g_create_error;
+
+static pic_status fail(pic_ctx *c, pic_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+    return s;
+}
+
+#define CUDA_OR_FAIL(c, call)                                                                              \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess) return fail((c), PIC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static void *dalloc(pic_ctx *c, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (c->opt.alloc) {
+        p = c->opt.alloc(bytes, c->opt.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->blocks.push_back({p, bytes});
+    return p;
+}
+
+static void dfree(pic_ctx *c, void *p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < c->blocks.size(); ++i)
+        if (c->blocks[i].p == p) {
+            if (c->opt.free) c->opt.free(p, c->opt.alloc_user);
+            else cudaFree(p);
+            c->blocks.erase(c->blocks.begin() + i);
+            return;
+        }
+}
+
+static void dfree_all(pic_ctx *c)
+{
+    for (auto &b : c->blocks) {
+        if (c->opt.free) c->opt.free(b.p, c->opt.alloc_user);
+        else cudaFree(b.p);
+    }
+    c->blocks.clear();
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+static bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+// ------------------------------------------------------------------------------------
+// options and creation
+// ------------------------------------------------------------------------------------
+extern "C" void pic_default_options(pic_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = PIC_PREC_FP32;
+    o->pusher = PIC_PUSHER_VAY;
+    o->filter_passes = 0;
+    o->threads = 256;
+    o->absorb_cells = 16;
+    o->absorb_strength = 0.1;
+    o->charge = -1.0;
+    o->mass = 1.0;
+    o->track_ids = 1;
+    o->device = -1;
+}
+
+extern "C" const char *pic_last_error(const pic_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+static int activeaxis(int ndim, int a) { return !(ndim == 2 && a == 1); }
+
+static pic_status upload_inst(pic_ctx *c)
+{
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_inst, &c->h, sizeof(InstDev), cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+static pic_status encode_tmaps(pic_ctx *c, CUtensorMap *maps)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[3] = {(cuuint64_t)c->h.P[0], (cuuint64_t)c->h.P[1], (cuuint64_t)c->h.P[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->h.sy * c->es, (cuuint64_t)c->h.sz * c->es};
+    const cuuint32_t box[3] = {(cuuint32_t)c->h.box[0], (cuuint32_t)c->h.box[1], (cuuint32_t)c->h.box[2]};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int comp = 0; comp < 6; ++comp) {
+        void *base = comp < 3 ? c->h.E[comp] : c->h.B[comp - 3];
+        CUresult r = enc(&maps[comp], c->fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
+                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for component %d", (int)r, comp);
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], double dt, double gamma_boost, int shape_order,
+                                 const pic_options *opt, pic_ctx **out)
+{
+    if (!out) return fail(nullptr, PIC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !dx) return fail(nullptr, PIC_ERR_ARG, "grid or dx is NULL");
+    if (grid->ndim != 2 && grid->ndim != 3) return fail(nullptr, PIC_ERR_ARG, "ndim must be 2 or 3");
+    if (grid->ndim == 2 && grid->n[1] != 1) return fail(nullptr, PIC_ERR_ARG, "2D grids are x-z: n[1] must be 1");
+    for (int a = 0; a < 3; ++a) {
+        if (!activeaxis(grid->ndim, a)) continue;
+        if (grid->n[a] < 4) return fail(nullptr, PIC_ERR_ARG, "n[%d] = %d: at least 4 cells per axis", a, grid->n[a]);
+        if (grid->bc[a] != PIC_PERIODIC && grid->bc[a] != PIC_ABSORBING) return fail(nullptr, PIC_ERR_ARG, "bc[%d] invalid", a);
+        if (!(dx[a] > 0.0) || !std::isfinite(dx[a])) return fail(nullptr, PIC_ERR_ARG, "dx[%d] must be finite and > 0", a);
+    }
+    if ((long long)grid->n[0] * grid->n[1] * grid->n[2] >= (1LL << 31))
+        return fail(nullptr, PIC_ERR_ARG, "grid too large for int32 cell indices");
+    if (shape_order != 1 && shape_order != 2) return fail(nullptr, PIC_ERR_ARG, "shape_order must be 1 or 2");
+    if (!(gamma_boost >= 1.0) || !std::isfinite(gamma_boost)) return fail(nullptr, PIC_ERR_ARG, "gamma_boost must be >= 1");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, PIC_ERR_ARG, "dt must be finite and > 0");
+    double inv2 = 0.0;
+    for (int a = 0; a < 3; ++a)
+        if (activeaxis(grid->ndim, a)) inv2 += 1.0 / (dx[a] * dx[a]);
+    if (dt > 1.0 / std::sqrt(inv2) * (1.0 + 1e-12))
+        return fail(nullptr, PIC_ERR_CFL, "dt = %g exceeds the Courant limit %g", dt, 1.0 / std::sqrt(inv2));
+
+    pic_options o;
+    pic_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != PIC_PREC_FP32 && o.precision != PIC_PREC_FP64) return fail(nullptr, PIC_ERR_ARG, "precision invalid");
+    if (o.pusher != PIC_PUSHER_VAY && o.pusher != PIC_PUSHER_BORIS) return fail(nullptr, PIC_ERR_ARG, "pusher invalid");
+    if (o.filter_passes < 0 || o.filter_passes > 64) return fail(nullptr, PIC_ERR_ARG, "filter_passes out of range");
+    if (o.threads != 0 && o.threads != particle_threads())
+        return fail(nullptr, PIC_ERR_UNSUPPORTED, "threads = %d: this build runs %d threads per particle CTA", o.threads,
+                    particle_threads());
+    if (o.absorb_cells < 0 || !(o.absorb_strength >= 0.0 && o.absorb_strength < 1.0))
+        return fail(nullptr, PIC_ERR_ARG, "absorbing layer parameters out of range");
+    if (!(o.mass > 0.0) || !std::isfinite(o.charge)) return fail(nullptr, PIC_ERR_ARG, "species charge/mass invalid");
+    if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(nullptr, PIC_ERR_ARG, "alloc and free must be given together");
+
+    pic_ctx *c = new pic_ctx();
+    c->ndim = grid->ndim;
+    c->order = shape_order;
+    c->dt = dt;
+    c->gamma_b = gamma_boost;
+    c->opt = o;
+    c->fp64 = o.precision == PIC_PREC_FP64;
+    c->es = c->fp64 ? 8 : 4;
+    c->stream = (cudaStream_t)o.stream;
+    if (o.device >= 0) {
+        if (cudaSetDevice(o.device) != cudaSuccess) {
+            delete c;
+            return fail(nullptr, PIC_ERR_CUDA, "cudaSetDevice(%d) failed", o.device);
+        }
+    }
+    cudaGetDevice(&c->device);
+    for (int a = 0; a < 3; ++a) {
+        c->n[a] = grid->n[a];
+        c->bc[a] = activeaxis(grid->ndim, a) ? grid->bc[a] : PIC_PERIODIC;
+        c->dx[a] = dx[a];
+    }
+    InstDev &h = c->h;
+    std::memset(&h, 0, sizeof(h));
+    h.ndim = c->ndim;
+    int ts[3] = {o.tile[0], o.tile[1], o.tile[2]};
+    for (int a = 0; a < 3; ++a) {
+        h.n[a] = c->n[a];
+        h.bc[a] = c->bc[a];
+        h.gh[a] = activeaxis(c->ndim, a) ? kGhost : 0;
+        if (ts[a] <= 0) ts[a] = c->ndim == 3 ? 8 : 16;
+        if (!activeaxis(c->ndim, a)) ts[a] = 1;
+        h.ts[a] = ts[a];
+        h.nt[a] = (c->n[a] + ts[a] - 1) / ts[a];
+        h.dx[a] = dx[a];
+        if (activeaxis(c->ndim, a) && c->bc[a] == PIC_PERIODIC) c->any_periodic[a] = true;
+    }
+    if (ts[0] % 4 != 0) {
+        delete c;
+        return fail(nullptr, PIC_ERR_ARG, "tile[0] = %d must be a multiple of 4", ts[0]);
+    }
+    for (int a = 0; a < 3; ++a)
+        if (activeaxis(c->ndim, a) && ts[a] > 64) {
+            delete c;
+            return fail(nullptr, PIC_ERR_ARG, "tile[%d] = %d: at most 64", a, ts[a]);
+        }
+    h.P[0] = ((c->n[0] + 2 * kGhost) + 3) / 4 * 4;
+    h.P[1] = c->n[1] + 2 * h.gh[1];
+    h.P[2] = c->n[2] + 2 * h.gh[2];
+    h.sy = h.P[0];
+    h.sz = (long long)h.P[0] * h.P[1];
+    h.cstride = (h.sz * h.P[2] + 63) / 64 * 64;  // 256/512-byte aligned component arrays
+    h.ntiles = h.nt[0] * h.nt[1] * h.nt[2];
+    h.tile_base = 0;
+    h.R = particle_chunk();
+    h.filter_passes = o.filter_passes;
+    h.absorb_cells = o.absorb_cells;
+    h.absorb_strength = o.absorb_strength;
+    h.dt = dt;
+    h.q = o.charge;
+    h.m = o.mass;
+    // gather box (tile + guard) and J tile geometry
+    const int gx_lo = c->fp64 ? 2 : 4;  // x origin rounded so the TMA start is 16-byte aligned
+    const int xal = c->fp64 ? 2 : 4;
+    const int hi = shape_order == 2 ? 2 : 1;
+    h.box_lo[0] = -gx_lo;
+    h.box[0] = ((gx_lo + ts[0] + hi) + xal - 1) / xal * xal;
+    for (int a = 1; a < 3; ++a) {
+        if (activeaxis(c->ndim, a)) {
+            h.box_lo[a] = -1;
+            h.box[a] = 1 + ts[a] + hi;
+        } else {
+            h.box_lo[a] = 0;
+            h.box[a] = 1;
+        }
+    }
+    h.jlo = -shape_order;
+    for (int a = 0; a < 3; ++a) h.jdim[a] = activeaxis(c->ndim, a) ? ts[a] + (shape_order == 2 ? 5 : 3) : 1;
+    const size_t boxb = ((size_t)h.box[0] * h.box[1] * h.box[2] * c->es + 127) / 128 * 128;
+    c->smem = 128 + 6 * boxb + 3 * (size_t)h.jdim[0] * h.jdim[1] * h.jdim[2] * c->es;  // + alignment slack
+    if (c->smem > 200 * 1024) {
+        delete c;
+        return fail(nullptr, PIC_ERR_ARG, "tile too large: %zu bytes of shared memory per CTA", c->smem);
+    }
+    c->ncell = (long long)c->n[0] * c->n[1] * c->n[2];
+    {
+        long long gm = 0;
+        for (int a = 0; a < 3; ++a) {
+            const int o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
+            gm = std::max(gm, 6LL * 2 * h.gh[a] * h.P[o1] * h.P[o2]);
+        }
+        c->ghost_max = gm;
+    }
+    c->max_sweeps = o.filter_passes * (c->ndim == 3 ? 3 : 2);
+
+    // device memory: 12 field components (E, B, J, J scratch), bookkeeping, scratch
+    const size_t fbytes = 12 * (size_t)h.cstride * c->es;
+    unsigned char *F = (unsigned char *)dalloc(c, fbytes);
+    int *small = (int *)dalloc(c, 4096);
+    int nt1 = h.ntiles + 1;
+    int *tiles = (int *)dalloc(c, sizeof(int) * (size_t)(4 * nt1 + 2 * h.ntiles * kBuckets + h.ntiles + 64));
+    CUtensorMap *tm = (CUtensorMap *)dalloc(c, 6 * sizeof(CUtensorMap));
+    c->d_inst = (InstDev *)dalloc(c, sizeof(InstDev));
+    c->d_tile_start = (int *)dalloc(c, 2 * sizeof(int));
+    c->d_cell_start = (long long *)dalloc(c, 2 * sizeof(long long));
+    c->d_dense = (double *)dalloc(c, sizeof(double) * (size_t)c->ncell);
+    c->d_sums = (double *)dalloc(c, 64 * sizeof(double));
+    c->d_start = (int *)dalloc(c, sizeof(int) * (size_t)nt1);
+    c->d_start_ptr = (int **)dalloc(c, sizeof(int *));
+    if (!F || !small || !tiles || !tm || !c->d_inst || !c->d_tile_start || !c->d_cell_start || !c->d_dense || !c->d_sums ||
+        !c->d_start || !c->d_start_ptr) {
+        dfree_all(c);
+        delete c;
+        return fail(nullptr, PIC_ERR_OOM, "device allocation failed (%zu bytes of fields)", fbytes);
+    }
+    for (int a = 0; a < 3; ++a) {
+        h.E[a] = F + (size_t)(0 + a) * h.cstride * c->es;
+        h.B[a] = F + (size_t)(3 + a) * h.cstride * c->es;
+        h.J[a] = F + (size_t)(6 + a) * h.cstride * c->es;
+        h.Jt[a] = F + (size_t)(9 + a) * h.cstride * c->es;
+    }
+    h.cur = small;
+    h.err = small + 1;
+    h.live = small + 2;
+    h.jsel = small + 3;
+    h.lost = (unsigned long long *)(small + 4);
+    h.seg[0] = tiles;
+    h.seg[1] = tiles + nt1;
+    h.chunk_base[0] = tiles + 2 * nt1;
+    h.chunk_base[1] = tiles + 3 * nt1;
+    h.tot[0] = tiles + 4 * nt1;
+    h.tot[1] = tiles + 4 * nt1 + h.ntiles * kBuckets;
+    h.pop = tiles + 4 * nt1 + 2 * h.ntiles * kBuckets;
+    h.tmap = tm;
+
+    pic_status st = PIC_OK;
+    CUtensorMap maps[6];
+    if ((st = encode_tmaps(c, maps)) != PIC_OK) {
+        std::string e = c->err;
+        dfree_all(c);
+        delete c;
+        return fail(nullptr, st, "%s", e.c_str());
+    }
+    const int tstart[2] = {0, h.ntiles};
+    const long long cstart[2] = {0, c->ncell};
+    int *dptr_start = c->d_start;
+    bool okc = cudaMemsetAsync(F, 0, fbytes, c->stream) == cudaSuccess && cudaMemsetAsync(small, 0, 4096, c->stream) == cudaSuccess &&
+               cudaMemsetAsync(tiles, 0, sizeof(int) * (size_t)(4 * nt1 + 2 * h.ntiles * kBuckets + h.ntiles), c->stream) == cudaSuccess &&
+               cudaMemcpyAsync(tm, maps, sizeof(maps), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+               cudaMemcpyAsync(c->d_tile_start, tstart, sizeof(tstart), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+               cudaMemcpyAsync(c->d_cell_start, cstart, sizeof(cstart), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+               cudaMemcpyAsync(c->d_start_ptr, &dptr_start, sizeof(int *), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+               prepare_particles(c->ndim, c->order, c->fp64, o.pusher, c->smem) == cudaSuccess;
+    if (!okc || upload_inst(c) != PIC_OK) {
+        cudaError_t e = cudaGetLastError();
+        dfree_all(c);
+        delete c;
+        return fail(nullptr, PIC_ERR_CUDA, "device set-up failed: %s", cudaGetErrorString(e));
+    }
+    c->L.inst = c->d_inst;
+    c->L.tile_start = c->d_tile_start;
+    c->L.cell_start = c->d_cell_start;
+    c->L.ninst = 1;
+    c->L.total_tiles = h.ntiles;
+    c->L.total_cells = c->ncell;
+    *out = c;
+    return PIC_OK;
+}
+
+static void destroy_graph(pic_ctx *c)
+{
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+}
+
+extern "C" void pic_destroy(pic_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    destroy_graph(ctx);
+    for (auto e : ctx->events) cudaEventDestroy(e);
+    dfree_all(ctx);
+    delete ctx;
+}
+
+// ------------------------------------------------------------------------------------
+// particle loading: host stable sort by tile, then the initial layout (every tile's
+// particles in its own "stay" bucket, chunks of R particles)
+// ------------------------------------------------------------------------------------
+static pic_status ensure_particle_capacity(pic_ctx *c, int64_t n)
+{
+    InstDev &h = c->h;
+    const int want = (int)std::max<int64_t>(n, 1);
+    if (h.cell[0] && h.cap >= want) return PIC_OK;
+    for (int b = 0; b < 2; ++b) {
+        dfree(c, h.cell[b]);
+        dfree(c, h.chunk_pre[b]);
+        dfree(c, h.chunk_cb[b]);
+        h.cell[b] = nullptr;
+        h.chunk_pre[b] = h.chunk_cb[b] = nullptr;
+        h.id[b] = nullptr;
+    }
+    const int cap = want;
+    const int chunk_cap = h.ntiles + cap / h.R + 2;
+    const int nreal = c->ndim == 3 ? 7 : 6;  // offsets (3 or 2), momenta 3, weight
+    for (int b = 0; b < 2; ++b) {
+        const size_t per = (size_t)cap;
+        unsigned char *blk = (unsigned char *)dalloc(c, per * (sizeof(int) * 2) + per * nreal * c->es + 4096);
+        int *cb = (int *)dalloc(c, sizeof(int) * (size_t)chunk_cap * kPre);
+        int *cbb = (int *)dalloc(c, sizeof(int) * (size_t)chunk_cap * kBuckets);
+        if (!blk || !cb || !cbb) return fail(c, PIC_ERR_OOM, "particle buffers (%d particles) do not fit", cap);
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            void *p = blk + off;
+            off += (bytes + 255) & ~(size_t)255;
+            return p;
+        };
+        h.cell[b] = (int *)blk;
+        off = ((per * sizeof(int)) + 255) & ~(size_t)255;
+        h.id[b] = c->opt.track_ids ? (int *)take(per * sizeof(int)) : nullptr;
+        h.off[b][0] = take(per * c->es);
+        h.off[b][1] = c->ndim == 3 ? take(per * c->es) : nullptr;
+        h.off[b][2] = take(per * c->es);
+        for (int a = 0; a < 3; ++a) h.u[b][a] = take(per * c->es);
+        h.w[b] = take(per * c->es);
+        h.chunk_pre[b] = cb;
+        h.chunk_cb[b] = cbb;
+    }
+    h.cap = cap;
+    h.chunk_cap = chunk_cap;
+    c->stage_cap = 0;  // staging is re-sized lazily
+    c->version++;
+    return PIC_OK;
+}
+
+template <typename R>
+static void fill_typed(std::vector<unsigned char> &buf, const std::vector<double> &src, const std::vector<int64_t> &perm,
+                       int stride, int comp)
+{
+    buf.resize(perm.size() * sizeof(R));
+    R *d = (R *)buf.data();
+    for (size_t i = 0; i < perm.size(); ++i) d[i] = (R)src[(size_t)perm[i] * stride + comp];
+}
+
+static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, const double *off, const double *u,
+                                const double *w, const int32_t *id)
+{
+    InstDev &h = c->h;
+    if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", (long long)n);
+    if (n > 0 && (!cell || !off || !u || !w)) return fail(c, PIC_ERR_ARG, "particle arrays must not be NULL");
+    for (int64_t p = 0; p < n; ++p) {
+        if (cell[p] < 0 || cell[p] >= c->ncell) return fail(c, PIC_ERR_ARG, "particle %lld: cell %d outside the grid", (long long)p, cell[p]);
+        for (int a = 0; a < 3; ++a) {
+            if (!activeaxis(c->ndim, a)) continue;
+            const double o = off[3 * p + a];
+            if (!(o >= 0.0 && o < 1.0)) return fail(c, PIC_ERR_ARG, "particle %lld: offset %g outside [0,1)", (long long)p, o);
+        }
+        if (!finite3(u + 3 * p) || !std::isfinite(w[p])) return fail(c, PIC_ERR_NAN, "particle %lld: non-finite momentum or weight", (long long)p);
+    }
+    // stable counting sort by tile id
+    std::vector<int> tcount(h.ntiles + 1, 0);
+    std::vector<int> tile_of(n > 0 ? n : 1);
+    for (int64_t p = 0; p < n; ++p) {
+        const int ci = cell[p] % c->n[0], cj = (cell[p] / c->n[0]) % c->n[1], ck = cell[p] / (c->n[0] * c->n[1]);
+        const int t = ci / h.ts[0] + h.nt[0] * (cj / h.ts[1] + h.nt[1] * (ck / h.ts[2]));
+        tile_of[p] = t;
+        tcount[t + 1]++;
+    }
+    for (int t = 0; t < h.ntiles; ++t) tcount[t + 1] += tcount[t];
+    std::vector<int> seg(tcount);
+    std::vector<int64_t> perm(n);
+    {
+        std::vector<int> fillp(tcount.begin(), tcount.end() - 1);
+        for (int64_t p = 0; p < n; ++p) perm[fillp[tile_of[p]]++] = p;
+    }
+    pic_status st = ensure_particle_capacity(c, n);
+    if (st != PIC_OK) return st;
+    // host arrays in canonical order, storage precision
+    std::vector<int> hcell(n), hid(n);
+    for (int64_t i = 0; i < n; ++i) {
+        hcell[i] = cell[perm[i]];
+        hid[i] = id ? id[perm[i]] : (int)perm[i];
+    }
+    std::vector<double> voff(off, off + 3 * n), vu(u, u + 3 * n), vw(w, w + n);
+    std::vector<unsigned char> buf;
+    auto put = [&](void *dst, const std::vector<double> &src, int stride, int comp) -> pic_status {
+        if (c->fp64) fill_typed<double>(buf, src, perm, stride, comp);
+        else fill_typed<float>(buf, src, perm, stride, comp);
+        if (n > 0) CUDA_OR_FAIL(c, cudaMemcpy(dst, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+        return PIC_OK;
+    };
+    if (n > 0) {
+        CUDA_OR_FAIL(c, cudaMemcpy(h.cell[0], hcell.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        if (h.id[0]) CUDA_OR_FAIL(c, cudaMemcpy(h.id[0], hid.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (h.off[0][a] && (st = put(h.off[0][a], voff, 3, a)) != PIC_OK) return st;
+        if ((st = put(h.u[0][a], vu, 3, a)) != PIC_OK) return st;
+    }
+    if ((st = put(h.w[0], vw, 1, 0)) != PIC_OK) return st;
+    // initial layout 0
+    const int R = h.R;
+    std::vector<int> cbase(h.ntiles + 1, 0), tot((size_t)h.ntiles * kBuckets, 0), pop(h.ntiles, 0);
+    for (int t = 0; t < h.ntiles; ++t) {
+        const int m = seg[t + 1] - seg[t];
+        cbase[t + 1] = cbase[t] + (m + R - 1) / R;
+        tot[(size_t)t * kBuckets + kCenterDir] = m;
+        pop[t] = m;
+    }
+    const int nchunks = cbase[h.ntiles];
+    if (nchunks > h.chunk_cap) return fail(c, PIC_ERR_INTERNAL, "chunk capacity");
+    std::vector<int> pre((size_t)std::max(nchunks, 1) * kPre, 0), cbv((size_t)std::max(nchunks, 1) * kBuckets, 0);
+    for (int t = 0; t < h.ntiles; ++t) {
+        const int m = seg[t + 1] - seg[t];
+        for (int k = 0; k < cbase[t + 1] - cbase[t]; ++k) {
+            const int cc = cbase[t] + k;
+            const int sz = std::min(R, m - k * R);
+            for (int d = 0; d <= kBuckets; ++d) pre[(size_t)cc * kPre + d] = d <= kCenterDir ? 0 : sz;
+            cbv[(size_t)cc * kBuckets + kCenterDir] = k * R;
+        }
+    }
+    CUDA_OR_FAIL(c, cudaMemcpy(h.seg[0], seg.data(), sizeof(int) * (h.ntiles + 1), cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(c, cudaMemcpy(h.chunk_base[0], cbase.data(), sizeof(int) * (h.ntiles + 1), cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(c, cudaMemcpy(h.tot[0], tot.data(), sizeof(int) * tot.size(), cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(c, cudaMemcpy(h.pop, pop.data(), sizeof(int) * pop.size(), cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(c, cudaMemcpy(h.chunk_pre[0], pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(c, cudaMemcpy(h.chunk_cb[0], cbv.data(), sizeof(int) * cbv.size(), cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(c, cudaMemset(h.cur, 0, 16 + sizeof(unsigned long long)));
+    CUDA_OR_FAIL(c, cudaMemset(h.J[0], 0, 3 * (size_t)h.cstride * c->es));
+    c->loaded = true;
+    c->step = 0;
+    c->last_filtered = 0;
+    destroy_graph(c);
+    return upload_inst(c);
+}
+
+extern "C" pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3, const double *u3,
+                                         const double *w, const int32_t *id)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_load_particles on a batch");
+    cudaSetDevice(ctx->device);
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    return load_internal(ctx, n, cell, off3, u3, w, id);
+}
+
+static pic_status ghost_fill_now(pic_ctx *c)
+{
+    for (int a = 0; a < 3; ++a)
+        if (c->any_periodic[a]) CUDA_OR_FAIL(c, launch_ghost(c->fp64, c->L, a, c->ghost_max, c->stream));
+    return PIC_OK;
+}
+
+static pic_status set_field_internal(pic_ctx *c, int comp, const double *host)
+{
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_dense, host, sizeof(double) * (size_t)c->ncell, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, launch_unpack(c->fp64, c->h, comp, c->d_dense, c->ncell, c->stream));
+    pic_status st = ghost_fill_now(c);
+    if (st != PIC_OK) return st;
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_field(pic_ctx *ctx, int comp, const double *host, size_t count)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_set_field on a batch");
+    if (comp < PIC_EX || comp > PIC_JZ) return fail(ctx, PIC_ERR_ARG, "component %d cannot be set", comp);
+    if (!host || count < (size_t)ctx->ncell) return fail(ctx, PIC_ERR_ARG, "need %lld values", ctx->ncell);
+    for (long long i = 0; i < ctx->ncell; ++i)
+        if (!std::isfinite(host[i])) return fail(ctx, PIC_ERR_NAN, "non-finite field value at %lld", i);
+    cudaSetDevice(ctx->device);
+    return set_field_internal(ctx, comp, host);
+}
+
+extern "C" pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *laser, const pic_plasma_lab *plasma,
+                                         const pic_beam_lab *beam)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_load_lab_frame on a batch");
+    if (laser && !(laser->lambda0 > 0 && laser->waist > 0 && laser->duration > 0 && std::isfinite(laser->a0) &&
+                   std::isfinite(laser->z_center)))
+        return fail(ctx, PIC_ERR_ARG, "laser parameters invalid");
+    if (plasma && !(plasma->ppc >= 1 && plasma->n0 >= 0 && std::isfinite(plasma->n0) && plasma->ramp_len >= 0 &&
+                    std::isfinite(plasma->z_start) && finite3(plasma->u_th)))
+        return fail(ctx, PIC_ERR_ARG, "plasma parameters invalid");
+    if (beam && !(beam->n >= 1 && beam->gamma > 1.0 && beam->sigma_r >= 0 && beam->sigma_z >= 0 && beam->rel_spread >= 0 &&
+                  std::isfinite(beam->z0) && std::isfinite(beam->total_weight)))
+        return fail(ctx, PIC_ERR_ARG, "beam parameters invalid");
+    cudaSetDevice(ctx->device);
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    Geometry G{ctx->ndim, {ctx->n[0], ctx->n[1], ctx->n[2]}, {ctx->dx[0], ctx->dx[1], ctx->dx[2]}};
+    LabParticles P;
+    std::vector<double> Ex, By;
+    transform_lab_inputs(G, ctx->gamma_b, laser, plasma, beam, P, Ex, By);
+    // fields: all zero except the laser
+    CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->h.E[0], 0, 12 * (size_t)ctx->h.cstride * ctx->es, ctx->stream));
+    pic_status st;
+    if (laser) {
+        if ((st = set_field_internal(ctx, PIC_EX, Ex.data())) != PIC_OK) return st;
+        if ((st = set_field_internal(ctx, PIC_BY, By.data())) != PIC_OK) return st;
+    }
+    const int64_t np = (int64_t)P.cell.size();
+    return load_internal(ctx, np, P.cell.data(), P.off.data(), P.mom.data(), P.weight.data(), P.id.data());
+}
+
+// ------------------------------------------------------------------------------------
+// stepping
+// ------------------------------------------------------------------------------------
+static const Launch &launch_of(pic_ctx *c) { return c->L; }
+
+struct PhaseTimer {
+    pic_ctx *c;
+    int slot;
+    void begin(int phase)
+    {
+        if (c->profiling) cudaEventRecord(c->events[(size_t)(slot * kPhases + phase) * 2], c->stream);
+    }
+    void end(int phase)
+    {
+        if (!c->profiling) return;
+        cudaEventRecord(c->events[(size_t)(slot * kPhases + phase) * 2 + 1], c->stream);
+        c->recorded[(size_t)slot * kPhases + phase] = 1;
+    }
+};
+
+static pic_status fold_timings(pic_ctx *c);
+
+static pic_status enqueue_step(pic_ctx *c, int mask)
+{
+    const Launch &L = launch_of(c);
+    const int fp64 = c->fp64;
+    PhaseTimer tm{c, c->ev_steps};
+    if (c->profiling && c->ev_steps >= kEventSteps) {
+        pic_status st = fold_timings(c);
+        if (st != PIC_OK) return st;
+        tm.slot = 0;
+    }
+    int launches = 0;
+    if (mask & PIC_PHASE_PARTICLES) {
+        tm.begin(4);
+        if (c->is_batch) {
+            for (auto m : c->members)
+                CUDA_OR_FAIL(c, cudaMemsetAsync(m->h.J[0], 0, 3 * (size_t)m->h.cstride * m->es, c->stream));
+        } else {
+            CUDA_OR_FAIL(c, cudaMemsetAsync(c->h.J[0], 0, 3 * (size_t)c->h.cstride * c->es, c->stream));
+        }
+        tm.end(4);
+        tm.begin(1);
+        CUDA_OR_FAIL(c, launch_scan(L, 0, nullptr, c->stream));
+        tm.end(1);
+        tm.begin(0);
+        CUDA_OR_FAIL(c, launch_particles(c->ndim, c->order, fp64, c->opt.pusher, L, c->smem, c->stream));
+        tm.end(0);
+        launches += 2;
+    }
+    int filtered = 0;
+    if ((mask & PIC_PHASE_FILTER) && c->max_sweeps > 0) {
+        tm.begin(2);
+        CUDA_OR_FAIL(c, launch_filter(fp64, L, c->max_sweeps, c->stream));
+        tm.end(2);
+        filtered = 1;
+        launches += c->max_sweeps;
+    }
+    if (mask & PIC_PHASE_MAXWELL) {
+        tm.begin(3);
+        CUDA_OR_FAIL(c, launch_maxwell(fp64, L, filtered, c->stream));
+        launches += 3;
+        for (int a = 0; a < 3; ++a)
+            if (c->any_periodic[a]) {
+                CUDA_OR_FAIL(c, launch_ghost(fp64, L, a, c->ghost_max, c->stream));
+                launches++;
+            }
+        tm.end(3);
+    }
+    if (mask & (PIC_PHASE_FILTER | PIC_PHASE_MAXWELL)) {
+        c->last_filtered = filtered;
+        if (c->is_batch)
+            for (auto m : c->members) m->last_filtered = filtered;
+    }
+    if (c->profiling) {
+        c->ev_steps = tm.slot + 1;
+        c->acc.launches += launches;
+        c->acc.steps += 1;
+    }
+    return PIC_OK;
+}
+
+static pic_status refresh_batch(pic_ctx *c);
+
+extern "C" pic_status pic_step(pic_ctx *ctx, int n)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (n < 0) return fail(ctx, PIC_ERR_ARG, "n must be >= 0");
+    cudaSetDevice(ctx->device);
+    if (ctx->is_batch) {
+        pic_status st = refresh_batch(ctx);
+        if (st != PIC_OK) return st;
+    } else if (!ctx->loaded) {
+        return fail(ctx, PIC_ERR_STATE, "pic_step before any load");
+    }
+    for (int s = 0; s < n; ++s) {
+        if (ctx->profiling || ctx->stream == nullptr) {
+            pic_status st = enqueue_step(ctx, PIC_PHASE_ALL);
+            if (st != PIC_OK) return st;
+        } else {
+            if (!ctx->graph) {
+                cudaGraph_t g;
+                CUDA_OR_FAIL(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                pic_status st = enqueue_step(ctx, PIC_PHASE_ALL);
+                cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+                if (st != PIC_OK) return st;
+                if (e != cudaSuccess) return fail(ctx, PIC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+                e = cudaGraphInstantiate(&ctx->graph, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    ctx->graph = nullptr;
+                    return fail(ctx, PIC_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+                }
+            }
+            CUDA_OR_FAIL(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+        }
+        ctx->step++;
+        if (ctx->is_batch)
+            for (auto m : ctx->members) m->step++;
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_run_phases(pic_ctx *ctx, int mask)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (mask <= 0 || mask > PIC_PHASE_ALL) return fail(ctx, PIC_ERR_ARG, "phase mask %d invalid", mask);
+    cudaSetDevice(ctx->device);
+    if (ctx->is_batch) {
+        pic_status st = refresh_batch(ctx);
+        if (st != PIC_OK) return st;
+    } else if (!ctx->loaded) {
+        return fail(ctx, PIC_ERR_STATE, "pic_run_phases before any load");
+    }
+    pic_status st = enqueue_step(ctx, mask);
+    if (st != PIC_OK) return st;
+    if (mask == PIC_PHASE_ALL) {
+        ctx->step++;
+        if (ctx->is_batch)
+            for (auto m : ctx->members) m->step++;
+    }
+    return PIC_OK;
+}
+
+static pic_status check_device_error(pic_ctx *c)
+{
+    int err = 0;
+    CUDA_OR_FAIL(c, cudaMemcpy(&err, c->h.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & kErrTimeout) return fail(c, PIC_ERR_TIMEOUT, "a bounded device wait timed out (error word 0x%x)", err);
+    if (err & kErrSpeed) return fail(c, PIC_ERR_PARTICLE_SPEED, "a particle moved a cell or more in one step, or is not finite (0x%x)", err);
+    if (err & (kErrInternal | kErrCapacity)) return fail(c, PIC_ERR_INTERNAL, "device consistency check failed (0x%x)", err);
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_synchronize(pic_ctx *ctx)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaGetLastError());
+    if (ctx->is_batch) {
+        for (auto m : ctx->members) {
+            pic_status st = check_device_error(m);
+            if (st != PIC_OK) return fail(ctx, st, "%s", m->err.c_str());
+        }
+        return PIC_OK;
+    }
+    return check_device_error(ctx);
+}
+
+// ------------------------------------------------------------------------------------
+// getters
+// ------------------------------------------------------------------------------------
+extern "C" pic_status pic_get_field(pic_ctx *ctx, int comp, double *host_out, size_t count)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "getters take a member, not a batch");
+    if (comp < PIC_EX || comp > PIC_DIVE) return fail(ctx, PIC_ERR_ARG, "component %d invalid", comp);
+    if (!host_out || count < (size_t)ctx->ncell) return fail(ctx, PIC_ERR_ARG, "need room for %lld values", ctx->ncell);
+    pic_status st = pic_synchronize(ctx);
+    if (st != PIC_OK) return st;
+    if (comp == PIC_RHO) {
+        CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_dense, 0, sizeof(double) * (size_t)ctx->ncell, ctx->stream));
+        if (ctx->loaded) CUDA_OR_FAIL(ctx, launch_rho(ctx->order, ctx->fp64, ctx->L, ctx->d_dense, ctx->stream));
+    } else if (comp == PIC_DIVE) {
+        CUDA_OR_FAIL(ctx, launch_dive(ctx->fp64, ctx->h, ctx->d_dense, ctx->ncell, ctx->stream));
+    } else {
+        CUDA_OR_FAIL(ctx, launch_pack(ctx->fp64, ctx->h, comp, ctx->last_filtered, ctx->d_dense, ctx->ncell, ctx->stream));
+    }
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(host_out, ctx->d_dense, sizeof(double) * (size_t)ctx->ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
+}
+
+static pic_status count_live(pic_ctx *c, int with_offsets, int *live)
+{
+    CUDA_OR_FAIL(c, launch_scan(c->L, 1, c->d_start_ptr, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(live, c->h.live, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    (void)with_offsets;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_num_particles(pic_ctx *ctx, int64_t *n_out)
+{
+    if (!ctx || !n_out) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "getters take a member, not a batch");
+    pic_status st = pic_synchronize(ctx);
+    if (st != PIC_OK) return st;
+    int live = 0;
+    if (ctx->loaded && (st = count_live(ctx, 0, &live)) != PIC_OK) return st;
+    *n_out = live;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off3, double *u3, double *w, int32_t *id,
+                                        int64_t cap, int64_t *n_out)
+{
+    if (!ctx || !n_out) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "getters take a member, not a batch");
+    pic_status st = pic_synchronize(ctx);
+    if (st != PIC_OK) return st;
+    *n_out = 0;
+    if (!ctx->loaded) return PIC_OK;
+    int live = 0;
+    if ((st = count_live(ctx, 1, &live)) != PIC_OK) return st;
+    *n_out = live;
+    if (live > cap) return fail(ctx, PIC_ERR_ARG, "cap %lld < %d live particles", (long long)cap, live);
+    if (live == 0) return PIC_OK;
+    InstDev &h = ctx->h;
+    if (ctx->stage_cap < h.cap) {
+        dfree(ctx, ctx->st_cell);
+        ctx->st_cell = nullptr;
+        const size_t per = (size_t)h.cap;
+        unsigned char *blk = (unsigned char *)dalloc(ctx, per * (2 * sizeof(int) + 7 * sizeof(double)) + 2048);
+        if (!blk) return fail(ctx, PIC_ERR_OOM, "read-out staging does not fit");
+        size_t o = 0;
+        auto take = [&](size_t b) {
+            void *p = blk + o;
+            o += (b + 255) & ~(size_t)255;
+            return p;
+        };
+        ctx->st_cell = (int *)take(per * sizeof(int));
+        ctx->st_id = (int *)take(per * sizeof(int));
+        ctx->st_off = (double *)take(per * 3 * sizeof(double));
+        ctx->st_u = (double *)take(per * 3 * sizeof(double));
+        ctx->st_w = (double *)take(per * sizeof(double));
+        ctx->stage_cap = h.cap;
+    }
+    CUDA_OR_FAIL(ctx, launch_readout(ctx->fp64, ctx->L, ctx->d_start_ptr, ctx->st_cell, ctx->st_off, ctx->st_u, ctx->st_w,
+                                     ctx->st_id, ctx->stream));
+    const size_t n = (size_t)live;
+    if (cell) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(cell, ctx->st_cell, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    if (id) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(id, ctx->st_id, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    if (off3) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(off3, ctx->st_off, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (u3) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(u3, ctx->st_u, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (w) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(w, ctx->st_w, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
+}
+
+extern "C" pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out)
+{
+    if (!ctx || !out) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "getters take a member, not a batch");
+    pic_status st = pic_synchronize(ctx);
+    int err = 0;
+    cudaMemcpy(&err, ctx->h.err, sizeof(int), cudaMemcpyDeviceToHost);
+    std::memset(out, 0, sizeof(*out));
+    out->error_flags = err;
+    if (st != PIC_OK) return st;
+    CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_sums, 0, 3 * sizeof(double), ctx->stream));
+    if (ctx->loaded) CUDA_OR_FAIL(ctx, launch_particle_sums(ctx->fp64, ctx->L, ctx->d_sums, ctx->stream));
+    CUDA_OR_FAIL(ctx, launch_field_energy(ctx->fp64, ctx->L, ctx->d_sums, ctx->stream));
+    double sums[3];
+    unsigned long long lost = 0;
+    int live = 0;
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(sums, ctx->d_sums, sizeof(sums), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(&lost, ctx->h.lost, sizeof(lost), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->loaded && (st = count_live(ctx, 0, &live)) != PIC_OK) return st;
+    out->step = ctx->step;
+    out->t = ctx->step * ctx->dt;
+    out->kinetic_energy = sums[0];
+    out->total_charge = sums[1];
+    out->field_energy = sums[2];
+    out->n_particles = live;
+    out->n_lost = (int64_t)lost;
+    return check_device_error(ctx);
+}
+
+// ------------------------------------------------------------------------------------
+// profiling
+// ------------------------------------------------------------------------------------
+static pic_status fold_timings(pic_ctx *c)
+{
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < c->ev_steps; ++s)
+        for (int ph = 0; ph < kPhases; ++ph) {
+            if (!c->recorded[(size_t)s * kPhases + ph]) continue;
+            c->recorded[(size_t)s * kPhases + ph] = 0;
+            cudaEvent_t a = c->events[(size_t)(s * kPhases + ph) * 2], b = c->events[(size_t)(s * kPhases + ph) * 2 + 1];
+            float ms = 0.f;
+            CUDA_OR_FAIL(c, cudaEventElapsedTime(&ms, a, b));
+            double *dst = ph == 0 ? &c->acc.ms_particles : ph == 1 ? &c->acc.ms_scan : ph == 2 ? &c->acc.ms_filter
+                          : ph == 3 ? &c->acc.ms_maxwell : &c->acc.ms_other;
+            *dst += ms;
+        }
+    c->ev_steps = 0;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_profiling(pic_ctx *ctx, int on, int reset)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (on && ctx->events.empty()) {
+        ctx->events.resize((size_t)kEventSteps * kPhases * 2);
+        ctx->recorded.assign((size_t)kEventSteps * kPhases, 0);
+        for (auto &e : ctx->events) CUDA_OR_FAIL(ctx, cudaEventCreate(&e));
+    }
+    if (ctx->profiling && !on) {
+        pic_status st = fold_timings(ctx);
+        if (st != PIC_OK) return st;
+    }
+    if (reset) {
+        if (!ctx->events.empty()) {
+            pic_status st = fold_timings(ctx);
+            if (st != PIC_OK) return st;
+        }
+        std::memset(&ctx->acc, 0, sizeof(ctx->acc));
+    }
+    ctx->profiling = on != 0;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_timings(pic_ctx *ctx, pic_timings *out)
+{
+    if (!ctx || !out) return PIC_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (!ctx->events.empty()) {
+        pic_status st = fold_timings(ctx);
+        if (st != PIC_OK) return st;
+    }
+    *out = ctx->acc;
+    return PIC_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// batching
+// ------------------------------------------------------------------------------------
+static pic_status refresh_batch(pic_ctx *c)
+{
+    bool stale = c->member_versions.size() != c->members.size();
+    for (size_t i = 0; !stale && i < c->members.size(); ++i) stale = c->member_versions[i] != c->members[i]->version;
+    for (auto m : c->members)
+        if (!m->loaded) return fail(c, PIC_ERR_STATE, "a batch member has no particles loaded");
+    if (!stale) return PIC_OK;
+    const int n = (int)c->members.size();
+    std::vector<InstDev> insts(n);
+    std::vector<int> ts(n + 1, 0);
+    std::vector<long long> cs(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        insts[i] = c->members[i]->h;
+        insts[i].tile_base = ts[i];
+        ts[i + 1] = ts[i] + insts[i].ntiles;
+        cs[i + 1] = cs[i] + c->members[i]->ncell;
+    }
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_inst, insts.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_tile_start, ts.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_cell_start, cs.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    c->L.total_tiles = ts[n];
+    c->L.total_cells = cs[n];
+    c->member_versions.clear();
+    for (auto m : c->members) c->member_versions.push_back(m->version);
+    destroy_graph(c);
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx **batch)
+{
+    if (!batch) return fail(nullptr, PIC_ERR_ARG, "batch is NULL");
+    *batch = nullptr;
+    if (n < 1 || !instances) return fail(nullptr, PIC_ERR_ARG, "need at least one instance");
+    pic_ctx *f = instances[0];
+    for (int i = 0; i < n; ++i) {
+        pic_ctx *m = instances[i];
+        if (!m || m->is_batch) return fail(nullptr, PIC_ERR_ARG, "instance %d is NULL or a batch", i);
+        if (m->ndim != f->ndim || m->order != f->order || m->fp64 != f->fp64 || m->opt.pusher != f->opt.pusher ||
+            m->device != f->device || m->smem != f->smem || m->h.ts[0] != f->h.ts[0] || m->h.ts[1] != f->h.ts[1] ||
+            m->h.ts[2] != f->h.ts[2])
+            return fail(nullptr, PIC_ERR_ARG, "instance %d differs in dimension, shape, precision, pusher, tile or device", i);
+        for (int j = 0; j < i; ++j)
+            if (instances[j] == m) return fail(nullptr, PIC_ERR_ARG, "instance %d appears twice", i);
+    }
+    pic_ctx *c = new pic_ctx();
+    c->is_batch = true;
+    c->members.assign(instances, instances + n);
+    c->ndim = f->ndim;
+    c->order = f->order;
+    c->fp64 = f->fp64;
+    c->es = f->es;
+    c->opt = f->opt;
+    c->device = f->device;
+    c->stream = f->stream;
+    c->smem = f->smem;
+    c->h = f->h;
+    c->d_inst = (InstDev *)dalloc(c, sizeof(InstDev) * n);
+    c->d_tile_start = (int *)dalloc(c, sizeof(int) * (n + 1));
+    c->d_cell_start = (long long *)dalloc(c, sizeof(long long) * (n + 1));
+    if (!c->d_inst || !c->d_tile_start || !c->d_cell_start) {
+        dfree_all(c);
+        delete c;
+        return fail(nullptr, PIC_ERR_OOM, "batch tables do not fit");
+    }
+    for (auto m : c->members) {
+        for (int a = 0; a < 3; ++a) c->any_periodic[a] = c->any_periodic[a] || m->any_periodic[a];
+        c->ghost_max = std::max(c->ghost_max, m->ghost_max);
+        c->max_sweeps = std::max(c->max_sweeps, m->max_sweeps);
+    }
+    c->L.inst = c->d_inst;
+    c->L.tile_start = c->d_tile_start;
+    c->L.cell_start = c->d_cell_start;
+    c->L.ninst = n;
+    *batch = c;
+    return PIC_OK;
+}

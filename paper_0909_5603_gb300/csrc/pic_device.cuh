@@ -1,0 +1,259 @@
+// pic_device.cuh -- per-particle device arithmetic of the boosted-frame PIC step:
+// B-spline shape factors, Vay and Boris pushers, position update, and the TMA /
+// mbarrier primitives of the field-staging stage (inline PTX, sm_103a).
+#pragma once
+
+#include "pic_internal.h"
+
+namespace pic {
+
+// ------------------------------------------------------------------------------------
+// Shape factors of order 1 (linear) and 2 (quadratic B-spline) for a particle in cell l
+// with in-cell offset o.  "Nodal" quantities sit at integer positions, "staggered" ones
+// at i + 1/2 (Yee grid).  Each call returns the first node (relative to the tile) and
+// the ORD + 1 weights.
+// ------------------------------------------------------------------------------------
+template <int ORD, typename R>
+__device__ __forceinline__ int shape_nodal(int l, R o, R w[ORD + 1])
+{
+    if (ORD == 1) {
+        w[0] = R(1) - o;
+        w[1] = o;
+        return l;
+    } else {
+        const bool up = o >= R(0.5);
+        const R f = up ? o - R(1) : o;  // distance from the nearest node, in [-1/2, 1/2)
+        const R a = R(0.5) - f, b = R(0.5) + f;
+        w[0] = R(0.5) * a * a;
+        w[1] = R(0.75) - f * f;
+        w[2] = R(0.5) * b * b;
+        return l + (up ? 1 : 0) - 1;
+    }
+}
+
+template <int ORD, typename R>
+__device__ __forceinline__ int shape_stag(int l, R o, R w[ORD + 1])
+{
+    if (ORD == 1) {
+        const bool up = o >= R(0.5);
+        const R f = up ? o - R(0.5) : o + R(0.5);
+        w[0] = R(1) - f;
+        w[1] = f;
+        return up ? l : l - 1;
+    } else {
+        const R f = o - R(0.5);
+        const R a = R(0.5) - f, b = R(0.5) + f;
+        w[0] = R(0.5) * a * a;
+        w[1] = R(0.75) - f * f;
+        w[2] = R(0.5) * b * b;
+        return l - 1;
+    }
+}
+
+// Shape weights of the old and new positions on one common window of ORD + 2 nodes
+// starting at node `ws` (tile-relative), for the Esirkepov deposit.  The nearest nodes
+// of the two positions differ by at most one (moves below one cell per step).
+template <int ORD, typename R>
+__device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R S0[ORD + 2], R S1[ORD + 2])
+{
+    R w0[ORD + 1], w1[ORD + 1];
+    const int b0 = shape_nodal<ORD>(l0, o0, w0);
+    const int b1 = shape_nodal<ORD>(l1, o1, w1);
+    const int ws = b0 < b1 ? b0 : b1;
+    const int s0 = b0 - ws, s1 = b1 - ws;  // 0 or 1
+#pragma unroll
+    for (int i = 0; i < ORD + 2; ++i) {
+        const R a0 = (i < ORD + 1) ? w0[i < ORD + 1 ? i : 0] : R(0);
+        const R a1 = (i >= 1) ? w0[i >= 1 ? i - 1 : 0] : R(0);
+        S0[i] = s0 == 0 ? a0 : a1;
+        const R c0 = (i < ORD + 1) ? w1[i < ORD + 1 ? i : 0] : R(0);
+        const R c1 = (i >= 1) ? w1[i >= 1 ? i - 1 : 0] : R(0);
+        S1[i] = s1 == 0 ? c0 : c1;
+    }
+    return ws;
+}
+
+// ------------------------------------------------------------------------------------
+// Vay pusher (Sec. 2 of the paper; Vay, Phys. Plasmas 15, 056701 (2008)).  c = 1,
+// h = q dt / (2 m):
+//   u' = u + 2h E + h v x B,  tau = h B,  u* = u'.tau,  sigma = (1 + u'^2) - tau^2,
+//   gamma^2 = (sigma + sqrt(sigma^2 + 4 (tau^2 + u*^2))) / 2   (sigma >= 0)
+//           = 2 (tau^2 + u*^2) / (sqrt(...) - sigma)            (sigma < 0, same value),
+//   t = tau / gamma,  s = 1 / (1 + t^2),  u_new = s (u' + (u'.t) t + u' x t).
+// FP32 form: sigma is the one quantity that cancels at large gamma (gamma'^2 ~ tau^2), so
+// gamma'^2, tau^2 and their difference are formed in FP64 from the FP32 operands; the
+// roots are FP32, taken on the cancellation-free branch.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void push_vay(float u[3], const float E[3], const float B[3], float h)
+{
+    const float g = sqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const float ig = 1.f / g;
+    const float v0 = u[0] * ig, v1 = u[1] * ig, v2 = u[2] * ig;
+    const float up0 = u[0] + 2.f * h * E[0] + h * (v1 * B[2] - v2 * B[1]);
+    const float up1 = u[1] + 2.f * h * E[1] + h * (v2 * B[0] - v0 * B[2]);
+    const float up2 = u[2] + 2.f * h * E[2] + h * (v0 * B[1] - v1 * B[0]);
+    const float t0 = h * B[0], t1 = h * B[1], t2 = h * B[2];
+    const float ustar = up0 * t0 + up1 * t1 + up2 * t2;
+    const double gp2 = 1.0 + (double)up0 * up0 + (double)up1 * up1 + (double)up2 * up2;
+    const double tau2d = (double)t0 * t0 + (double)t1 * t1 + (double)t2 * t2;
+    const float sigma = (float)(gp2 - tau2d);
+    const float tau2 = (float)tau2d;
+    const float q4 = tau2 + ustar * ustar;
+    const float root = sqrtf(sigma * sigma + 4.f * q4);
+    const float g2 = sigma >= 0.f ? 0.5f * (sigma + root) : 2.f * q4 / (root - sigma);
+    const float ign = 1.f / sqrtf(g2);
+    const float s0 = t0 * ign, s1 = t1 * ign, s2 = t2 * ign;
+    const float s = 1.f / (1.f + s0 * s0 + s1 * s1 + s2 * s2);
+    const float upt = up0 * s0 + up1 * s1 + up2 * s2;
+    u[0] = s * (up0 + upt * s0 + (up1 * s2 - up2 * s1));
+    u[1] = s * (up1 + upt * s1 + (up2 * s0 - up0 * s2));
+    u[2] = s * (up2 + upt * s2 + (up0 * s1 - up1 * s0));
+}
+
+__device__ __forceinline__ void push_vay(double u[3], const double E[3], const double B[3], double h)
+{
+    const double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double v0 = u[0] / g, v1 = u[1] / g, v2 = u[2] / g;
+    const double up0 = u[0] + 2.0 * h * E[0] + h * (v1 * B[2] - v2 * B[1]);
+    const double up1 = u[1] + 2.0 * h * E[1] + h * (v2 * B[0] - v0 * B[2]);
+    const double up2 = u[2] + 2.0 * h * E[2] + h * (v0 * B[1] - v1 * B[0]);
+    const double t0 = h * B[0], t1 = h * B[1], t2 = h * B[2];
+    const double tau2 = t0 * t0 + t1 * t1 + t2 * t2;
+    const double ustar = up0 * t0 + up1 * t1 + up2 * t2;
+    const double sigma = (1.0 + up0 * up0 + up1 * up1 + up2 * up2) - tau2;
+    const double q4 = tau2 + ustar * ustar;
+    const double root = sqrt(sigma * sigma + 4.0 * q4);
+    const double g2 = sigma >= 0.0 ? 0.5 * (sigma + root) : 2.0 * q4 / (root - sigma);
+    const double gn = sqrt(g2);
+    const double s0 = t0 / gn, s1 = t1 / gn, s2 = t2 / gn;
+    const double s = 1.0 / (1.0 + s0 * s0 + s1 * s1 + s2 * s2);
+    const double upt = up0 * s0 + up1 * s1 + up2 * s2;
+    u[0] = s * (up0 + upt * s0 + (up1 * s2 - up2 * s1));
+    u[1] = s * (up1 + upt * s1 + (up2 * s0 - up0 * s2));
+    u[2] = s * (up2 + upt * s2 + (up0 * s1 - up1 * s0));
+}
+
+// Boris pusher (Sec. 2; BorisICNSP): half electric kick, rotation with t = h B / gamma^-,
+// s = 2 t / (1 + t^2), half electric kick.
+template <typename R>
+__device__ __forceinline__ void push_boris(R u[3], const R E[3], const R B[3], R h)
+{
+    const R um0 = u[0] + h * E[0], um1 = u[1] + h * E[1], um2 = u[2] + h * E[2];
+    const R gm = sqrt(R(1) + um0 * um0 + um1 * um1 + um2 * um2);
+    const R t0 = h * B[0] / gm, t1 = h * B[1] / gm, t2 = h * B[2] / gm;
+    const R f = R(2) / (R(1) + t0 * t0 + t1 * t1 + t2 * t2);
+    const R s0 = f * t0, s1 = f * t1, s2 = f * t2;
+    const R p0 = um0 + (um1 * t2 - um2 * t1);
+    const R p1 = um1 + (um2 * t0 - um0 * t2);
+    const R p2 = um2 + (um0 * t1 - um1 * t0);
+    u[0] = um0 + (p1 * s2 - p2 * s1) + h * E[0];
+    u[1] = um1 + (p2 * s0 - p0 * s2) + h * E[1];
+    u[2] = um2 + (p0 * s1 - p1 * s0) + h * E[2];
+}
+
+// ------------------------------------------------------------------------------------
+// Position update in cell units: o += dt v / dx; k = floor(o); o -= k; an offset that
+// rounds to 1 after the subtraction becomes 0 in the next cell.  FP64 uses the same
+// operation order as a plain evaluation of (o + (dt * (u / g)) / dx) with every product
+// and quotient rounded (no contraction).  Returns the cell step k in {-1, 0, 1}; a move
+// outside (-1, 2) (impossible below the Courant limit unless values are not finite)
+// leaves the particle in place and sets *bad.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ int move_axis(float &o, float u, float ig, float dt_dx, bool &bad)
+{
+    float x = __fadd_rn(o, __fmul_rn(dt_dx, __fmul_rn(u, ig)));
+    if (!(x > -1.f && x < 2.f)) {
+        bad = true;
+        return 0;
+    }
+    const float k = floorf(x);
+    x = __fsub_rn(x, k);
+    int ki = (int)k;
+    if (x >= 1.f) {
+        x = 0.f;
+        ki += 1;
+    }
+    o = x;
+    return ki;
+}
+
+__device__ __forceinline__ int move_axis(double &o, double u, double g, double dt, double dx, bool &bad)
+{
+    double x = __dadd_rn(o, __ddiv_rn(__dmul_rn(dt, __ddiv_rn(u, g)), dx));
+    if (!(x > -1.0 && x < 2.0)) {
+        bad = true;
+        return 0;
+    }
+    const double k = floor(x);
+    x = __dsub_rn(x, k);
+    int ki = (int)k;
+    if (x >= 1.0) {
+        x = 0.0;
+        ki += 1;
+    }
+    o = x;
+    return ki;
+}
+
+__device__ __forceinline__ double gamma_of(double u0, double u1, double u2)
+{
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dadd_rn(1.0, __dmul_rn(u0, u0)), __dmul_rn(u1, u1)), __dmul_rn(u2, u2)));
+}
+
+// ------------------------------------------------------------------------------------
+// TMA (cp.async.bulk.tensor) and mbarrier primitives.  Every wait is bounded in time.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Waits for phase `parity` of the barrier for at most ~`limit_cycles` SM clocks.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit_cycles)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit_cycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+}  // namespace pic

@@ -1,0 +1,120 @@
+// pic_internal.h -- device view of one simulation instance and shared definitions of
+// the sm_103a boosted-frame PIC kernels.  Not part of the public ABI (include/pic.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+constexpr int kGhost = 4;       // ghost layers per side of every active axis (fields)
+constexpr int kDirs = 27;       // tile-to-tile move directions (3 per axis)
+constexpr int kDead = 27;       // bucket of particles removed at absorbing faces
+constexpr int kBuckets = 28;    // 27 directions + dead
+constexpr int kPre = 29;        // per chunk: exclusive prefix of the 28 buckets + size
+constexpr int kCenterDir = 13;  // (0,0,0)
+
+// device error word bits (sticky)
+constexpr int kErrTimeout = 1;      // a bounded mbarrier wait gave up
+constexpr int kErrSpeed = 2;        // |displacement| >= 1 cell or non-finite in a step
+constexpr int kErrInternal = 4;     // layout/count consistency check failed
+constexpr int kErrCapacity = 8;     // more particles than the buffers hold
+
+// Device view of one instance.  Pointers are device addresses; field arrays are padded
+// with kGhost layers per side on active axes, x rows padded to a 16-byte multiple.
+struct InstDev {
+    int ndim;
+    int n[3];       // interior cells
+    int bc[3];      // 0 periodic, 1 absorbing
+    int gh[3];      // ghost layers per axis (kGhost or 0 on the inactive y of 2D)
+    int P[3];       // padded dims
+    long long sy, sz;  // padded strides (elements)
+    long long cstride; // elements per component array
+    int ts[3];      // tile size
+    int nt[3];      // tiles per axis
+    int ntiles;
+    int tile_base;  // first global tile index of this instance in a launch
+    int R;          // particles per chunk (threads * particles per thread)
+    int cap;        // particle capacity per buffer
+    int chunk_cap;  // chunk records per layout
+    int filter_passes;
+    int absorb_cells;
+    double absorb_strength;
+    double dt, dx[3], q, m;
+    // fields (element type set by the precision of the launch)
+    void *E[3], *B[3], *J[3], *Jt[3];  // Jt: scratch for filter sweeps
+    // particles, two buffers
+    int *cell[2];
+    void *off[2][3];
+    void *u[2][3];
+    void *w[2];
+    int *id[2];   // null when ids are not tracked
+    // tile layouts, two sets (input / output of a step)
+    int *seg[2];        // [ntiles + 1] segment starts in the particle buffer
+    int *chunk_base[2]; // [ntiles + 1] first chunk record of each tile
+    int *chunk_pre[2];  // [chunk_cap * kPre]
+    int *chunk_cb[2];   // [chunk_cap * kBuckets] count of each bucket in earlier chunks of the tile
+    int *tot[2];        // [ntiles * kBuckets] bucket totals of each tile
+    int *pop;           // [ntiles] particles in each tile at the step boundary
+    int *cur;           // device parity: which layout/buffer holds the current state
+    int *jsel;          // which J array (0: J, 1: Jt) holds the filtered current
+    int *err;           // sticky error word
+    unsigned long long *lost; // particles removed so far
+    int *live;          // live particles (written by the scan)
+    const CUtensorMap *tmap;  // 6 maps: Ex Ey Ez Bx By Bz boxes for the gather stage
+    int box[3];         // TMA box extents (elements)
+    int box_lo[3];      // box origin relative to the tile origin (cells, <= 0)
+    int jlo;            // J tile origin relative to the tile origin (-1 or -2)
+    int jdim[3];        // J tile extents
+};
+
+// launch-wide view of a set of instances stepped together
+struct Launch {
+    const InstDev *inst;  // device array
+    const int *tile_start;// [ninst + 1] global tile offsets (device)
+    const long long *cell_start; // [ninst + 1] global interior-cell offsets (device)
+    int ninst;
+    int total_tiles;
+    long long total_cells;
+};
+
+__device__ __forceinline__ int find_instance(const int *tile_start, int ninst, int g)
+{
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_start + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_instance_ll(const long long *start, int ninst, long long g)
+{
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// host-side launchers
+cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, const Launch &L, size_t smem, cudaStream_t s);
+int particle_chunk();
+int particle_threads();
+cudaError_t launch_scan(const Launch &L, int mode, int *const *dst, cudaStream_t s);
+cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, int *cell, double *off, double *u,
+                           double *w, int *id, cudaStream_t s);
+cudaError_t launch_particle_sums(int fp64, const Launch &L, double *sums, cudaStream_t s);
+cudaError_t launch_rho(int order, int fp64, const Launch &L, double *rho, cudaStream_t s);
+cudaError_t launch_filter(int fp64, const Launch &L, int max_sweeps, cudaStream_t s);
+cudaError_t launch_maxwell(int fp64, const Launch &L, int filtered, cudaStream_t s);
+cudaError_t launch_ghost(int fp64, const Launch &L, int axis, long long per_inst_max, cudaStream_t s);
+cudaError_t prepare_particles(int ndim, int order, int fp64, int pusher, size_t smem);
+cudaError_t launch_field_energy(int fp64, const Launch &L, double *sums, cudaStream_t s);
+cudaError_t launch_pack(int fp64, const InstDev &I, int comp, int filtered, double *dense, long long ncell, cudaStream_t s);
+cudaError_t launch_unpack(int fp64, const InstDev &I, int comp, const double *dense, long long ncell, cudaStream_t s);
+cudaError_t launch_dive(int fp64, const InstDev &I, double *dense, long long ncell, cudaStream_t s);
+
+}  // namespace pic

@@ -1,0 +1,62 @@
+"""Seeded synthetic inputs shared by the CUDA-path tests, the oracle tests and the smoke
+check.  Holds no arithmetic of the PIC method: only random particle and field arrays in
+the layout of include/pic.h (values chosen exactly representable in FP32, so an FP32
+store of them is lossless).
+"""
+import numpy as np
+
+
+def f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def uniform_plasma(n, ndim, ppc, sigma_u, seed, weight=None, drift=(0.0, 0.0, 0.0)):
+    """ppc particles per cell at uniform random in-cell offsets, Gaussian momenta
+    (sigma_u per component, plus a drift), equal weights (default 1/ppc)."""
+    rng = np.random.default_rng(seed)
+    n = list(n)
+    if ndim == 2:
+        n[1] = 1
+    ncell = n[0] * n[1] * n[2]
+    cell = np.repeat(np.arange(ncell, dtype=np.int32), ppc)
+    npart = cell.size
+    off = f32(rng.random((npart, 3), dtype=np.float32))
+    if ndim == 2:
+        off[:, 1] = 0.0
+    u = f32(rng.normal(0.0, sigma_u, (npart, 3)) + np.asarray(drift))
+    w = np.full(npart, (1.0 / ppc) if weight is None else weight)
+    return dict(cell=cell, off=off, u=u, w=f32(w), id=np.arange(npart, dtype=np.int32))
+
+
+def random_particles(n, ndim, npart, sigma_u, seed):
+    """npart particles in random cells (uneven tile populations, empty tiles possible)."""
+    rng = np.random.default_rng(seed)
+    n = list(n)
+    if ndim == 2:
+        n[1] = 1
+    ncell = n[0] * n[1] * n[2]
+    cell = rng.integers(0, ncell, npart).astype(np.int32)
+    off = f32(rng.random((npart, 3), dtype=np.float32))
+    if ndim == 2:
+        off[:, 1] = 0.0
+    u = f32(rng.normal(0.0, sigma_u, (npart, 3)))
+    w = f32(rng.uniform(0.5, 1.5, npart))
+    return dict(cell=cell, off=off, u=u, w=w, id=np.arange(npart, dtype=np.int32))
+
+
+def smooth_fields(n, ndim, amp, seed, modes=3):
+    """Six smooth periodic random fields (sums of a few Fourier modes), (n2, n1, n0) each."""
+    rng = np.random.default_rng(seed)
+    n = list(n)
+    if ndim == 2:
+        n[1] = 1
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    out = []
+    for _ in range(6):
+        f = np.zeros(i.shape)
+        for _m in range(modes):
+            m = rng.integers(0, 3, 3)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += rng.normal() * np.cos(2 * np.pi * (m[0] * i / n[0] + m[1] * j / n[1] + m[2] * k / n[2]) + ph)
+        out.append(f32(amp * f))
+    return out

@@ -1,0 +1,76 @@
+"""The C ABI library loads and exports every entry point that include/pic.h declares;
+argument validation that needs no device answers with the documented status codes."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_0909_5603_gb300 as pic
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "pic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z_]+)\s*\(", src)) - {"pic_alloc_fn", "pic_free_fn"})
+
+
+@pytest.fixture(scope="module")
+def L():
+    pic.build()
+    return pic.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 17
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(pic.EXPORTED)
+
+
+def test_default_options(L):
+    o = pic.pic_default_options()
+    assert o.precision == pic.PIC_PREC_FP32 and o.pusher == pic.PIC_PUSHER_VAY
+    assert o.absorb_cells == 16 and abs(o.absorb_strength - 0.1) < 1e-15
+    assert o.charge == -1.0 and o.mass == 1.0 and o.track_ids == 1
+
+
+def _create(ndim, n, bc, dx, dt, order=1, gamma=1.0, opt=None):
+    h = ctypes.c_void_p()
+    g = pic.pic_grid(ndim, (ctypes.c_int * 3)(*n), (ctypes.c_int * 3)(*bc))
+    st = pic.lib().pic_create(ctypes.byref(g), (ctypes.c_double * 3)(*dx), dt, gamma, order,
+                              ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    return st, h
+
+
+def test_argument_validation_before_any_device_call(L):
+    # Courant limit 1/sqrt(3) for a unit cube
+    st, h = _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.6)
+    assert st == pic.PIC_ERR_CFL and not h.value
+    assert b"Courant" in L.pic_last_error(None)
+    assert _create(4, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.5)[0] == pic.PIC_ERR_ARG
+    assert _create(2, (16, 2, 16), (0, 0, 0), (1, 1, 1), 0.5)[0] == pic.PIC_ERR_ARG
+    assert _create(3, (16, 16, 2), (0, 0, 0), (1, 1, 1), 0.5)[0] == pic.PIC_ERR_ARG
+    assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.5, order=3)[0] == pic.PIC_ERR_ARG
+    assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.5, gamma=0.5)[0] == pic.PIC_ERR_ARG
+    assert _create(3, (16, 16, 16), (0, 0, 0), (1, -1, 1), 0.5)[0] == pic.PIC_ERR_ARG
+    o = pic.pic_default_options()
+    o.threads = 96
+    assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.5, opt=o)[0] == pic.PIC_ERR_UNSUPPORTED
+    o = pic.pic_default_options()
+    o.tile[0] = 6
+    assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.5, opt=o)[0] == pic.PIC_ERR_ARG
+    o = pic.pic_default_options()
+    o.precision = 7
+    assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.5, opt=o)[0] == pic.PIC_ERR_ARG
+
+
+def test_null_handles(L):
+    assert L.pic_step(None, 1) == pic.PIC_ERR_ARG
+    assert L.pic_synchronize(None) == pic.PIC_ERR_ARG
+    L.pic_destroy(None)
+    out = ctypes.c_void_p()
+    assert L.pic_batch_create(0, None, ctypes.byref(out)) == pic.PIC_ERR_ARG

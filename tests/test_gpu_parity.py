@@ -1,0 +1,308 @@
+"""CUDA path vs the FP64 oracle, element by element, on the same seeded inputs.
+
+Every call goes through the C ABI (paper_0909_5603_gb300 is a ctypes binding).  Bars:
+integer work (cells, canonical particle order, ids, counts) bit-exact; floating point
+within the benchmark spec's tolerances -- 1e-12 relative in FP64 mode, 1e-5 relative after
+100 steps in FP32 mode -- with the relative error of an array taken as
+max|gpu - oracle| / max|oracle| (the infinity-norm relative error).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_0909_5603_gb300 as pic
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = pic.PIC_PREC_FP32, pic.PIC_PREC_FP64
+VAY, BORIS = pic.PIC_PUSHER_VAY, pic.PIC_PUSHER_BORIS
+COMPS = [pic.PIC_EX, pic.PIC_EY, pic.PIC_EZ, pic.PIC_BX, pic.PIC_BY, pic.PIC_BZ]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pic.build()
+    oracle.build()
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+def pair(ndim, n, bc, dx, dt, order, prec, pusher=VAY, passes=0, tile=None, gamma=1.0):
+    if tile is None:
+        tile = (8, 8, 8) if ndim == 3 else (16, 1, 16)
+    g = pic.Simulation(ndim, n, bc, dx, dt, gamma_boost=gamma, order=order, precision=prec, pusher=pusher,
+                       filter_passes=passes, tile=tile)
+    o = oracle.Sim(ndim, n, bc, dx, dt, order=order, pusher=pusher, filter_passes=passes, tile=tile)
+    return g, o
+
+
+def load_both(g, o, parts):
+    g.load_particles(parts["cell"], parts["off"], parts["u"], parts["w"], parts["id"])
+    o.set_particles(parts["cell"], parts["off"], parts["u"], parts["w"], parts["id"])
+
+
+def set_fields_both(g, o, fields, comps=COMPS):
+    for c, f in zip(comps, fields):
+        g.set_field(c, f)
+        o.set_field(c, f)
+
+
+def compare_particles(g, o, tol, exact_order=True):
+    pg, po = g.get_particles(), o.get_particles()
+    assert pg["cell"].size == po["cell"].size
+    if exact_order:
+        assert np.array_equal(pg["id"], po["id"])
+        assert np.array_equal(pg["cell"], po["cell"])
+        assert rel(pg["off"], po["off"]) <= tol
+        assert rel(pg["u"], po["u"]) <= tol
+        assert rel(pg["w"], po["w"]) <= tol
+    else:
+        ig, io = np.argsort(pg["id"]), np.argsort(po["id"])
+        assert np.array_equal(pg["id"][ig], po["id"][io])
+        ng = np.asarray(g.n)
+        pos_g = _positions(pg, ng)[ig]
+        pos_o = _positions(po, ng)[io]
+        d = pos_g - pos_o
+        d -= np.round(d / ng) * ng  # periodic images
+        assert np.abs(d).max() <= tol * max(1.0, np.abs(pos_o).max())
+        assert rel(pg["u"][ig], po["u"][io]) <= tol
+    return pg, po
+
+
+def _positions(p, n):
+    c = p["cell"]
+    ijk = np.stack([c % n[0], (c // n[0]) % n[1], c // (n[0] * n[1])], 1).astype(np.float64)
+    return ijk + p["off"]
+
+
+def compare_fields(g, o, comps, tol):
+    for c in comps:
+        fo = o.get_field(c)
+        if np.abs(fo).max() == 0:
+            assert np.abs(g.get_field(c)).max() == 0
+            continue
+        assert rel(g.get_field(c), fo) <= tol, (c, rel(g.get_field(c), fo))
+
+
+# ---------------------------------------------------------------------------- phases
+CASES_3D = dict(ndim=3, n=(20, 16, 24), dx=(1.0, 0.9, 1.1), dt=0.45)
+CASES_2D = dict(ndim=2, n=(36, 1, 44), dx=(1.0, 1.0, 0.8), dt=0.5)
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-13), (FP32, 2e-6)])
+@pytest.mark.parametrize("case", ["3d_per", "3d_abs", "2d_per", "2d_abs"])
+def test_maxwell_phase(case, prec, tol):
+    c = dict(CASES_3D if case.startswith("3d") else CASES_2D)
+    bc = (0, 0, 0) if case.endswith("per") else (1, 1, 1)
+    g, o = pair(c["ndim"], c["n"], bc, c["dx"], c["dt"], 1, prec)
+    f = synth.smooth_fields(c["n"], c["ndim"], 0.3, seed=4)
+    set_fields_both(g, o, f)
+    J = synth.smooth_fields(c["n"], c["ndim"], 0.05, seed=5)[:3]
+    set_fields_both(g, o, J, [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ])
+    g.load_particles(np.zeros(0, np.int32), np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0))
+    for _ in range(3):
+        g.run_phases(pic.PIC_PHASE_MAXWELL)
+        o.maxwell()
+    compare_fields(g, o, COMPS, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-14), (FP32, 1e-6)])
+@pytest.mark.parametrize("ndim,bc", [(3, (0, 0, 0)), (3, (1, 0, 1)), (2, (0, 0, 0)), (2, (1, 0, 1))])
+@pytest.mark.parametrize("passes", [1, 3])
+def test_filter_phase(ndim, bc, passes, prec, tol):
+    c = dict(CASES_3D if ndim == 3 else CASES_2D)
+    g, o = pair(ndim, c["n"], bc, c["dx"], c["dt"], 1, prec, passes=passes)
+    rng = np.random.default_rng(9)
+    J = [synth.f32(rng.normal(size=(c["n"][2], c["n"][1] if ndim == 3 else 1, c["n"][0]))) for _ in range(3)]
+    set_fields_both(g, o, J, [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ])
+    g.load_particles(np.zeros(0, np.int32), np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0))
+    g.run_phases(pic.PIC_PHASE_FILTER)
+    o.filter()
+    compare_fields(g, o, [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ], tol)
+
+
+PARTICLE_CASES = [(nd, order, pusher, bcs) for nd in (3, 2) for order in (1, 2) for pusher in (VAY, BORIS)
+                  for bcs in ("per", "abs")]
+
+
+@pytest.mark.parametrize("ndim,order,pusher,bcs", PARTICLE_CASES)
+def test_particle_phase_fp64(ndim, order, pusher, bcs):
+    """One gather + push + move + deposit + reorder, random smooth fields, random cells
+    (uneven and empty tiles, ragged last tiles), momenta large enough to cross tiles."""
+    c = dict(CASES_3D if ndim == 3 else CASES_2D)
+    bc = (0, 0, 0) if bcs == "per" else (1, 1, 1)
+    g, o = pair(ndim, c["n"], bc, c["dx"], c["dt"], order, FP64, pusher=pusher)
+    f = synth.smooth_fields(c["n"], ndim, 0.2, seed=11)
+    set_fields_both(g, o, f)
+    parts = synth.random_particles(c["n"], ndim, 12000, 1.5, seed=12)
+    load_both(g, o, parts)
+    for _ in range(2):
+        g.run_phases(pic.PIC_PHASE_PARTICLES)
+        o.particle_phase()
+    compare_fields(g, o, [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ], 1e-12)
+    compare_particles(g, o, 1e-12)
+    dg, do = g.diagnostics(), o.diagnostics()
+    assert dg["n_particles"] == do["n_particles"] and dg["n_lost"] == do["n_lost"]
+
+
+@pytest.mark.parametrize("ndim,order", [(3, 1), (3, 2), (2, 1), (2, 2)])
+def test_particle_phase_fp32(ndim, order):
+    c = dict(CASES_3D if ndim == 3 else CASES_2D)
+    g, o = pair(ndim, c["n"], (0, 0, 0), c["dx"], c["dt"], order, FP32)
+    set_fields_both(g, o, synth.smooth_fields(c["n"], ndim, 0.2, seed=13))
+    load_both(g, o, synth.random_particles(c["n"], ndim, 12000, 1.5, seed=14))
+    g.run_phases(pic.PIC_PHASE_PARTICLES)
+    o.particle_phase()
+    compare_fields(g, o, [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ], 2e-5)
+    compare_particles(g, o, 2e-6, exact_order=False)
+
+
+def test_multichunk_tiles_and_sort_permutation():
+    """Tiles holding several chunks (> 1024 particles); many tile crossings per step; the
+    canonical order (stable sort by tile) must stay bit-exact over steps."""
+    n = (16, 16, 24)
+    g, o = pair(3, n, (0, 0, 1), (1, 1, 1), 0.5, 2, FP64)
+    parts = synth.uniform_plasma(n, 3, 9, 1.2, seed=15)  # 9 ppc -> 4608 per 8^3 tile
+    load_both(g, o, parts)
+    for s in range(6):
+        g.run_phases(pic.PIC_PHASE_PARTICLES)
+        o.particle_phase()
+        pg, po = g.get_particles(), o.get_particles()
+        assert np.array_equal(pg["id"], po["id"]), s
+        assert np.array_equal(pg["cell"], po["cell"]), s
+    assert g.diagnostics()["n_lost"] == o.diagnostics()["n_lost"] > 0
+
+
+# ------------------------------------------------------------------------ whole steps
+@pytest.mark.parametrize("ndim,order,passes,bcs", [(3, 2, 3, "abs"), (3, 1, 0, "per"), (2, 2, 1, "per"), (2, 1, 2, "abs")])
+def test_full_steps_fp64(ndim, order, passes, bcs):
+    c = dict(CASES_3D if ndim == 3 else CASES_2D)
+    bc = (0, 0, 0) if bcs == "per" else (1, 1, 1)
+    g, o = pair(ndim, c["n"], bc, c["dx"], c["dt"], order, FP64, passes=passes)
+    set_fields_both(g, o, synth.smooth_fields(c["n"], ndim, 0.05, seed=16))
+    load_both(g, o, synth.uniform_plasma(c["n"], ndim, 2, 0.3, seed=17))
+    g.step(8)
+    o.step(8)
+    compare_fields(g, o, COMPS + [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ], 1e-12)
+    compare_particles(g, o, 1e-12)
+
+
+def test_config1_2d3v_fp64_100_steps():
+    """2D3V 128x128 periodic, 4 ppc (65,536 electrons), sigma_u = 0.01, CIC, Vay, no
+    filter, dx = 1 skin depth (n0 = 1), dt = 0.5, 100 steps: all fields and particles."""
+    n = (128, 1, 128)
+    g, o = pair(2, n, (0, 0, 0), (1.0, 1.0, 1.0), 0.5, 1, FP64, tile=(16, 1, 16))
+    load_both(g, o, synth.uniform_plasma(n, 2, 4, 0.01, seed=1))
+    g.step(100)
+    o.step(100)
+    compare_fields(g, o, COMPS + [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ], 1e-12)
+    compare_particles(g, o, 1e-12)
+    dg, do = g.diagnostics(), o.diagnostics()
+    assert abs(dg["field_energy"] - do["field_energy"]) <= 1e-12 * do["field_energy"]
+    assert abs(dg["kinetic_energy"] - do["kinetic_energy"]) <= 1e-12 * do["kinetic_energy"]
+
+
+def test_config1_2d3v_fp32_100_steps():
+    n = (128, 1, 128)
+    g, o = pair(2, n, (0, 0, 0), (1.0, 1.0, 1.0), 0.5, 1, FP32, tile=(16, 1, 16))
+    load_both(g, o, synth.uniform_plasma(n, 2, 4, 0.01, seed=1))
+    g.step(100)
+    o.step(100)
+    compare_fields(g, o, COMPS + [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ], 1e-5)
+    compare_particles(g, o, 1e-5, exact_order=False)
+
+
+# ------------------------------------------------------------- loaders and getters
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("ndim", [3, 2])
+def test_lab_frame_load(ndim, prec):
+    gb = 13.0
+    n = (16, 12, 64) if ndim == 3 else (24, 1, 96)
+    dz = 2.0
+    dx = (3.0, 3.0, dz)
+    g, o = pair(ndim, n, (1, 1, 1), dx, 0.5 * dz, 2, prec, gamma=gb)
+    laser = (2.0, 1.0, 15.0, 10.0, 8.0)
+    plasma = (1.0 / 900 * (2 * np.pi) ** 2, 5.0, 2.0, 2, (0.0, 0.0, 0.0), 3)
+    beam = (500, 30.0, 1e-3, 2.0, 1.0, 4.0, 1e3, 7)
+    g.load_lab_frame(laser=laser, plasma=plasma, beam=beam)
+    o.load_lab_frame(gb, laser=laser, plasma=[*plasma[:4], *plasma[4], plasma[5]], beam=beam)
+    pg, po = g.get_particles(), o.get_particles()
+    assert np.array_equal(pg["id"], po["id"]) and np.array_equal(pg["cell"], po["cell"])
+    if prec == FP64:
+        for k in ("off", "u", "w"):
+            assert np.array_equal(pg[k], po[k]), k
+        tol = 1e-15
+    else:
+        for k in ("off", "u", "w"):
+            assert np.array_equal(pg[k], po[k].astype(np.float32).astype(np.float64)), k
+        tol = 6e-8
+    for c in (pic.PIC_EX, pic.PIC_BY):
+        assert rel(g.get_field(c), o.get_field(c)) <= tol
+
+
+def test_rho_dive_and_diagnostics_fp64():
+    n = (20, 16, 24)
+    g, o = pair(3, n, (0, 1, 0), (1.0, 0.9, 1.1), 0.45, 2, FP64)
+    set_fields_both(g, o, synth.smooth_fields(n, 3, 0.1, seed=18))
+    load_both(g, o, synth.random_particles(n, 3, 5000, 0.5, seed=19))
+    g.step(2)
+    o.step(2)
+    assert rel(g.get_field(pic.PIC_RHO), o.rho()) <= 1e-12
+    assert rel(g.get_field(pic.PIC_DIVE), o.div_e()) <= 1e-12
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("field_energy", "kinetic_energy", "total_charge"):
+        assert abs(dg[k] - do[k]) <= 1e-12 * abs(do[k]), k
+    assert dg["n_particles"] == do["n_particles"] and dg["step"] == do["step"] == 2
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_gauss_law_on_gpu(order):
+    """Esirkepov + Yee on the GPU keep div E - rho constant to round-off (FP64)."""
+    n = (24, 16, 16)
+    g = pic.Simulation(3, n, (0, 0, 0), (1, 1, 1), 0.5, order=order, precision=FP64)
+    parts = synth.uniform_plasma(n, 3, 2, 0.3, seed=20)
+    g.load_particles(parts["cell"], parts["off"], parts["u"], parts["w"], parts["id"])
+    r0 = g.get_field(pic.PIC_DIVE) - g.get_field(pic.PIC_RHO)
+    g.step(10)
+    r1 = g.get_field(pic.PIC_DIVE) - g.get_field(pic.PIC_RHO)
+    assert np.abs(r1 - r0).max() < 1e-11
+    assert g.diagnostics()["field_energy"] > 0
+
+
+def test_batch_matches_oracle_per_instance():
+    """Instances of different sizes and densities advanced in one launch per phase."""
+    sims, orcs = [], []
+    for i, (nx, nz, ppc) in enumerate([(32, 48, 2), (64, 32, 5), (48, 48, 1)]):
+        n = (nx, 1, nz)
+        g, o = pair(2, n, (0, 0, 1), (1.0, 1.0, 1.0), 0.5, 1 + i % 2, FP64, passes=i)
+        set_fields_both(g, o, synth.smooth_fields(n, 2, 0.05, seed=30 + i))
+        load_both(g, o, synth.uniform_plasma(n, 2, ppc, 0.2, seed=40 + i))
+        sims.append(g)
+        orcs.append(o)
+    # shape orders differ: one batch per order
+    b1 = pic.Batch([sims[0], sims[2]])
+    b2 = pic.Batch([sims[1]])
+    for _ in range(6):
+        b1.step(1)
+        b2.step(1)
+    for o in orcs:
+        o.step(6)
+    for g, o in zip(sims, orcs):
+        compare_fields(g, o, COMPS, 1e-12)
+        compare_particles(g, o, 1e-12)
+
+
+def test_errors_surface_as_status():
+    g = pic.Simulation(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.5)
+    with pytest.raises(pic.PicError) as e:
+        g.step(1)
+    assert e.value.status == pic.PIC_ERR_STATE
+    with pytest.raises(pic.PicError) as e:
+        g.load_particles(np.array([0], np.int32), np.array([[1.5, 0.0, 0.0]]), np.zeros((1, 3)), np.ones(1))
+    assert e.value.status == pic.PIC_ERR_ARG
+    with pytest.raises(pic.PicError) as e:
+        g.load_particles(np.array([0], np.int32), np.array([[0.5, 0.0, 0.0]]), np.array([[np.nan, 0, 0]]), np.ones(1))
+    assert e.value.status == pic.PIC_ERR_NAN
