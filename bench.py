@@ -268,7 +268,7 @@ def run_ours(args, rank, world):
         torch.cuda.empty_cache()
 
     # ---- end to end through the C ABI with host buffers
-    e2e = end_to_end(pic, w, args, torch)
+    e2e = None if args.skip_e2e else end_to_end(pic, w, args, torch)
 
     if rank != 0:
         return
@@ -341,6 +341,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -379,19 +379,13 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             // ---- Esirkepov deposit into the shared J tile
             {
                 constexpr int W = ORD + 2;
-                R S0x[W], S1x[W], S0y[W], S1y[W], S0z[W], S1z[W];
-                const int wsx = shape_window<ORD>(l[0], o[0], l1[0], o1[0], S0x, S1x) - I.jlo;
-                const int wsz = shape_window<ORD>(l[2], o[2], l1[2], o1[2], S0z, S1z) - I.jlo;
-                R DSx[W], DSz[W];
-#pragma unroll
-                for (int i = 0; i < W; ++i) { DSx[i] = S1x[i] - S0x[i]; DSz[i] = S1z[i] - S0z[i]; }
+                R S0x[W], DSx[W], S0y[W], DSy[W], S0z[W], DSz[W];
+                const int wsx = shape_window<ORD>(l[0], o[0], l1[0], o1[0], S0x, DSx) - I.jlo;
+                const int wsz = shape_window<ORD>(l[2], o[2], l1[2], o1[2], S0z, DSz) - I.jlo;
                 R *Jx = sJ, *Jy = sJ + jvol, *Jz = sJ + 2 * jvol;
                 const R qw = qdv * w;
                 if (ND == 3) {
-                    const int wsy = shape_window<ORD>(l[1], o[1], l1[1], o1[1], S0y, S1y) - jlo_y;
-                    R DSy[W];
-#pragma unroll
-                    for (int i = 0; i < W; ++i) DSy[i] = S1y[i] - S0y[i];
+                    const int wsy = shape_window<ORD>(l[1], o[1], l1[1], o1[1], S0y, DSy) - jlo_y;
                     const R fx = -qw * jfx, fy = -qw * jfy, fz = -qw * jfz;
                     const R third = R(1.0 / 3.0);
                     // Jx: running sum of DSx along x, times the transverse factor

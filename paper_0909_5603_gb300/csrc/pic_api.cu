@@ -477,13 +477,21 @@ static pic_status ensure_particle_capacity(pic_ctx *c, int64_t n)
     return PIC_OK;
 }
 
+// Converts to the storage precision in canonical order.  In-cell offsets (unit_interval)
+// stay below 1: an FP64 offset within half an FP32 ulp of 1 would round to 1.0f, so it
+// is stored as the largest float below 1 (same cell, error below 6e-8).
 template <typename R>
 static void fill_typed(std::vector<unsigned char> &buf, const std::vector<double> &src, const std::vector<int64_t> &perm,
-                       int stride, int comp)
+                       int stride, int comp, bool unit_interval)
 {
     buf.resize(perm.size() * sizeof(R));
     R *d = (R *)buf.data();
-    for (size_t i = 0; i < perm.size(); ++i) d[i] = (R)src[(size_t)perm[i] * stride + comp];
+    const R below_one = std::nextafter(R(1), R(0));
+    for (size_t i = 0; i < perm.size(); ++i) {
+        R v = (R)src[(size_t)perm[i] * stride + comp];
+        if (unit_interval && v >= R(1)) v = below_one;
+        d[i] = v;
+    }
 }
 
 static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, const double *off, const double *u,
@@ -527,9 +535,9 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
     }
     std::vector<double> voff(off, off + 3 * n), vu(u, u + 3 * n), vw(w, w + n);
     std::vector<unsigned char> buf;
-    auto put = [&](void *dst, const std::vector<double> &src, int stride, int comp) -> pic_status {
-        if (c->fp64) fill_typed<double>(buf, src, perm, stride, comp);
-        else fill_typed<float>(buf, src, perm, stride, comp);
+    auto put = [&](void *dst, const std::vector<double> &src, int stride, int comp, bool unit) -> pic_status {
+        if (c->fp64) fill_typed<double>(buf, src, perm, stride, comp, unit);
+        else fill_typed<float>(buf, src, perm, stride, comp, unit);
         if (n > 0) CUDA_OR_FAIL(c, cudaMemcpy(dst, buf.data(), buf.size(), cudaMemcpyHostToDevice));
         return PIC_OK;
     };
@@ -538,10 +546,10 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
         if (h.id[0]) CUDA_OR_FAIL(c, cudaMemcpy(h.id[0], hid.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     }
     for (int a = 0; a < 3; ++a) {
-        if (h.off[0][a] && (st = put(h.off[0][a], voff, 3, a)) != PIC_OK) return st;
-        if ((st = put(h.u[0][a], vu, 3, a)) != PIC_OK) return st;
+        if (h.off[0][a] && (st = put(h.off[0][a], voff, 3, a, true)) != PIC_OK) return st;
+        if ((st = put(h.u[0][a], vu, 3, a, false)) != PIC_OK) return st;
     }
-    if ((st = put(h.w[0], vw, 1, 0)) != PIC_OK) return st;
+    if ((st = put(h.w[0], vw, 1, 0, false)) != PIC_OK) return st;
     // initial layout 0
     const int R = h.R;
     std::vector<int> cbase(h.ntiles + 1, 0), tot((size_t)h.ntiles * kBuckets, 0), pop(h.ntiles, 0);

@@ -50,25 +50,49 @@ __device__ __forceinline__ int shape_stag(int l, R o, R w[ORD + 1])
     }
 }
 
-// Shape weights of the old and new positions on one common window of ORD + 2 nodes
-// starting at node `ws` (tile-relative), for the Esirkepov deposit.  The nearest nodes
-// of the two positions differ by at most one (moves below one cell per step).
+// Old shape S0 and its change DS = S1 - S0 on one common window of ORD + 2 nodes starting
+// at node `ws` (tile-relative), for the Esirkepov deposit.  The nearest nodes of the two
+// positions differ by at most one (moves below one cell per step).  When they coincide
+// (the common case) DS is formed from d = f1 - f0, the exact difference of the two
+// offsets from that node, as products with d -- e.g. for order 2 the centre weight gives
+// (3/4 - f1^2) - (3/4 - f0^2) = -d (f0 + f1) -- instead of subtracting two O(1) weights,
+// which in FP32 would lose the small displacement to cancellation.
 template <int ORD, typename R>
-__device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R S0[ORD + 2], R S1[ORD + 2])
+__device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R S0[ORD + 2], R DS[ORD + 2])
 {
     R w0[ORD + 1], w1[ORD + 1];
     const int b0 = shape_nodal<ORD>(l0, o0, w0);
     const int b1 = shape_nodal<ORD>(l1, o1, w1);
+    if (b0 == b1) {
+        // same nodes: offsets from the first node of the window
+        const R f0 = o0 - R(b0 - l0 + (ORD == 2 ? 1 : 0));
+        const R f1 = o1 - R(b1 - l1 + (ORD == 2 ? 1 : 0));
+        const R d = f1 - f0;
+#pragma unroll
+        for (int i = 0; i <= ORD; ++i) S0[i] = w0[i];
+        S0[ORD + 1] = R(0);
+        if (ORD == 1) {
+            DS[0] = -d;
+            DS[1] = d;
+        } else {
+            const R s = f0 + f1;
+            DS[0] = R(-0.5) * d * (R(1) - s);
+            DS[1] = -d * s;
+            DS[2] = R(0.5) * d * (R(1) + s);
+        }
+        DS[ORD + 1] = R(0);
+        return b0;
+    }
     const int ws = b0 < b1 ? b0 : b1;
     const int s0 = b0 - ws, s1 = b1 - ws;  // 0 or 1
 #pragma unroll
     for (int i = 0; i < ORD + 2; ++i) {
         const R a0 = (i < ORD + 1) ? w0[i < ORD + 1 ? i : 0] : R(0);
         const R a1 = (i >= 1) ? w0[i >= 1 ? i - 1 : 0] : R(0);
-        S0[i] = s0 == 0 ? a0 : a1;
         const R c0 = (i < ORD + 1) ? w1[i < ORD + 1 ? i : 0] : R(0);
         const R c1 = (i >= 1) ? w1[i >= 1 ? i - 1 : 0] : R(0);
-        S1[i] = s1 == 0 ? c0 : c1;
+        S0[i] = s0 == 0 ? a0 : a1;
+        DS[i] = (s1 == 0 ? c0 : c1) - S0[i];
     }
     return ws;
 }
