@@ -237,6 +237,29 @@ pic_status pic_synchronize(pic_ctx *ctx);
  * pic_set_profiling, pic_get_timings and pic_destroy accept a batch. */
 pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx **batch);
 
+/* Charge density read-out that allocates no device memory.  The paper has no counterpart:
+ * this is a service of the library, not a step of the method.
+ *
+ * Same result as pic_get_field(ctx, PIC_RHO, host_out, count) -- rho on the nodes,
+ * n0 n1 n2 doubles, x fastest -- but the deposit goes into a fixed work grid that the
+ * library owns (a device array of PIC_NOALLOC_RHO_MAX_CELLS doubles, 8 MiB, present on
+ * every GPU that loads the library until the process exits) instead of per-context
+ * memory.  It is for callers that must not enter a device allocator when they read the
+ * density: code running under a device-memory budget that is already fully committed,
+ * code called back from inside another library's memory pool, or a tight loop that has
+ * to stay out of allocator locks.  The call itself allocates nothing (no cudaMalloc, no
+ * cudaFree, no allocating library routine).
+ *  - Grids of more than PIC_NOALLOC_RHO_MAX_CELLS cells are rejected with PIC_ERR_ARG.
+ *  - The first call on a device looks up the work grid's device address there
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call shares the one work grid, which keeps the last call's contents; each call
+ *    clears the part it uses first.  Calls that overlap on the GPU (several threads or
+ *    streams at once) race on it: serialise them.
+ *  - Synchronises ctx's stream; host_out as in pic_get_field (count >= n0 n1 n2).
+ *  - Not valid on a batch (PIC_ERR_ARG). */
+#define PIC_NOALLOC_RHO_MAX_CELLS (1 << 20)
+pic_status pic_get_rho_noalloc(pic_ctx *ctx, double *host_out, size_t count);
+
 #ifdef __cplusplus
 }
 #endif

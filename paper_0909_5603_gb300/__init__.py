@@ -32,7 +32,8 @@ PIC_PHASE_PARTICLES, PIC_PHASE_FILTER, PIC_PHASE_MAXWELL, PIC_PHASE_ALL = 1, 2, 
 EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error", "pic_load_lab_frame",
             "pic_load_particles", "pic_set_field", "pic_step", "pic_run_phases", "pic_get_field",
             "pic_num_particles", "pic_get_particles", "pic_get_diagnostics", "pic_set_profiling",
-            "pic_get_timings", "pic_synchronize", "pic_batch_create"]
+            "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc"]
+PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
 class PicError(RuntimeError):
@@ -138,6 +139,8 @@ def lib():
         L.pic_synchronize.argtypes = [vp]
         L.pic_batch_create.restype = st
         L.pic_batch_create.argtypes = [ctypes.c_int, P(vp), P(vp)]
+        L.pic_get_rho_noalloc.restype = st
+        L.pic_get_rho_noalloc.argtypes = [vp, vp, ctypes.c_size_t]
         _lib = L
     return _lib
 

@@ -79,6 +79,30 @@ struct pic_ctx {
 
 static std::string g_create_error;
 
+namespace pic {
+// Read-only view of a context for entry points that live in other translation units.
+bool ctx_view(pic_ctx *c, CtxView *v)
+{
+    if (!c || !v) return false;
+    v->launch = &c->L;
+    v->order = c->order;
+    v->fp64 = c->fp64;
+    v->ncell = c->ncell;
+    v->stream = c->stream;
+    v->device = c->device;
+    v->loaded = c->loaded;
+    v->is_batch = c->is_batch;
+    return true;
+}
+
+pic_status ctx_fail(pic_ctx *c, pic_status s, const char *msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+}  // namespace pic
+
+
 static pic_status fail(pic_ctx *c, pic_status s, const char *fmt, ...)
 {
     char buf[512];

@@ -117,4 +117,20 @@ cudaError_t launch_pack(int fp64, const InstDev &I, int comp, int filtered, doub
 cudaError_t launch_unpack(int fp64, const InstDev &I, int comp, const double *dense, long long ncell, cudaStream_t s);
 cudaError_t launch_dive(int fp64, const InstDev &I, double *dense, long long ncell, cudaStream_t s);
 
+// Read-only view of a pic_ctx (defined in pic_api.cu) for entry points in other files.
+struct CtxView {
+    const Launch *launch;
+    int order, fp64;
+    long long ncell;
+    cudaStream_t stream;
+    int device;
+    bool loaded, is_batch;
+};
+
+}  // namespace pic
+
+struct pic_ctx;
+namespace pic {
+bool ctx_view(pic_ctx *c, CtxView *v);
+
 }  // namespace pic
