@@ -198,7 +198,7 @@ def run_ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     pic.build()
-    w = workload()
+    w = workload(args.nz)
     ncell = w["n"][0] * w["n"][1] * w["n"][2]
     sim = pic.Simulation(3, w["n"], (1, 1, 1), w["dx"], w["dt"], gamma_boost=GAMMA_B, order=2,
                          precision=pic.PIC_PREC_FP32, pusher=pic.PIC_PUSHER_VAY, filter_passes=3, tile=(8, 8, 8),
@@ -279,8 +279,8 @@ def run_ours(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "boosted LWFA stage (3D laser wakefield), gamma_boost 13, 128x128x1024 cells, "
-                                   "2 ppc = 33,554,432 particles, order-2 shape, 3-pass 1-2-1 filter, Vay, "
+            "config": {"workload": f"boosted LWFA stage (3D laser wakefield), gamma_boost 13, 128x128x{args.nz} cells, "
+                                   f"2 ppc = {n0:,} particles, order-2 shape, 3-pass 1-2-1 filter, Vay, "
                                    "FP32 + FP64 gamma solve",
                        "particles": n0, "cells": ncell, "l2": "inputs larger than L2 (1.07 GB of particles)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
@@ -342,6 +342,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--nz", type=int, default=N_GRID[2],
+                    help="cells along z (a shorter slab of the same workload, for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
