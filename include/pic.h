@@ -90,7 +90,7 @@ typedef struct {
                                only in the Vay gamma solve and the diagnostics sums;
                                PIC_PREC_FP64: everything FP64 */
     int pusher;             /* PIC_PUSHER_VAY (default) or PIC_PUSHER_BORIS */
-    int filter_passes;      /* binomial 1-2-1 passes on J per step (0 = none) */
+    int filter_passes;      /* binomial 1-2-1 passes on J per step, 0..8 (0 = none) */
     int tile[3];            /* particle tile in cells; 0 = default (8^3 in 3D, 16x1x16 in
                                2D); tile[0] must be a multiple of 4 */
     int threads;            /* threads per particle CTA: 128 or 256 (0 = 256) */

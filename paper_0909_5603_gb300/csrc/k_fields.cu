@@ -21,11 +21,11 @@ __device__ __forceinline__ bool cell_of(const Launch &L, long long g, CellPos &c
     if (g >= L.total_cells) return false;
     c.ii = find_instance_ll(L.cell_start, L.ninst, g);
     I = L.inst + c.ii;
-    long long r = g - L.cell_start[c.ii];
-    c.i = (int)(r % I->n[0]);
-    r /= I->n[0];
-    c.j = (int)(r % I->n[1]);
-    c.k = (int)(r / I->n[1]);
+    const int r = (int)(g - L.cell_start[c.ii]);  // < 2^31 cells per instance
+    const int rq = fast_div(r, I->div_n0);
+    c.i = r - rq * I->n[0];
+    c.k = fast_div(rq, I->div_n1);
+    c.j = rq - c.k * I->n[1];
     c.p = (c.i + I->gh[0]) + I->sy * (c.j + I->gh[1]) + I->sz * (c.k + I->gh[2]);
     return true;
 }
@@ -47,22 +47,16 @@ __device__ __forceinline__ void neighbour_offsets(const InstDev &I, const CellPo
     }
 }
 
-// Absorbing-layer factor prod_a (1 - s (d_a / L)^2), d_a = depth into the layer.
-__device__ __forceinline__ double damp_factor(const InstDev &I, const CellPos &c)
+// Absorbing-layer factor prod_a (1 - s (d_a / L)^2), d_a = depth into the layer, read
+// from the per-axis tables the host filled in FP64 (product taken x, y, z in order).
+template <typename R>
+__device__ __forceinline__ R damp_factor(const InstDev &I, const CellPos &c)
 {
-    const int L = I.absorb_cells;
-    if (L <= 0) return 1.0;
-    double f = 1.0;
+    R f = R(1);
     const int idx[3] = {c.i, c.j, c.k};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if ((I.ndim == 2 && a == 1) || I.bc[a] == 0) continue;
-        int d = 0;
-        if (L - idx[a] > d) d = L - idx[a];
-        if (idx[a] - (I.n[a] - 1 - L) > d) d = idx[a] - (I.n[a] - 1 - L);
-        const double r = (double)d / (double)L;
-        f *= 1.0 - I.absorb_strength * r * r;
-    }
+    for (int a = 0; a < 3; ++a)
+        if (I.damp[a]) f *= ((const R *)I.damp[a])[idx[a]];
     return f;
 }
 
@@ -93,7 +87,7 @@ __global__ void __launch_bounds__(256) k_bhalf(Launch L, int damp)
     R by = By[p] - h * (dEx_dz - dEz_dx);
     R bz = Bz[p] - h * (dEy_dx - dEx_dy);
     if (damp) {
-        const R f = R(damp_factor(I, c));
+        const R f = damp_factor<R>(I, c);
         bx *= f;
         by *= f;
         bz *= f;
@@ -116,7 +110,8 @@ __global__ void __launch_bounds__(256) k_efull(Launch L, int filtered)
     neighbour_offsets(I, c, up, dn);
     const R *Bx = (const R *)I.B[0], *By = (const R *)I.B[1], *Bz = (const R *)I.B[2];
     R *Ex = (R *)I.E[0], *Ey = (R *)I.E[1], *Ez = (R *)I.E[2];
-    const int nsweeps = I.filter_passes * (I.ndim == 3 ? 3 : 2);
+    // one filter sweep per active axis alternates J -> Jt -> J ...
+    const int nsweeps = I.filter_passes > 0 ? (I.ndim == 3 ? 3 : 2) : 0;
     void *const *Jsrc = (filtered && (nsweeps & 1)) ? I.Jt : I.J;
     const R *Jx = (const R *)Jsrc[0], *Jy = (const R *)Jsrc[1], *Jz = (const R *)Jsrc[2];
     const R dt = R(I.dt);
@@ -129,37 +124,112 @@ __global__ void __launch_bounds__(256) k_efull(Launch L, int filtered)
         dBz_dy = (bz - Bz[p + dn[1]]) * iy;
         dBx_dy = (bx - Bx[p + dn[1]]) * iy;
     }
-    const R f = R(damp_factor(I, c));
+    const R f = damp_factor<R>(I, c);
     Ex[p] = f * (Ex[p] + dt * ((dBz_dy - dBy_dz) - Jx[p]));
     Ey[p] = f * (Ey[p] + dt * ((dBx_dz - dBz_dx) - Jy[p]));
     Ez[p] = f * (Ez[p] + dt * ((dBy_dx - dBx_dy) - Jz[p]));
 }
 
-// One binomial sweep J <- J(i-1)/4 + J(i)/2 + J(i+1)/4 along one axis for the three
-// components; sweep s of an instance reads J (s even) or Jt (s odd) and writes the
-// other.  Sweeps cycle x, (y,) z within each pass.  Instances with fewer sweeps skip.
-template <typename R>
-__global__ void __launch_bounds__(256) k_filter(Launch L, int s)
+// Binomial filter along one axis, all passes at once.  The x, y and z operators (each
+// with its boundary: periodic wrap, or zero outside an absorbing box after every pass)
+// act on different axes and commute, so `passes` rounds of (x, y, z) equal x^passes,
+// y^passes, z^passes.  One CTA takes a pencil of kPencil cells along the axis (times 32
+// x-columns for the y and z axes), loads it with `passes` halo cells per side into shared
+// memory, applies the passes there (J <- J(i-1)/4 + J(i)/2 + J(i+1)/4, re-zeroing cells
+// outside an absorbing box after each pass) and writes the pencil back: one read and one
+// write per cell and axis instead of one per pass.  Reads src, writes dst (J / Jt).
+constexpr int kPencil = 64;
+constexpr int kMaxPasses = 8;
+
+__device__ __forceinline__ bool filter_active_axis(const InstDev &I, int axis)
 {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    CellPos c;
-    const InstDev *Ip;
-    if (!cell_of(L, g, c, Ip)) return;
-    const InstDev &I = *Ip;
-    const int naxes = I.ndim == 3 ? 3 : 2;
-    if (s >= I.filter_passes * naxes) return;
-    const int ai = s % naxes;
-    const int axis = I.ndim == 3 ? ai : (ai == 0 ? 0 : 2);
-    long long up[3], dn[3];
-    neighbour_offsets(I, c, up, dn);
-    void *const *src = (s & 1) ? I.Jt : I.J;
-    void *const *dst = (s & 1) ? I.J : I.Jt;
-    const long long p = c.p;
-#pragma unroll
+    return I.filter_passes > 0 && !(I.ndim == 2 && axis == 1);
+}
+
+// A pencil is 32 lines parallel to `axis` times kPencil cells along it.  Lines: for the
+// x axis, 32 consecutive (y, z) rows; for y and z, 32 consecutive x columns at one z (y).
+template <typename R>
+__global__ void __launch_bounds__(256) k_filter_axis(Launch L, int axis, const long long *pencil_start, int src_is_jt)
+{
+    __shared__ R buf[2][kPencil + 2 * kMaxPasses][33];
+    const long long g = blockIdx.x;
+    if (g >= pencil_start[L.ninst]) return;
+    const int ii = find_instance_ll(pencil_start, L.ninst, g);
+    const InstDev &I = L.inst[ii];
+    if (!filter_active_axis(I, axis)) return;
+    const int P = min(I.filter_passes, kMaxPasses);
+    const int n = I.n[axis];
+    const bool per = I.bc[axis] == 0;
+    const int nseg = (n + kPencil - 1) / kPencil;
+    long long r = g - pencil_start[ii];
+    const int q0 = (int)(r % nseg) * kPencil;  // first cell of the segment along the axis
+    r /= nseg;
+    const long long st[3] = {1, I.sy, I.sz};
+    const long long sa = st[axis];
+    // line c -> padded offset of its cell 0 along the axis, or -1 when the line is absent
+    long long line_off[1];
+    (void)line_off;
+    auto line = [&](int c) -> long long {
+        if (axis == 0) {
+            const long long row = r * 32 + c;
+            if (row >= (long long)I.n[1] * I.n[2]) return -1;
+            const int y = (int)(row % I.n[1]), z = (int)(row / I.n[1]);
+            return I.gh[0] + st[1] * (y + I.gh[1]) + st[2] * (z + I.gh[2]);
+        }
+        const int ncol = (I.n[0] + 31) / 32;
+        const int x = (int)(r % ncol) * 32 + c;
+        const int other = (int)(r / ncol);  // z for the y axis, y for the z axis
+        if (x >= I.n[0]) return -1;
+        if (axis == 1) return (x + I.gh[0]) + st[1] * I.gh[1] + st[2] * (other + I.gh[2]);
+        return (x + I.gh[0]) + st[1] * (other + I.gh[1]) + st[2] * I.gh[2];
+    };
+    void *const *src = src_is_jt ? I.Jt : I.J;
+    void *const *dst = src_is_jt ? I.J : I.Jt;
+    const int len = kPencil + 2 * P;
+    const int tid = threadIdx.x;
     for (int comp = 0; comp < 3; ++comp) {
         const R *a = (const R *)src[comp];
         R *b = (R *)dst[comp];
-        b[p] = R(0.25) * a[p + dn[axis]] + R(0.5) * a[p] + R(0.25) * a[p + up[axis]];
+        // load buf[s][c] = line c at axis position q0 + s - P (wrapped, or 0 outside)
+        for (int e = tid; e < len * 32; e += blockDim.x) {
+            int s_, c_;
+            if (axis == 0) { c_ = e / len; s_ = e - c_ * len; } else { s_ = e >> 5; c_ = e & 31; }
+            const long long lo = line(c_);
+            int q = q0 + s_ - P;
+            bool ok = lo >= 0;
+            if (q < 0 || q >= n) {
+                // a ragged last pencil can reach more than one period past the end
+                if (per) q = ((q % n) + n) % n;
+                else ok = false;
+            }
+            buf[0][s_][c_] = ok ? a[lo + (long long)q * sa] : R(0);
+        }
+        __syncthreads();
+        int cur = 0;
+        for (int pass = 0; pass < P; ++pass) {
+            for (int e = tid; e < len * 32; e += blockDim.x) {
+                int s_, c_;
+                if (axis == 0) { c_ = e / len; s_ = e - c_ * len; } else { s_ = e >> 5; c_ = e & 31; }
+                R v = R(0);
+                if (s_ >= 1 && s_ < len - 1) {
+                    v = R(0.25) * buf[cur][s_ - 1][c_] + R(0.5) * buf[cur][s_][c_] + R(0.25) * buf[cur][s_ + 1][c_];
+                    const int q = q0 + s_ - P;
+                    if (!per && (q < 0 || q >= n)) v = R(0);
+                }
+                buf[cur ^ 1][s_][c_] = v;
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+        for (int e = tid; e < kPencil * 32; e += blockDim.x) {
+            int s_, c_;
+            if (axis == 0) { c_ = e / kPencil; s_ = e - c_ * kPencil; } else { s_ = e >> 5; c_ = e & 31; }
+            const int q = q0 + s_;
+            const long long lo = line(c_);
+            if (q >= n || lo < 0) continue;
+            b[lo + (long long)q * sa] = buf[cur][s_ + P][c_];
+        }
+        __syncthreads();
     }
 }
 
@@ -237,7 +307,7 @@ __global__ void k_pack(InstDev I, int comp, int filtered, double *dense, long lo
     if (comp < 3) src = I.E[comp];
     else if (comp < 6) src = I.B[comp - 3];
     else {
-        const int nsweeps = I.filter_passes * (I.ndim == 3 ? 3 : 2);
+        const int nsweeps = I.filter_passes > 0 ? (I.ndim == 3 ? 3 : 2) : 0;
         src = (filtered && (nsweeps & 1)) ? I.Jt[comp - 6] : I.J[comp - 6];
     }
     dense[g] = (double)((const R *)src)[p];
@@ -281,13 +351,22 @@ __global__ void k_dive(InstDev I, double *dense, long long ncell)
 // ------------------------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t launch_filter(int fp64, const Launch &L, int max_sweeps, cudaStream_t s)
+cudaError_t launch_filter(int fp64, const Launch &L, const long long *const pencil_start[3],
+                          const long long pencil_total[3], int ndim, cudaStream_t s)
 {
-    for (int sw = 0; sw < max_sweeps; ++sw) {
-        if (fp64)
-            k_filter<double><<<blocks_for(L.total_cells, 256), 256, 0, s>>>(L, sw);
-        else
-            k_filter<float><<<blocks_for(L.total_cells, 256), 256, 0, s>>>(L, sw);
+    // axes in order x, (y,) z; sweep k reads J when k is even, Jt when odd
+    int k = 0;
+    for (int axis = 0; axis < 3; ++axis) {
+        if (ndim == 2 && axis == 1) continue;
+        if (pencil_total[axis] > 0) {
+            const unsigned nb = (unsigned)pencil_total[axis];
+            const int threads = 256;
+            if (fp64)
+                k_filter_axis<double><<<nb, threads, 0, s>>>(L, axis, pencil_start[axis], k & 1);
+            else
+                k_filter_axis<float><<<nb, threads, 0, s>>>(L, axis, pencil_start[axis], k & 1);
+        }
+        ++k;
     }
     return cudaGetLastError();
 }

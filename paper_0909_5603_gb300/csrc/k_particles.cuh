@@ -17,9 +17,9 @@
 namespace pic {
 
 constexpr int kNT = 256;          // threads per particle CTA
-constexpr int kPPT = 4;           // particles per thread per chunk
 constexpr int kNW = kNT / 32;
-constexpr int kChunk = kNT * kPPT;  // particles per chunk
+constexpr int kChunk = kNT;       // particles per chunk: one per thread
+constexpr int kFlushChunks = 2047 / kChunk;  // fixed-point J flush interval (see FixedAcc)
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 
 // -------------------------------------------------------------------------------------
@@ -132,8 +132,12 @@ static __device__ void build_sources(const InstDev &I, int lay, int tx, int ty, 
 // Buffer position of slot p (0 <= p < S.count) of the destination tile.
 __device__ __forceinline__ int slot_position(const InstDev &I, int lay, const SrcTable &S, int p)
 {
-    int s = 0;
-    while (s + 1 < S.n && S.pre[s + 1] <= p) ++s;
+    // the last source whose prefix is <= p (empty sources share their successor's prefix)
+    int s = 0, top = S.n - 1;
+    while (s < top) {
+        const int mid = (s + top + 1) >> 1;
+        if (S.pre[mid] <= p) s = mid; else top = mid - 1;
+    }
     const int j = p - S.pre[s];
     if (S.pos0[s] >= 0) return S.pos0[s] + j;
     // several chunks: the last chunk whose earlier-chunks count of this bucket is <= j
@@ -181,25 +185,66 @@ __device__ __forceinline__ R interp(const R *f, int bx, int bxy, int i0, int j0,
     return acc;
 }
 
-struct PState {
-    int cell;
-    int id;
-    int bucket;  // 0..26 direction, 27 dead, 28 no particle
-};
+// Global index of J tile element e (component, local x, y, z) after wrapping (periodic)
+// or clipping (absorbing, returns -1) its guard cells.
+__device__ __forceinline__ long long j_global_index(const InstDev &I, const int T0[3], int ND, int e, int jvol, int &comp)
+{
+    comp = e / jvol;
+    const int rem = e - comp * jvol;
+    const int lx = rem % I.jdim[0];
+    const int ly = (rem / I.jdim[0]) % I.jdim[1];
+    const int lz = rem / (I.jdim[0] * I.jdim[1]);
+    int gidx[3] = {T0[0] + I.jlo + lx, ND == 3 ? T0[1] + I.jlo + ly : 0, T0[2] + I.jlo + lz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (ND == 2 && a == 1) continue;
+        if (gidx[a] < 0 || gidx[a] >= I.n[a]) {
+            if (I.bc[a] != 0) return -1;
+            gidx[a] += gidx[a] < 0 ? I.n[a] : -I.n[a];
+        }
+    }
+    return (gidx[0] + I.gh[0]) + I.sy * (gidx[1] + I.gh[1]) + I.sz * (gidx[2] + I.gh[2]);
+}
 
-template <typename R>
-struct Kin {
-    R o[3], u[3], w;
-};
+// FP32 tile: value = (H + L 2^-16) / scale, added to global J; the tile is cleared.
+__device__ __forceinline__ void flush_j_fixed(const InstDev &I, const int T0[3], int ND, int *H, int *Lo, int jvol,
+                                              float inv_scale, int tid, int nt)
+{
+    for (int e = tid; e < 3 * jvol; e += nt) {
+        const int hv = H[e], lv = Lo[e];
+        if ((hv | lv) == 0) continue;
+        H[e] = 0;
+        Lo[e] = 0;
+        int comp;
+        const long long gi = j_global_index(I, T0, ND, e, jvol, comp);
+        if (gi < 0) continue;
+        const float v = ((float)hv + (float)lv * (1.0f / 65536.0f)) * inv_scale;
+        atomicAdd((float *)I.J[comp] + gi, v);
+    }
+}
+
+__device__ __forceinline__ void flush_j_double(const InstDev &I, const int T0[3], int ND, const double *J, int jvol,
+                                               int tid, int nt)
+{
+    for (int e = tid; e < 3 * jvol; e += nt) {
+        const double v = J[e];
+        if (v == 0.0) continue;
+        int comp;
+        const long long gi = j_global_index(I, T0, ND, e, jvol, comp);
+        if (gi < 0) continue;
+        atomicAdd((double *)I.J[comp] + gi, v);
+    }
+}
 
 template <int ND, int ORD, typename R, int PUSHER>
 __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launch L)
 {
+    constexpr bool kFixed = sizeof(R) == 4;  // FP32: fixed-point integer J accumulation
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ SrcTable S;
     __shared__ uint64_t bar;
-    __shared__ int s_base[kBuckets], s_run[kBuckets], s_round[kBuckets];
-    __shared__ int s_cnt[kPPT][kNW][kBuckets];
+    __shared__ int s_base[kBuckets], s_run[kBuckets];
+    __shared__ int s_cnt[kNW][kBuckets];
 
     const int g = blockIdx.x;
     const int ii = find_instance(L.tile_start, L.ninst, g);
@@ -228,14 +273,18 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     }
 
     // shared-memory carve-up (base rounded up to 128 bytes for TMA): 6 field boxes, then
-    // 3 J components
+    // the J tile: 3 components of jvol cells, as FP64 values (FP64 mode) or as two 32-bit
+    // integer arrays H and L of 3 jvol each (FP32 mode) -- 8 bytes per cell either way
     const int boxn = I.box[0] * I.box[1] * I.box[2];
     const int box_bytes = boxn * (int)sizeof(R);
     const int box_stride = (box_bytes + 127) & ~127;
     unsigned char *sbase = smem + ((128u - (smem_addr(smem) & 127u)) & 127u);
     R *sF = reinterpret_cast<R *>(sbase);
-    R *sJ = reinterpret_cast<R *>(sbase + 6 * box_stride);
+    unsigned char *sJraw = sbase + 6 * box_stride;
     const int jvol = I.jdim[0] * I.jdim[1] * I.jdim[2];
+    int *sJH = reinterpret_cast<int *>(sJraw);
+    int *sJL = sJH + 3 * jvol;
+    double *sJD = reinterpret_cast<double *>(sJraw);
 
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -248,7 +297,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             tma_load_3d(sbase + c * box_stride, I.tmap + c, x, y, z, &bar);
         build_sources(I, in, tx, ty, tz, S);
     }
-    for (int e = tid; e < 3 * jvol; e += kNT) sJ[e] = R(0);
+    for (int e = tid; e < 6 * jvol; e += kNT) sJH[e] = 0;  // zeroes the FP64 tile too
     if (tid < kBuckets) s_run[tid] = 0;
     __syncthreads();
     const bool ok = mbar_wait_bounded(&bar, 0, kWaitCycles);
@@ -261,11 +310,11 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     }
     if (tid == 0 && S.count != count) atomicOr(I.err, kErrInternal);
 
-    // per-instance constants in the working precision
-    const R dt = R(I.dt);
+    // per-instance constants in the working precision; in FP32 mode the current factors
+    // carry the fixed-point scale (see FixedAcc)
     const R h = R(0.5 * I.q / I.m * I.dt);
     const double dV = I.dx[0] * I.dx[1] * I.dx[2];
-    const R qdv = R(I.q / dV);
+    const R qdv = R(I.q / dV) * (kFixed ? R(I.jscale) : R(1));
     const R jfx = R(I.dx[0] / I.dt), jfy = R(I.dx[1] / I.dt), jfz = R(I.dx[2] / I.dt);
     const R dtdx[3] = {R(I.dt / I.dx[0]), R(I.dt / I.dx[1]), R(I.dt / I.dx[2])};
     const int bx = I.box[0], bxy = I.box[0] * I.box[1];
@@ -280,65 +329,71 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     const R *u_in[3] = {(const R *)I.u[in][0], (const R *)I.u[in][1], (const R *)I.u[in][2]};
     const R *w_in = (const R *)I.w[in];
     const int *id_in = I.id[in];
+    int *cell_out = I.cell[out];
+    R *off_out[3] = {(R *)I.off[out][0], (R *)I.off[out][1], (R *)I.off[out][2]};
+    R *u_out[3] = {(R *)I.u[out][0], (R *)I.u[out][1], (R *)I.u[out][2]};
+    R *w_out = (R *)I.w[out];
+    int *id_out = I.id[out];
 
     for (int base = 0, r = 0; base < count; base += kChunk, ++r) {
-        for (int e = tid; e < kPPT * kNW * kBuckets; e += kNT) (&s_cnt[0][0][0])[e] = 0;
-        __syncthreads();
-        PState st[kPPT];
-        Kin<R> kn[kPPT];
-#pragma unroll
-        for (int k = 0; k < kPPT; ++k) {
-            const int slot = base + k * kNT + tid;
-            st[k].bucket = 28;
-            if (slot >= count) continue;
-            const int pos = slot_position(I, in, S, slot);
-            if (pos < 0 || pos >= I.cap) {
-                atomicOr(I.err, kErrInternal);
-                continue;
-            }
+        for (int e = tid; e < kNW * kBuckets; e += kNT) (&s_cnt[0][0])[e] = 0;
+        int bucket = 28;  // 0..26 direction, 27 dead, 28 no particle
+        int cell_new = 0, pid = 0;
+        R o1[3] = {R(0), R(0), R(0)}, u[3] = {R(0), R(0), R(0)}, w = R(0);
+        const int slot = base + tid;
+        const int pos = slot < count ? slot_position(I, in, S, slot) : -1;
+        if (slot < count && (pos < 0 || pos >= I.cap)) atomicOr(I.err, kErrInternal);
+        int l[3] = {0, 0, 0}, cc[3] = {0, 0, 0};
+        bool have = false;
+        if (pos >= 0 && pos < I.cap) {
             const int c = __ldg(cell_in + pos);
-            const int cx = c % I.n[0];
-            const int cyz = c / I.n[0];
-            const int cy = cyz % I.n[1];
-            const int cz = cyz / I.n[1];
-            int l[3] = {cx - T0[0], cy - T0[1], cz - T0[2]};
-            if (l[0] < 0 || l[0] >= tsx || l[1] < 0 || l[1] >= tsy || l[2] < 0 || l[2] >= tsz) {
-                atomicOr(I.err, kErrInternal);
-                continue;
-            }
-            R o[3], u[3];
+            const int cyz = fast_div(c, I.div_n0);
+            cc[0] = c - cyz * I.n[0];
+            cc[2] = fast_div(cyz, I.div_n1);
+            cc[1] = cyz - cc[2] * I.n[1];
+            l[0] = cc[0] - T0[0];
+            l[1] = cc[1] - T0[1];
+            l[2] = cc[2] - T0[2];
+            have = l[0] >= 0 && l[0] < tsx && l[1] >= 0 && l[1] < tsy && l[2] >= 0 && l[2] < tsz;
+            if (!have) atomicOr(I.err, kErrInternal);
+        }
+        if (have) {
+            R o[3];
             o[0] = __ldg(off_in[0] + pos);
             o[1] = ND == 3 ? __ldg(off_in[1] + pos) : R(0);
             o[2] = __ldg(off_in[2] + pos);
             u[0] = __ldg(u_in[0] + pos);
             u[1] = __ldg(u_in[1] + pos);
             u[2] = __ldg(u_in[2] + pos);
-            const R w = __ldg(w_in + pos);
-            st[k].id = id_in ? __ldg(id_in + pos) : 0;
+            w = __ldg(w_in + pos);
+            pid = id_in ? __ldg(id_in + pos) : 0;
 
             // ---- gather (Yee positions: E_a staggered along a, B_a along the other two)
-            R wn[3][ORD + 1], wsg[3][ORD + 1];
-            int bn[3], bsg[3];
-            bn[0] = shape_nodal<ORD>(l[0], o[0], wn[0]) - I.box_lo[0];
-            bsg[0] = shape_stag<ORD>(l[0], o[0], wsg[0]) - I.box_lo[0];
-            if (ND == 3) {
-                bn[1] = shape_nodal<ORD>(l[1], o[1], wn[1]) - I.box_lo[1];
-                bsg[1] = shape_stag<ORD>(l[1], o[1], wsg[1]) - I.box_lo[1];
-            } else {
-                bn[1] = bsg[1] = 0;
-#pragma unroll
-                for (int q = 0; q <= ORD; ++q) wn[1][q] = wsg[1][q] = R(0);
-                wn[1][0] = wsg[1][0] = R(1);
-            }
-            bn[2] = shape_nodal<ORD>(l[2], o[2], wn[2]) - I.box_lo[2];
-            bsg[2] = shape_stag<ORD>(l[2], o[2], wsg[2]) - I.box_lo[2];
             R E[3], B[3];
-            E[0] = interp<ND, ORD, R>(sF + 0 * (box_stride / sizeof(R)), bx, bxy, bsg[0], bn[1], bn[2], wsg[0], wn[1], wn[2]);
-            E[1] = interp<ND, ORD, R>(sF + 1 * (box_stride / sizeof(R)), bx, bxy, bn[0], bsg[1], bn[2], wn[0], wsg[1], wn[2]);
-            E[2] = interp<ND, ORD, R>(sF + 2 * (box_stride / sizeof(R)), bx, bxy, bn[0], bn[1], bsg[2], wn[0], wn[1], wsg[2]);
-            B[0] = interp<ND, ORD, R>(sF + 3 * (box_stride / sizeof(R)), bx, bxy, bn[0], bsg[1], bsg[2], wn[0], wsg[1], wsg[2]);
-            B[1] = interp<ND, ORD, R>(sF + 4 * (box_stride / sizeof(R)), bx, bxy, bsg[0], bn[1], bsg[2], wsg[0], wn[1], wsg[2]);
-            B[2] = interp<ND, ORD, R>(sF + 5 * (box_stride / sizeof(R)), bx, bxy, bsg[0], bsg[1], bn[2], wsg[0], wsg[1], wn[2]);
+            {
+                R wn[3][ORD + 1], wsg[3][ORD + 1];
+                int bn[3], bsg[3];
+                bn[0] = shape_nodal<ORD>(l[0], o[0], wn[0]) - I.box_lo[0];
+                bsg[0] = shape_stag<ORD>(l[0], o[0], wsg[0]) - I.box_lo[0];
+                if (ND == 3) {
+                    bn[1] = shape_nodal<ORD>(l[1], o[1], wn[1]) - I.box_lo[1];
+                    bsg[1] = shape_stag<ORD>(l[1], o[1], wsg[1]) - I.box_lo[1];
+                } else {
+                    bn[1] = bsg[1] = 0;
+#pragma unroll
+                    for (int q = 0; q <= ORD; ++q) wn[1][q] = wsg[1][q] = R(0);
+                    wn[1][0] = wsg[1][0] = R(1);
+                }
+                bn[2] = shape_nodal<ORD>(l[2], o[2], wn[2]) - I.box_lo[2];
+                bsg[2] = shape_stag<ORD>(l[2], o[2], wsg[2]) - I.box_lo[2];
+                const int bs = box_stride / (int)sizeof(R);
+                E[0] = interp<ND, ORD, R>(sF + 0 * bs, bx, bxy, bsg[0], bn[1], bn[2], wsg[0], wn[1], wn[2]);
+                E[1] = interp<ND, ORD, R>(sF + 1 * bs, bx, bxy, bn[0], bsg[1], bn[2], wn[0], wsg[1], wn[2]);
+                E[2] = interp<ND, ORD, R>(sF + 2 * bs, bx, bxy, bn[0], bn[1], bsg[2], wn[0], wn[1], wsg[2]);
+                B[0] = interp<ND, ORD, R>(sF + 3 * bs, bx, bxy, bn[0], bsg[1], bsg[2], wn[0], wsg[1], wsg[2]);
+                B[1] = interp<ND, ORD, R>(sF + 4 * bs, bx, bxy, bsg[0], bn[1], bsg[2], wsg[0], wn[1], wsg[2]);
+                B[2] = interp<ND, ORD, R>(sF + 5 * bs, bx, bxy, bsg[0], bsg[1], bn[2], wsg[0], wsg[1], wn[2]);
+            }
 
             // ---- push
             if (PUSHER == 0)
@@ -348,7 +403,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
 
             // ---- move
             bool bad = false;
-            R o1[3] = {o[0], o[1], o[2]};
+            o1[0] = o[0]; o1[1] = o[1]; o1[2] = o[2];
             int kstep[3] = {0, 0, 0};
             R vy;
             if (sizeof(R) == 4) {
@@ -374,105 +429,22 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
                 o1[0] = o[0]; o1[1] = o[1]; o1[2] = o[2];
                 kstep[0] = kstep[1] = kstep[2] = 0;
             }
-            const int l1[3] = {l[0] + kstep[0], l[1] + kstep[1], l[2] + kstep[2]};
 
             // ---- Esirkepov deposit into the shared J tile
             {
-                constexpr int W = ORD + 2;
-                R S0x[W], DSx[W], S0y[W], DSy[W], S0z[W], DSz[W];
-                const int wsx = shape_window<ORD>(l[0], o[0], l1[0], o1[0], S0x, DSx) - I.jlo;
-                const int wsz = shape_window<ORD>(l[2], o[2], l1[2], o1[2], S0z, DSz) - I.jlo;
-                R *Jx = sJ, *Jy = sJ + jvol, *Jz = sJ + 2 * jvol;
+                const int l1[3] = {l[0] + kstep[0], l[1] + kstep[1], l[2] + kstep[2]};
                 const R qw = qdv * w;
-                if (ND == 3) {
-                    const int wsy = shape_window<ORD>(l[1], o[1], l1[1], o1[1], S0y, DSy) - jlo_y;
-                    const R fx = -qw * jfx, fy = -qw * jfy, fz = -qw * jfz;
-                    const R third = R(1.0 / 3.0);
-                    // Jx: running sum of DSx along x, times the transverse factor
-#pragma unroll
-                    for (int k = 0; k < W; ++k)
-#pragma unroll
-                        for (int j = 0; j < W; ++j) {
-                            const R Y = S0y[j] * S0z[k] + R(0.5) * (DSy[j] * S0z[k] + S0y[j] * DSz[k]) + third * DSy[j] * DSz[k];
-                            R acc = R(0);
-                            R *row = Jx + wsx + jd0 * (wsy + j) + jd01 * (wsz + k);
-#pragma unroll
-                            for (int i = 0; i < W - 1; ++i) {
-                                acc += DSx[i];
-                                const R v = fx * acc * Y;
-                                if (v != R(0)) atomicAdd(row + i, v);
-                            }
-                        }
-#pragma unroll
-                    for (int k = 0; k < W; ++k)
-#pragma unroll
-                        for (int i = 0; i < W; ++i) {
-                            const R X = S0x[i] * S0z[k] + R(0.5) * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) + third * DSx[i] * DSz[k];
-                            R acc = R(0);
-                            R *col = Jy + (wsx + i) + jd0 * wsy + jd01 * (wsz + k);
-#pragma unroll
-                            for (int j = 0; j < W - 1; ++j) {
-                                acc += DSy[j];
-                                const R v = fy * acc * X;
-                                if (v != R(0)) atomicAdd(col + jd0 * j, v);
-                            }
-                        }
-#pragma unroll
-                    for (int j = 0; j < W; ++j)
-#pragma unroll
-                        for (int i = 0; i < W; ++i) {
-                            const R X = S0x[i] * S0y[j] + R(0.5) * (DSx[i] * S0y[j] + S0x[i] * DSy[j]) + third * DSx[i] * DSy[j];
-                            R acc = R(0);
-                            R *col = Jz + (wsx + i) + jd0 * (wsy + j) + jd01 * wsz;
-#pragma unroll
-                            for (int k = 0; k < W - 1; ++k) {
-                                acc += DSz[k];
-                                const R v = fz * acc * X;
-                                if (v != R(0)) atomicAdd(col + jd01 * k, v);
-                            }
-                        }
-                } else {
-                    // 2D3V in the x-z plane (y invariant): in-plane currents by running sums,
-                    // the out-of-plane Jy from the averaged shape.
-                    const R fx = -qw * jfx, fz = -qw * jfz, fyo = qw * vy;
-                    const R third = R(1.0 / 3.0);
-#pragma unroll
-                    for (int k = 0; k < W; ++k) {
-                        const R Y = S0z[k] + R(0.5) * DSz[k];
-                        R acc = R(0);
-                        R *row = Jx + wsx + jd01 * (wsz + k);
-#pragma unroll
-                        for (int i = 0; i < W - 1; ++i) {
-                            acc += DSx[i];
-                            const R v = fx * acc * Y;
-                            if (v != R(0)) atomicAdd(row + i, v);
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < W; ++i) {
-                        const R X = S0x[i] + R(0.5) * DSx[i];
-                        R acc = R(0);
-                        R *col = Jz + (wsx + i) + jd01 * wsz;
-#pragma unroll
-                        for (int k = 0; k < W - 1; ++k) {
-                            acc += DSz[k];
-                            const R v = fz * acc * X;
-                            if (v != R(0)) atomicAdd(col + jd01 * k, v);
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < W; ++k)
-#pragma unroll
-                        for (int i = 0; i < W; ++i) {
-                            const R v = fyo * (S0x[i] * S0z[k] + R(0.5) * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) +
-                                               third * DSx[i] * DSz[k]);
-                            if (v != R(0)) atomicAdd(Jy + (wsx + i) + jd01 * (wsz + k), v);
-                        }
-                }
+                const R fx = -qw * jfx, fy = ND == 3 ? -qw * jfy : qw * vy, fz = -qw * jfz;
+                if (kFixed)
+                    deposit_esirkepov<ND, ORD, R>(l, o, l1, o1, fx, fy, fz, I.jlo, jlo_y, jd0, jd01, jvol,
+                                                  FixedAcc{sJH, sJL});
+                else
+                    deposit_esirkepov<ND, ORD, R>(l, o, l1, o1, fx, fy, fz, I.jlo, jlo_y, jd0, jd01, jvol,
+                                                  DoubleAcc{sJD});
             }
 
             // ---- new cell, destination tile, bucket
-            int cn[3] = {cx + kstep[0], cy + kstep[1], cz + kstep[2]};
+            int cn[3] = {cc[0] + kstep[0], cc[1] + kstep[1], cc[2] + kstep[2]};
             bool dead = false;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -485,37 +457,30 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
                 }
             }
             if (dead) {
-                st[k].bucket = kDead;
+                bucket = kDead;
             } else {
                 const int ddx = axis_dir(tx, cn[0] / I.ts[0], I.nt[0], I.bc[0]);
                 const int ddy = ND == 3 ? axis_dir(ty, cn[1] / I.ts[1], I.nt[1], I.bc[1]) : 0;
                 const int ddz = axis_dir(tz, cn[2] / I.ts[2], I.nt[2], I.bc[2]);
-                st[k].bucket = (ddz + 1) * 9 + (ddy + 1) * 3 + (ddx + 1);
+                bucket = (ddz + 1) * 9 + (ddy + 1) * 3 + (ddx + 1);
             }
-            st[k].cell = cn[0] + I.n[0] * (cn[1] + I.n[1] * cn[2]);
-            kn[k].o[0] = o1[0]; kn[k].o[1] = o1[1]; kn[k].o[2] = o1[2];
-            kn[k].u[0] = u[0]; kn[k].u[1] = u[1]; kn[k].u[2] = u[2];
-            kn[k].w = w;
+            cell_new = cn[0] + I.n[0] * (cn[1] + I.n[1] * cn[2]);
         }
 
-        // ---- stable ranking of the chunk by bucket: order (k, warp, lane)
-        int rank[kPPT];
-#pragma unroll
-        for (int k = 0; k < kPPT; ++k) {
-            const unsigned peers = __match_any_sync(0xffffffffu, st[k].bucket);
-            rank[k] = __popc(peers & ((1u << lane) - 1u));
-            if (st[k].bucket < kBuckets && lane == __ffs(peers) - 1) s_cnt[k][warp][st[k].bucket] = __popc(peers);
-        }
+        // ---- stable ranking of the chunk by bucket: order (warp, lane)
+        const unsigned peers = __match_any_sync(0xffffffffu, bucket);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        __syncthreads();  // s_cnt cleared by every thread before any leader writes
+        if (bucket < kBuckets && lane == __ffs(peers) - 1) s_cnt[warp][bucket] = __popc(peers);
         __syncthreads();
         if (tid < kBuckets) {
             int run = 0;
-            for (int k = 0; k < kPPT; ++k)
-                for (int ww = 0; ww < kNW; ++ww) {
-                    const int v = s_cnt[k][ww][tid];
-                    s_cnt[k][ww][tid] = run;
-                    run += v;
-                }
-            s_round[tid] = run;
+            for (int ww = 0; ww < kNW; ++ww) {
+                const int v = s_cnt[ww][tid];
+                s_cnt[ww][tid] = run;
+                run += v;
+            }
+            s_base[tid] = run;  // this chunk's total of the bucket, turned into a base below
         }
         __syncthreads();
         if (tid == 0) {
@@ -524,34 +489,35 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             int *pre = I.chunk_pre[out] + (long long)c * kPre;
             int *cb = I.chunk_cb[out] + (long long)c * kBuckets;
             for (int d = 0; d < kBuckets; ++d) {
+                const int tot = s_base[d];
                 s_base[d] = acc;
                 pre[d] = acc;
                 cb[d] = s_run[d];
-                s_run[d] += s_round[d];
-                acc += s_round[d];
+                s_run[d] += tot;
+                acc += tot;
             }
             pre[kBuckets] = acc;
         }
         __syncthreads();
-        int *cell_out = I.cell[out];
-        R *off_out[3] = {(R *)I.off[out][0], (R *)I.off[out][1], (R *)I.off[out][2]};
-        R *u_out[3] = {(R *)I.u[out][0], (R *)I.u[out][1], (R *)I.u[out][2]};
-        R *w_out = (R *)I.w[out];
-        int *id_out = I.id[out];
-#pragma unroll
-        for (int k = 0; k < kPPT; ++k) {
-            const int b = st[k].bucket;
-            if (b >= kDead) continue;
-            const int pos = seg_out + base + s_base[b] + s_cnt[k][warp][b] + rank[k];
-            cell_out[pos] = st[k].cell;
-            off_out[0][pos] = kn[k].o[0];
-            if (ND == 3) off_out[1][pos] = kn[k].o[1];
-            off_out[2][pos] = kn[k].o[2];
-            u_out[0][pos] = kn[k].u[0];
-            u_out[1][pos] = kn[k].u[1];
-            u_out[2][pos] = kn[k].u[2];
-            w_out[pos] = kn[k].w;
-            if (id_out) id_out[pos] = st[k].id;
+
+        // ---- write the particle out, partitioned by bucket
+        if (bucket < kDead) {
+            const int p = seg_out + base + s_base[bucket] + s_cnt[warp][bucket] + rank;
+            cell_out[p] = cell_new;
+            off_out[0][p] = o1[0];
+            if (ND == 3) off_out[1][p] = o1[1];
+            off_out[2][p] = o1[2];
+            u_out[0][p] = u[0];
+            u_out[1][p] = u[1];
+            u_out[2][p] = u[2];
+            w_out[p] = w;
+            if (id_out) id_out[p] = pid;
+        }
+
+        // ---- FP32: fold the fixed-point J into global memory before it could overflow
+        if (kFixed && (r + 1) % kFlushChunks == 0 && base + kChunk < count) {
+            __syncthreads();
+            flush_j_fixed(I, T0, ND, sJH, sJL, jvol, I.jinv, tid, kNT);
         }
         __syncthreads();
     }
@@ -568,31 +534,11 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     }
     if (tid == 0 && s_run[kDead] > 0) atomicAdd(I.lost, (unsigned long long)s_run[kDead]);
 
-    // ---- flush the J tile (guard cells wrap on periodic axes, clip on absorbing ones)
-    for (int e = tid; e < 3 * jvol; e += kNT) {
-        const R v = sJ[e];
-        if (v == R(0)) continue;
-        const int comp = e / jvol;
-        const int rem = e - comp * jvol;
-        const int lx = rem % I.jdim[0];
-        const int ly = (rem / I.jdim[0]) % I.jdim[1];
-        const int lz = rem / jd01;
-        int gidx[3] = {T0[0] + I.jlo + lx, ND == 3 ? T0[1] + I.jlo + ly : 0, T0[2] + I.jlo + lz};
-        bool keep = true;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (ND == 2 && a == 1) continue;
-            if (gidx[a] < 0 || gidx[a] >= I.n[a]) {
-                if (I.bc[a] == 0)
-                    gidx[a] += gidx[a] < 0 ? I.n[a] : -I.n[a];
-                else
-                    keep = false;
-            }
-        }
-        if (!keep) continue;
-        R *J = (R *)I.J[comp];
-        atomicAdd(J + (gidx[0] + I.gh[0]) + I.sy * (gidx[1] + I.gh[1]) + I.sz * (gidx[2] + I.gh[2]), v);
-    }
+    // ---- flush the J tile
+    if (kFixed)
+        flush_j_fixed(I, T0, ND, sJH, sJL, jvol, I.jinv, tid, kNT);
+    else
+        flush_j_double(I, T0, ND, sJD, jvol, tid, kNT);
 }
 
 }  // namespace pic

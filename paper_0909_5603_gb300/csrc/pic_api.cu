@@ -52,6 +52,8 @@ struct pic_ctx {
     long long ghost_max = 0;
     bool any_periodic[3] = {false, false, false};
     int max_sweeps = 0;
+    long long *d_pencil = nullptr;       // per axis: [ninst + 1] filter pencil offsets (device)
+    long long pencil_total[3] = {0, 0, 0};
     std::vector<Block> blocks;
     uint64_t version = 1;  // bumps when device pointers of the instance change
     // state
@@ -235,7 +237,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     if (grid->ndim == 2 && grid->n[1] != 1) return fail(nullptr, PIC_ERR_ARG, "2D grids are x-z: n[1] must be 1");
     for (int a = 0; a < 3; ++a) {
         if (!activeaxis(grid->ndim, a)) continue;
-        if (grid->n[a] < 4) return fail(nullptr, PIC_ERR_ARG, "n[%d] = %d: at least 4 cells per axis", a, grid->n[a]);
+        if (grid->n[a] < 8) return fail(nullptr, PIC_ERR_ARG, "n[%d] = %d: at least 8 cells per axis", a, grid->n[a]);
         if (grid->bc[a] != PIC_PERIODIC && grid->bc[a] != PIC_ABSORBING) return fail(nullptr, PIC_ERR_ARG, "bc[%d] invalid", a);
         if (!(dx[a] > 0.0) || !std::isfinite(dx[a])) return fail(nullptr, PIC_ERR_ARG, "dx[%d] must be finite and > 0", a);
     }
@@ -255,7 +257,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     if (opt) o = *opt;
     if (o.precision != PIC_PREC_FP32 && o.precision != PIC_PREC_FP64) return fail(nullptr, PIC_ERR_ARG, "precision invalid");
     if (o.pusher != PIC_PUSHER_VAY && o.pusher != PIC_PUSHER_BORIS) return fail(nullptr, PIC_ERR_ARG, "pusher invalid");
-    if (o.filter_passes < 0 || o.filter_passes > 64) return fail(nullptr, PIC_ERR_ARG, "filter_passes out of range");
+    if (o.filter_passes < 0 || o.filter_passes > 8) return fail(nullptr, PIC_ERR_ARG, "filter_passes must be 0..8");
     if (o.threads != 0 && o.threads != particle_threads())
         return fail(nullptr, PIC_ERR_UNSUPPORTED, "threads = %d: this build runs %d threads per particle CTA", o.threads,
                     particle_threads());
@@ -292,7 +294,9 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     for (int a = 0; a < 3; ++a) {
         h.n[a] = c->n[a];
         h.bc[a] = c->bc[a];
-        h.gh[a] = activeaxis(c->ndim, a) ? kGhost : 0;
+        // x carries one extra ghost layer so the gather box can start one cell before the
+        // tile on a 16-byte boundary (TMA)
+        h.gh[a] = activeaxis(c->ndim, a) ? kGhost + (a == 0 ? 1 : 0) : 0;
         if (ts[a] <= 0) ts[a] = c->ndim == 3 ? 8 : 16;
         if (!activeaxis(c->ndim, a)) ts[a] = 1;
         h.ts[a] = ts[a];
@@ -309,7 +313,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
             delete c;
             return fail(nullptr, PIC_ERR_ARG, "tile[%d] = %d: at most 64", a, ts[a]);
         }
-    h.P[0] = ((c->n[0] + 2 * kGhost) + 3) / 4 * 4;
+    h.P[0] = ((c->n[0] + 2 * h.gh[0]) + 3) / 4 * 4;
     h.P[1] = c->n[1] + 2 * h.gh[1];
     h.P[2] = c->n[2] + 2 * h.gh[2];
     h.sy = h.P[0];
@@ -324,12 +328,13 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     h.dt = dt;
     h.q = o.charge;
     h.m = o.mass;
-    // gather box (tile + guard) and J tile geometry
-    const int gx_lo = c->fp64 ? 2 : 4;  // x origin rounded so the TMA start is 16-byte aligned
+    // gather box (tile + guard) and J tile geometry; the box starts one cell before the
+    // tile (padded x coordinate T0 + 4, 16-byte aligned) and its x extent is a multiple of
+    // 16 bytes
     const int xal = c->fp64 ? 2 : 4;
     const int hi = shape_order == 2 ? 2 : 1;
-    h.box_lo[0] = -gx_lo;
-    h.box[0] = ((gx_lo + ts[0] + hi) + xal - 1) / xal * xal;
+    h.box_lo[0] = -1;
+    h.box[0] = ((1 + ts[0] + hi) + xal - 1) / xal * xal;
     for (int a = 1; a < 3; ++a) {
         if (activeaxis(c->ndim, a)) {
             h.box_lo[a] = -1;
@@ -339,10 +344,14 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
             h.box[a] = 1;
         }
     }
+    h.div_n0 = make_fastdiv(c->n[0]);
+    h.div_n1 = make_fastdiv(c->n[1]);
     h.jlo = -shape_order;
     for (int a = 0; a < 3; ++a) h.jdim[a] = activeaxis(c->ndim, a) ? ts[a] + (shape_order == 2 ? 5 : 3) : 1;
     const size_t boxb = ((size_t)h.box[0] * h.box[1] * h.box[2] * c->es + 127) / 128 * 128;
-    c->smem = 128 + 6 * boxb + 3 * (size_t)h.jdim[0] * h.jdim[1] * h.jdim[2] * c->es;  // + alignment slack
+    // 6 field boxes + the J tile at 8 bytes per cell and component (FP64 values, or the two
+    // 32-bit fixed-point halves in FP32 mode) + alignment slack
+    c->smem = 128 + 6 * boxb + 3 * (size_t)h.jdim[0] * h.jdim[1] * h.jdim[2] * 8;
     if (c->smem > 200 * 1024) {
         delete c;
         return fail(nullptr, PIC_ERR_ARG, "tile too large: %zu bytes of shared memory per CTA", c->smem);
@@ -372,8 +381,9 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     c->d_sums = (double *)dalloc(c, 64 * sizeof(double));
     c->d_start = (int *)dalloc(c, sizeof(int) * (size_t)nt1);
     c->d_start_ptr = (int **)dalloc(c, sizeof(int *));
+    c->d_pencil = (long long *)dalloc(c, 6 * sizeof(long long));
     if (!F || !small || !tiles || !tm || !c->d_inst || !c->d_tile_start || !c->d_cell_start || !c->d_dense || !c->d_sums ||
-        !c->d_start || !c->d_start_ptr) {
+        !c->d_start || !c->d_start_ptr || !c->d_pencil) {
         dfree_all(c);
         delete c;
         return fail(nullptr, PIC_ERR_OOM, "device allocation failed (%zu bytes of fields)", fbytes);
@@ -398,6 +408,36 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     h.pop = tiles + 4 * nt1 + 2 * h.ntiles * kBuckets;
     h.tmap = tm;
 
+    // absorbing-layer factors per axis: 1 - s (d/L)^2 at depth d = max(0, L - i, i - (n-1-L)),
+    // evaluated in FP64 and stored in the working precision
+    for (int a = 0; a < 3; ++a) {
+        h.damp[a] = nullptr;
+        if (!activeaxis(c->ndim, a) || c->bc[a] != PIC_ABSORBING || o.absorb_cells <= 0) continue;
+        std::vector<double> f(c->n[a]);
+        const int L = o.absorb_cells;
+        for (int i = 0; i < c->n[a]; ++i) {
+            int d = 0;
+            if (L - i > d) d = L - i;
+            if (i - (c->n[a] - 1 - L) > d) d = i - (c->n[a] - 1 - L);
+            const double r = (double)d / (double)L;
+            f[i] = 1.0 - o.absorb_strength * r * r;
+        }
+        void *tab = dalloc(c, c->es * (size_t)c->n[a]);
+        if (!tab) {
+            dfree_all(c);
+            delete c;
+            return fail(nullptr, PIC_ERR_OOM, "absorbing-layer table allocation failed");
+        }
+        std::vector<float> f32(f.begin(), f.end());
+        const void *src = c->fp64 ? (const void *)f.data() : (const void *)f32.data();
+        if (cudaMemcpy(tab, src, c->es * (size_t)c->n[a], cudaMemcpyHostToDevice) != cudaSuccess) {
+            dfree_all(c);
+            delete c;
+            return fail(nullptr, PIC_ERR_CUDA, "absorbing-layer table upload failed");
+        }
+        h.damp[a] = tab;
+    }
+
     pic_status st = PIC_OK;
     CUtensorMap maps[6];
     if ((st = encode_tmaps(c, maps)) != PIC_OK) {
@@ -405,6 +445,12 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
         dfree_all(c);
         delete c;
         return fail(nullptr, st, "%s", e.c_str());
+    }
+    long long pencils[6];
+    for (int a = 0; a < 3; ++a) {
+        c->pencil_total[a] = o.filter_passes > 0 ? filter_pencils(c->n, c->ndim, a) : 0;
+        pencils[2 * a] = 0;
+        pencils[2 * a + 1] = c->pencil_total[a];
     }
     const int tstart[2] = {0, h.ntiles};
     const long long cstart[2] = {0, c->ncell};
@@ -415,6 +461,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
                cudaMemcpyAsync(c->d_tile_start, tstart, sizeof(tstart), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
                cudaMemcpyAsync(c->d_cell_start, cstart, sizeof(cstart), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
                cudaMemcpyAsync(c->d_start_ptr, &dptr_start, sizeof(int *), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+               cudaMemcpyAsync(c->d_pencil, pencils, sizeof(pencils), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
                prepare_particles(c->ndim, c->order, c->fp64, o.pusher, c->smem) == cudaSuccess;
     if (!okc || upload_inst(c) != PIC_OK) {
         cudaError_t e = cudaGetLastError();
@@ -601,6 +648,20 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
     CUDA_OR_FAIL(c, cudaMemcpy(h.pop, pop.data(), sizeof(int) * pop.size(), cudaMemcpyHostToDevice));
     CUDA_OR_FAIL(c, cudaMemcpy(h.chunk_pre[0], pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
     CUDA_OR_FAIL(c, cudaMemcpy(h.chunk_cb[0], cbv.data(), sizeof(int) * cbv.size(), cudaMemcpyHostToDevice));
+    // FP32 fixed-point current scale: the power of two that maps the bound |q| max(w) / dV
+    // on any single current contribution to at most 2^20
+    {
+        double wmax = 0.0;
+        for (int64_t p = 0; p < n; ++p) wmax = std::max(wmax, std::fabs(w[p]));
+        const double bound = std::fabs(c->opt.charge) * wmax / (c->dx[0] * c->dx[1] * c->dx[2]);
+        int e = 0;
+        if (bound > 0.0) {
+            std::frexp(bound, &e);  // bound < 2^e
+            e = std::max(-100, std::min(100, e));
+        }
+        h.jscale = bound > 0.0 ? (float)std::ldexp(1.0, 20 - e) : 1.0f;
+        h.jinv = bound > 0.0 ? (float)std::ldexp(1.0, e - 20) : 1.0f;
+    }
     CUDA_OR_FAIL(c, cudaMemset(h.cur, 0, 16 + sizeof(unsigned long long)));
     CUDA_OR_FAIL(c, cudaMemset(h.J[0], 0, 3 * (size_t)h.cstride * c->es));
     c->loaded = true;
@@ -732,11 +793,13 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
     }
     int filtered = 0;
     if ((mask & PIC_PHASE_FILTER) && c->max_sweeps > 0) {
+        const int nin = c->is_batch ? (int)c->members.size() : 1;
+        const long long *starts[3] = {c->d_pencil, c->d_pencil + (nin + 1), c->d_pencil + 2 * (nin + 1)};
         tm.begin(2);
-        CUDA_OR_FAIL(c, launch_filter(fp64, L, c->max_sweeps, c->stream));
+        CUDA_OR_FAIL(c, launch_filter(fp64, L, starts, c->pencil_total, c->ndim, c->stream));
         tm.end(2);
         filtered = 1;
-        launches += c->max_sweeps;
+        for (int a = 0; a < 3; ++a) launches += c->pencil_total[a] > 0 ? 1 : 0;
     }
     if (mask & PIC_PHASE_MAXWELL) {
         tm.begin(3);
@@ -1051,6 +1114,12 @@ static pic_status refresh_batch(pic_ctx *c)
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_inst, insts.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, c->stream));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_tile_start, ts.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, c->stream));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_cell_start, cs.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+    std::vector<long long> ps((size_t)3 * (n + 1), 0);
+    for (int a = 0; a < 3; ++a) {
+        for (int i = 0; i < n; ++i) ps[(size_t)a * (n + 1) + i + 1] = ps[(size_t)a * (n + 1) + i] + c->members[i]->pencil_total[a];
+        c->pencil_total[a] = ps[(size_t)a * (n + 1) + n];
+    }
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_pencil, ps.data(), sizeof(long long) * ps.size(), cudaMemcpyHostToDevice, c->stream));
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
     c->L.total_tiles = ts[n];
     c->L.total_cells = cs[n];
@@ -1091,7 +1160,8 @@ extern "C" pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx
     c->d_inst = (InstDev *)dalloc(c, sizeof(InstDev) * n);
     c->d_tile_start = (int *)dalloc(c, sizeof(int) * (n + 1));
     c->d_cell_start = (long long *)dalloc(c, sizeof(long long) * (n + 1));
-    if (!c->d_inst || !c->d_tile_start || !c->d_cell_start) {
+    c->d_pencil = (long long *)dalloc(c, sizeof(long long) * 3 * (n + 1));
+    if (!c->d_inst || !c->d_tile_start || !c->d_cell_start || !c->d_pencil) {
         dfree_all(c);
         delete c;
         return fail(nullptr, PIC_ERR_OOM, "batch tables do not fit");

@@ -50,21 +50,21 @@ __device__ __forceinline__ int shape_stag(int l, R o, R w[ORD + 1])
     }
 }
 
-// Old shape S0 and its change DS = S1 - S0 on one common window of ORD + 2 nodes starting
-// at node `ws` (tile-relative), for the Esirkepov deposit.  The nearest nodes of the two
-// positions differ by at most one (moves below one cell per step).  When they coincide
-// (the common case) DS is formed from d = f1 - f0, the exact difference of the two
-// offsets from that node, as products with d -- e.g. for order 2 the centre weight gives
-// (3/4 - f1^2) - (3/4 - f0^2) = -d (f0 + f1) -- instead of subtracting two O(1) weights,
-// which in FP32 would lose the small displacement to cancellation.
+// Old shape S0 and its change DS = S1 - S0 on one common window starting at node `ws`
+// (tile-relative), for the Esirkepov deposit; `nw` is the number of window nodes that can
+// be non-zero: ORD + 1 when the particle keeps its nodes, ORD + 2 when it moves to the
+// next set (moves stay below one cell per step).  In the first case DS is formed from
+// d = f1 - f0, the exact difference of the two offsets from the first node, as products
+// with d -- e.g. for order 2 the centre weight gives (3/4 - f1^2) - (3/4 - f0^2) =
+// -d (f0 + f1) -- instead of subtracting two O(1) weights, which in FP32 would lose the
+// small displacement to cancellation.  Entries at and beyond nw are zero.
 template <int ORD, typename R>
-__device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R S0[ORD + 2], R DS[ORD + 2])
+__device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R S0[ORD + 2], R DS[ORD + 2], int &nw)
 {
     R w0[ORD + 1], w1[ORD + 1];
     const int b0 = shape_nodal<ORD>(l0, o0, w0);
     const int b1 = shape_nodal<ORD>(l1, o1, w1);
     if (b0 == b1) {
-        // same nodes: offsets from the first node of the window
         const R f0 = o0 - R(b0 - l0 + (ORD == 2 ? 1 : 0));
         const R f1 = o1 - R(b1 - l1 + (ORD == 2 ? 1 : 0));
         const R d = f1 - f0;
@@ -81,6 +81,7 @@ __device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R S0[ORD
             DS[2] = R(0.5) * d * (R(1) + s);
         }
         DS[ORD + 1] = R(0);
+        nw = ORD + 1;
         return b0;
     }
     const int ws = b0 < b1 ? b0 : b1;
@@ -94,7 +95,166 @@ __device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R S0[ORD
         S0[i] = s0 == 0 ? a0 : a1;
         DS[i] = (s1 == 0 ? c0 : c1) - S0[i];
     }
+    nw = ORD + 2;
     return ws;
+}
+
+// ------------------------------------------------------------------------------------
+// Shared-memory J accumulation policies for the deposit.
+//
+// FixedAcc (FP32 mode): contributions arrive pre-scaled so that each is at most 2^20 in
+// magnitude: any single current contribution is bounded by |q| w / dV (the Esirkepov
+// running sum never exceeds the displacement in cells, which is below dt / dx since
+// |v| < c, and the transverse factor is at most 1), so the instance's scale is the power
+// of two that maps |q| max(w) / dV to at most 2^20.  Each contribution is split into its
+// nearest integer H and the remainder rounded to 2^-16, L, and both are added with native
+// 32-bit integer shared atomics.  A cell receives at most one contribution per particle,
+// and the tile is folded into global memory at least every 2047 particles, so
+// |sum H| < 2^31 and |sum L| < 2^26: no overflow, a resolution of 2^-36 of the bound, and a
+// sum that does not depend on the order of the additions.  The float -> integer rounding
+// adds 1.5 * 2^23 (exact for |x| <= 2^22).
+// DoubleAcc (FP64 mode): FP64 shared atomics.
+// ------------------------------------------------------------------------------------
+struct FixedAcc {
+    int *H;
+    int *L;
+    __device__ __forceinline__ void add(int idx, float x) const
+    {
+        const float M = 12582912.0f;  // 1.5 * 2^23
+        const float y = __fadd_rn(x, M);
+        const int hi = __float_as_int(y) - 0x4B400000;
+        const float r = __fsub_rn(x, __fsub_rn(y, M));   // exact, |r| <= 1/2
+        const float z = __fmaf_rn(r, 65536.0f, M);
+        const int lo = __float_as_int(z) - 0x4B400000;
+        if (hi != 0) atomicAdd(H + idx, hi);
+        if (lo != 0) atomicAdd(L + idx, lo);
+    }
+};
+
+struct DoubleAcc {
+    double *J;
+    __device__ __forceinline__ void add(int idx, double x) const { atomicAdd(J + idx, x); }
+};
+
+// ------------------------------------------------------------------------------------
+// Esirkepov charge-conserving deposit of one particle into the shared J tile (three
+// components of jvol cells each, tile origin at node jlo).  With S0, DS the old shape and
+// its change per axis, in 3D
+//   Wx = DSx (S0y S0z + DSy S0z / 2 + S0y DSz / 2 + DSy DSz / 3)   (cyclic for y, z),
+//   Jx(i+1/2) - Jx(i-1/2) = f_x Wx(i),  f_x = -(q w / dV) dx / dt,
+// summed along x from zero at the window start; in 2D3V (x-z plane) Wx = DSx (S0z + DSz/2),
+// Wz = DSz (S0x + DSx/2) and the out-of-plane Jy = f_y' (S0x S0z + DSx S0z / 2 +
+// S0x DSz / 2 + DSx DSz / 3) with f_y' = (q w / dV) v_y.  Only the nw window nodes that
+// can be non-zero are visited; the running sum vanishes at the last node of the window.
+// ------------------------------------------------------------------------------------
+template <int ND, int ORD, typename R, typename Acc>
+__device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3], const int l1[3], const R o1[3], R fx,
+                                                  R fy, R fz, int jlo, int jlo_y, int jd0, int jd01, int jvol,
+                                                  const Acc &acc)
+{
+    constexpr int W = ORD + 2;
+    R S0x[W], DSx[W], S0y[W], DSy[W], S0z[W], DSz[W];
+    int nwx, nwy = 1, nwz;
+    const int wsx = shape_window<ORD>(l0[0], o0[0], l1[0], o1[0], S0x, DSx, nwx) - jlo;
+    const int wsz = shape_window<ORD>(l0[2], o0[2], l1[2], o1[2], S0z, DSz, nwz) - jlo;
+    const R half = R(0.5), third = R(1.0 / 3.0);
+    if (ND == 3) {
+        const int wsy = shape_window<ORD>(l0[1], o0[1], l1[1], o1[1], S0y, DSy, nwy) - jlo_y;
+        const int base = wsx + jd0 * wsy + jd01 * wsz;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            if (k >= nwz) break;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                if (j >= nwy) break;
+                const R Y = S0y[j] * S0z[k] + half * (DSy[j] * S0z[k] + S0y[j] * DSz[k]) + third * DSy[j] * DSz[k];
+                const R fY = fx * Y;
+                R run = R(0);
+#pragma unroll
+                for (int i = 0; i < W - 1; ++i) {
+                    if (i >= nwx - 1) break;
+                    run += DSx[i];
+                    const R v = fY * run;
+                    if (v != R(0)) acc.add(base + i + jd0 * j + jd01 * k, v);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            if (k >= nwz) break;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                if (i >= nwx) break;
+                const R X = S0x[i] * S0z[k] + half * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) + third * DSx[i] * DSz[k];
+                const R fX = fy * X;
+                R run = R(0);
+#pragma unroll
+                for (int j = 0; j < W - 1; ++j) {
+                    if (j >= nwy - 1) break;
+                    run += DSy[j];
+                    const R v = fX * run;
+                    if (v != R(0)) acc.add(jvol + base + i + jd0 * j + jd01 * k, v);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            if (j >= nwy) break;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                if (i >= nwx) break;
+                const R X = S0x[i] * S0y[j] + half * (DSx[i] * S0y[j] + S0x[i] * DSy[j]) + third * DSx[i] * DSy[j];
+                const R fX = fz * X;
+                R run = R(0);
+#pragma unroll
+                for (int k = 0; k < W - 1; ++k) {
+                    if (k >= nwz - 1) break;
+                    run += DSz[k];
+                    const R v = fX * run;
+                    if (v != R(0)) acc.add(2 * jvol + base + i + jd0 * j + jd01 * k, v);
+                }
+            }
+        }
+    } else {
+        // fy carries the out-of-plane factor (q w / dV) v_y here
+        const int base = wsx + jd01 * wsz;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            if (k >= nwz) break;
+            const R fY = fx * (S0z[k] + half * DSz[k]);
+            R run = R(0);
+#pragma unroll
+            for (int i = 0; i < W - 1; ++i) {
+                if (i >= nwx - 1) break;
+                run += DSx[i];
+                const R v = fY * run;
+                if (v != R(0)) acc.add(base + i + jd01 * k, v);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            if (i >= nwx) break;
+            const R fX = fz * (S0x[i] + half * DSx[i]);
+            R run = R(0);
+#pragma unroll
+            for (int k = 0; k < W - 1; ++k) {
+                if (k >= nwz - 1) break;
+                run += DSz[k];
+                const R v = fX * run;
+                if (v != R(0)) acc.add(2 * jvol + base + i + jd01 * k, v);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            if (k >= nwz) break;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                if (i >= nwx) break;
+                const R v = fy * (S0x[i] * S0z[k] + half * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) + third * DSx[i] * DSz[k]);
+                if (v != R(0)) acc.add(jvol + base + i + jd01 * k, v);
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------

@@ -15,6 +15,31 @@ constexpr int kBuckets = 28;    // 27 directions + dead
 constexpr int kPre = 29;        // per chunk: exclusive prefix of the 28 buckets + size
 constexpr int kCenterDir = 13;  // (0,0,0)
 
+// Division of 0 <= x < 2^31 by a fixed divisor d >= 1 without a divide instruction
+// (Granlund & Montgomery, "Division by invariant integers using multiplication", 1994,
+// round-up variant): s = ceil(log2 d), m = floor(2^(32+s) / d) + 1 (33 bits), then
+// floor(x / d) = (x * m) >> (32 + s).
+struct FastDiv {
+    unsigned long long m;
+    int s;
+    int d;
+};
+
+inline FastDiv make_fastdiv(int d)
+{
+    FastDiv f;
+    f.d = d;
+    f.s = 0;
+    while ((1LL << f.s) < d) ++f.s;
+    f.m = (1ULL << (32 + f.s)) / (unsigned long long)d + 1ULL;  // 32 + s <= 63 for d < 2^31
+    return f;
+}
+
+__host__ __device__ __forceinline__ int fast_div(int x, const FastDiv &f)
+{
+    return (int)(((unsigned long long)(unsigned)x * f.m) >> (32 + f.s));
+}
+
 // device error word bits (sticky)
 constexpr int kErrTimeout = 1;      // a bounded mbarrier wait gave up
 constexpr int kErrSpeed = 2;        // |displacement| >= 1 cell or non-finite in a step
@@ -63,6 +88,10 @@ struct InstDev {
     unsigned long long *lost; // particles removed so far
     int *live;          // live particles (written by the scan)
     const CUtensorMap *tmap;  // 6 maps: Ex Ey Ez Bx By Bz boxes for the gather stage
+    const void *damp[3];      // absorbing-layer factor per cell index along each axis
+                              // (working precision; null on periodic / inactive axes)
+    FastDiv div_n0, div_n1;   // cell index -> (i, j, k)
+    float jscale, jinv;       // FP32 fixed-point current: scale (a power of two) and 1/scale
     int box[3];         // TMA box extents (elements)
     int box_lo[3];      // box origin relative to the tile origin (cells, <= 0)
     int jlo;            // J tile origin relative to the tile origin (-1 or -2)
@@ -108,7 +137,19 @@ cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, i
                            double *w, int *id, cudaStream_t s);
 cudaError_t launch_particle_sums(int fp64, const Launch &L, double *sums, cudaStream_t s);
 cudaError_t launch_rho(int order, int fp64, const Launch &L, double *rho, cudaStream_t s);
-cudaError_t launch_filter(int fp64, const Launch &L, int max_sweeps, cudaStream_t s);
+cudaError_t launch_filter(int fp64, const Launch &L, const long long *const pencil_start[3],
+                          const long long pencil_total[3], int ndim, cudaStream_t s);
+// pencils of the per-axis filter kernel for an instance: kPencil (64) cells along the
+// axis times 32 lines (x: 32 consecutive (y, z) rows; y, z: 32 consecutive x columns)
+inline long long filter_pencils(const int n[3], int ndim, int axis)
+{
+    const int kP = 64;
+    if (ndim == 2 && axis == 1) return 0;
+    if (axis == 0) return (long long)((n[0] + kP - 1) / kP) * (((long long)n[1] * n[2] + 31) / 32);
+    const long long cols = (n[0] + 31) / 32;
+    if (axis == 1) return cols * ((n[1] + kP - 1) / kP) * n[2];
+    return cols * ((n[2] + kP - 1) / kP) * n[1];
+}
 cudaError_t launch_maxwell(int fp64, const Launch &L, int filtered, cudaStream_t s);
 cudaError_t launch_ghost(int fp64, const Launch &L, int axis, long long per_inst_max, cudaStream_t s);
 cudaError_t prepare_particles(int ndim, int order, int fp64, int pusher, size_t smem);
