@@ -101,6 +101,8 @@ def lib():
         L.orc_diagnostics.argtypes = [vp, _f64p]
         L.orc_load_lab_frame.restype = ctypes.c_int
         L.orc_load_lab_frame.argtypes = [vp, ctypes.c_double, vp, vp, vp]
+        L.orc_ion_integral.restype = ctypes.c_double
+        L.orc_ion_integral.argtypes = [vp, ctypes.c_double, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -227,6 +229,10 @@ class Sim:
         out = np.zeros(self.ncell)
         lib().orc_rho(self._h, out)
         return out.reshape(self.n[2], self.n[1], self.n[0])
+
+    def ion_integral(self, a, b):
+        """Ion-background charge between box coordinates a < b at t' = 0 (per unit area)."""
+        return lib().orc_ion_integral(self._h, float(a), float(b))
 
     def div_e(self):
         out = np.zeros(self.ncell)

@@ -41,6 +41,10 @@ struct orc_sim {
     int32_t *cell, *id;
     double *off, *u, *w; /* off and u: 3 per particle, interleaved */
     int64_t n_lost, step;
+    /* ion background of a lab-frame plasma load (see orc_ion_integral) */
+    int ion;
+    double ion_n0, ion_zs, ion_ramp, ion_gb, ion_beta;
+    int64_t n_pp; /* particle phases run since the last load */
 };
 
 /* Yee staggering (in cells) of each component along each axis. */
@@ -289,6 +293,8 @@ int orc_set_particles(orc_sim *s, int64_t np, const int32_t *cell, const double 
     }
     s->np = np;
     s->n_lost = 0;
+    s->ion = 0; /* particles loaded directly carry no ion background */
+    s->n_pp = 0;
     orc_sort(s);
     return 0;
 }
@@ -535,9 +541,76 @@ static void esirkepov(orc_sim *s, const int c0[3], const double o0[3], const int
  * offset that rounds to exactly 1 after the subtraction becomes 0 in the next cell.
  * Then the canonical stable sort by tile.
  * ---------------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------------------
+ * Ion background of a lab-frame plasma (Sec. 2, reading).  The plasma's ions are at rest
+ * in the lab frame, where they neutralise the electrons; only the electrons are
+ * macro-particles here, so the ions are a rigid charge density.  In the boosted frame their density is the lab
+ * profile contracted by gamma_b, rho_i0(s) = -q gamma_b n0 p(gamma_b s) at t' = 0 for s in
+ * the box [0, Lz), zero outside it (the ions of the loaded volume only, like the
+ * electrons), and it moves rigidly at -beta_b: rho_i(z, t') = rho_i0(z + beta_b t'),
+ * wrapped into the box when z is periodic.
+ *
+ * orc_ion_integral(a, b) = integral of rho_i0 over [a, b] (box coordinates at t' = 0).
+ * p is piecewise linear (zero, ramp, plateau), so each piece is integrated exactly by the
+ * trapezoid rule.  From it, with t^n = n dt:
+ *   current on the Jz face z_f = (k + 1/2) dz during step n (the ions crossing it):
+ *     Jz_i = -orc_ion_integral(z_f + beta t^n, z_f + beta t^{n+1}) / dt,
+ *   charge on node k (average over its dual cell [z_k - dz/2, z_k + dz/2]):
+ *     rho_i = orc_ion_integral(z_k - dz/2 + beta t, z_k + dz/2 + beta t) / dz,
+ * so the discrete continuity equation holds for the ions by construction.
+ * ---------------------------------------------------------------------------------- */
+static double ion_piece(const orc_sim *s, double lo, double hi)
+{
+    /* integral of rho_i0 over [lo, hi], both inside [0, Lz] */
+    double g = s->ion_gb, rmax = -s->q * g * s->ion_n0;
+    double za = s->ion_zs / g, zb = (s->ion_zs + s->ion_ramp) / g;
+    double total = 0.0;
+    /* ramp piece [za, zb): rho = rmax (g z - zs) / ramp, linear */
+    double a = lo > za ? lo : za, b = hi < zb ? hi : zb;
+    if (b > a) {
+        double fa = rmax * (g * a - s->ion_zs) / s->ion_ramp;
+        double fb = rmax * (g * b - s->ion_zs) / s->ion_ramp;
+        total += 0.5 * (fa + fb) * (b - a);
+    }
+    /* plateau [zb, inf): rho = rmax */
+    a = lo > zb ? lo : zb;
+    b = hi;
+    if (b > a) total += rmax * (b - a);
+    return total;
+}
+
+double orc_ion_integral(const orc_sim *s, double a, double b)
+{
+    if (!s->ion || !(b > a)) return 0.0;
+    double Lz = s->n[2] * s->dx[2];
+    if (s->bc[2] == ORC_ABSORBING || !s->active[2]) {
+        double lo = a > 0.0 ? a : 0.0, hi = b < Lz ? b : Lz;
+        return hi > lo ? ion_piece(s, lo, hi) : 0.0;
+    }
+    /* periodic: sum over the periods [m Lz, (m+1) Lz) that [a, b] meets */
+    double total = 0.0;
+    for (double m = floor(a / Lz); m * Lz < b; m += 1.0) {
+        double lo = a > m * Lz ? a : m * Lz, hi = b < (m + 1.0) * Lz ? b : (m + 1.0) * Lz;
+        if (hi > lo) total += ion_piece(s, lo - m * Lz, hi - m * Lz);
+    }
+    return total;
+}
+
+static void add_ion_current(orc_sim *s)
+{
+    double t0 = (double)s->n_pp * s->dt, t1 = (double)(s->n_pp + 1) * s->dt;
+    for (int k = 0; k < s->n[2]; ++k) {
+        double zf = (k + 0.5) * s->dx[2];
+        double jz = -orc_ion_integral(s, zf + s->ion_beta * t0, zf + s->ion_beta * t1) / s->dt;
+        for (int j = 0; j < s->n[1]; ++j)
+            for (int i = 0; i < s->n[0]; ++i) s->f[ORC_JZ][node_index(s, i, j, k)] += jz;
+    }
+}
+
 void orc_particle_phase(orc_sim *s)
 {
     for (int c = ORC_JX; c <= ORC_JZ; ++c) memset(s->f[c], 0, (size_t)s->ncell * sizeof(double));
+    if (s->ion && s->active[2]) add_ion_current(s);
     int64_t keep = 0;
     for (int64_t p = 0; p < s->np; ++p) {
         double E[3], B[3];
@@ -591,6 +664,7 @@ void orc_particle_phase(orc_sim *s)
         keep++;
     }
     s->np = keep;
+    s->n_pp++;
     orc_sort(s);
 }
 
@@ -764,6 +838,14 @@ void orc_rho(const orc_sim *s, double *out)
                     if (idx >= 0) out[idx] += s->q * s->w[p] / dV * wt;
                 }
     }
+    if (s->ion && s->active[2]) { /* plus the ion background on its dual cells */
+        double t = (double)s->n_pp * s->dt, dz = s->dx[2];
+        for (int k = 0; k < s->n[2]; ++k) {
+            double r = orc_ion_integral(s, (k - 0.5) * dz + s->ion_beta * t, (k + 0.5) * dz + s->ion_beta * t) / dz;
+            for (int j = 0; j < s->n[1]; ++j)
+                for (int i = 0; i < s->n[0]; ++i) out[node_index(s, i, j, k)] += r;
+        }
+    }
 }
 
 /* Discrete divergence of E on nodes: sum_a (E_a[i] - E_a[i - e_a]) / dx_a. */
@@ -864,6 +946,8 @@ int orc_load_lab_frame(orc_sim *s, double gb, const double *laser, const double 
     reserve(s, 1024);
     s->n_lost = 0;
     s->step = 0;
+    s->n_pp = 0;
+    s->ion = 0;
     for (int c = 0; c < ORC_NCOMP; ++c) memset(s->f[c], 0, (size_t)s->ncell * sizeof(double));
 
     if (laser) {
@@ -891,6 +975,12 @@ int orc_load_lab_frame(orc_sim *s, double gb, const double *laser, const double 
         double uth[3] = {plasma[4], plasma[5], plasma[6]};
         uint64_t seed = (uint64_t)plasma[7];
         double dV = s->dx[0] * s->dx[1] * s->dx[2];
+        s->ion = n0 > 0.0;
+        s->ion_n0 = n0;
+        s->ion_zs = zs;
+        s->ion_ramp = ramp;
+        s->ion_gb = gb;
+        s->ion_beta = b;
         for (int64_t cell = 0; cell < s->ncell; ++cell) {
             int c[3];
             cell_coords(s, (int32_t)cell, c);

@@ -64,6 +64,9 @@ void orc_div_e(const orc_sim *s, double *out);
 void orc_diagnostics(const orc_sim *s, double out[8]);
 int orc_load_lab_frame(orc_sim *s, double gamma_b, const double *laser, const double *plasma,
                        const double *beam);
+/* Charge of the lab-frame plasma's ion background between box coordinates a < b at
+ * t' = 0 (per unit transverse area); 0 when the last load had no plasma. */
+double orc_ion_integral(const orc_sim *s, double a, double b);
 
 #ifdef __cplusplus
 }
