@@ -27,6 +27,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+import synth  # noqa: E402  (seeded input recipes, shared with the tests)
 
 METRIC = "particle-steps/s (gather+Vay push+deposit) & % HBM roofline, FP32 vs FP64"
 
@@ -38,17 +41,7 @@ PPC = 2
 
 
 def workload(nz=N_GRID[2]):
-    b = math.sqrt(1.0 - 1.0 / GAMMA_B ** 2)
-    doppler = GAMMA_B * (1.0 + b)
-    dz = doppler * LAMBDA0 / 16.0          # 16 cells per boosted laser wavelength
-    dx = 2.0 * LAMBDA0                     # 10 cells across the waist
-    dt = 0.5 * dz
-    k0 = 2.0 * math.pi / LAMBDA0
-    n_c = k0 * k0                          # critical density (q = m = eps0 = c = 1)
-    duration = 10.0 * LAMBDA0              # 10 lab periods
-    laser = (2.0, LAMBDA0, 20.0 * LAMBDA0, duration, 2.0 * duration)
-    plasma = (n_c / 900.0, 0.0, 2.0 * dz * GAMMA_B, PPC, (0.0, 0.0, 0.0), 3)
-    return dict(n=(N_GRID[0], N_GRID[1], nz), dx=(dx, dx, dz), dt=dt, laser=laser, plasma=plasma)
+    return synth.lwfa_stage((N_GRID[0], N_GRID[1], nz), GAMMA_B, PPC, seed=3, lambda0=LAMBDA0)
 
 
 def measured_peaks():

@@ -68,7 +68,7 @@ enum { PIC_PREC_FP32 = 0, PIC_PREC_FP64 = 1 };
 enum { PIC_PUSHER_VAY = 0, PIC_PUSHER_BORIS = 1 };
 enum {
     PIC_EX = 0, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ,
-    PIC_RHO = 9, /* charge density deposited from the particles (getter only) */
+    PIC_RHO = 9, /* charge density on the nodes: particles + ion background (getter only) */
     PIC_DIVE = 10 /* discrete divergence of E on nodes (getter only) */
 };
 enum { PIC_PHASE_PARTICLES = 1, PIC_PHASE_FILTER = 2, PIC_PHASE_MAXWELL = 4, PIC_PHASE_ALL = 7 };
@@ -93,7 +93,8 @@ typedef struct {
     int filter_passes;      /* binomial 1-2-1 passes on J per step, 0..8 (0 = none) */
     int tile[3];            /* particle tile in cells; 0 = default (8^3 in 3D, 16x1x16 in
                                2D); tile[0] must be a multiple of 4 */
-    int threads;            /* threads per particle CTA: 128 or 256 (0 = 256) */
+    int threads;            /* threads per particle CTA: 0 = this build's size (256), or
+                               that size given explicitly (others: PIC_ERR_UNSUPPORTED) */
     int absorb_cells;       /* width L of the absorbing layer (default 16) */
     double absorb_strength; /* per-step damping 1 - s (d/L)^2 at depth d (default 0.1) */
     double charge, mass;    /* species charge and mass (default -1, 1) */
@@ -110,7 +111,7 @@ typedef struct {
     double t;              /* boosted-frame time step * dt */
     double field_energy;   /* (1/2) sum (E^2 + B^2) dV over the cells, FP64 sum */
     double kinetic_energy; /* sum w m (gamma - 1) over particles, FP64 sum */
-    double total_charge;   /* sum q w over particles, FP64 sum */
+    double total_charge;   /* sum q w over particles (ion background excluded), FP64 sum */
     int64_t n_particles;   /* live macro-particles */
     int64_t n_lost;        /* macro-particles removed at absorbing boundaries */
     int32_t error_flags;   /* sticky device error word (0 = none) */
@@ -184,13 +185,20 @@ typedef struct {
  * E'x = B'y), plasma at lab rest drifting at -beta with density gamma n0, beam
  * particles boosted then drifted ballistically to t' = 0.  Host FP64, seeded with
  * SplitMix64 (counter-based); particles falling outside the box are dropped.  Any of
- * the three may be NULL.  Resets step count, J and the lost counter. */
+ * the three may be NULL.  Resets step count, J and the lost counter.
+ * Ion background: the plasma's ions are at rest in the lab frame, so they are not
+ * macro-particles but a rigid charge density of the opposite charge, the lab profile
+ * contracted by gamma_b, filling the loaded box at t' = 0 and streaming at -beta_b
+ * (wrapping when z is periodic, leaving through the -z face when absorbing).  Every
+ * step adds their current on the Jz faces -- the charge of the profile crossing each
+ * face during the step, over dt -- and PIC_RHO adds their charge on each node's dual
+ * cell, so div E - rho stays constant for the ions too. */
 pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *laser, const pic_plasma_lab *plasma,
                               const pic_beam_lab *beam);
 
 /* Replaces the particles with n host particles (exact-input path).  cell[n]; off3[3n]
  * in [0,1) (PIC_ERR_ARG otherwise); u3[3n]; w[n]; id[n] or NULL (ids 0..n-1).  The
- * library sorts them into the canonical order. */
+ * library sorts them into the canonical order.  Clears any ion background. */
 pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3,
                               const double *u3, const double *w, const int32_t *id);
 

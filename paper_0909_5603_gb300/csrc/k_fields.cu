@@ -148,10 +148,14 @@ __device__ __forceinline__ bool filter_active_axis(const InstDev &I, int axis)
 
 // A pencil is 32 lines parallel to `axis` times kPencil cells along it.  Lines: for the
 // x axis, 32 consecutive (y, z) rows; for y and z, 32 consecutive x columns at one z (y).
+// Work assignment without divisions: for the x axis a warp walks one line (lanes along x,
+// coalesced), the 8 warps take lines 8 at a time; for y and z the lanes take the 32
+// columns (coalesced along x) and the warps step along the axis.
 template <typename R>
 __global__ void __launch_bounds__(256) k_filter_axis(Launch L, int axis, const long long *pencil_start, int src_is_jt)
 {
     __shared__ R buf[2][kPencil + 2 * kMaxPasses][33];
+    __shared__ long long s_line[32];
     const long long g = blockIdx.x;
     if (g >= pencil_start[L.ninst]) return;
     const int ii = find_instance_ll(pencil_start, L.ninst, g);
@@ -166,68 +170,73 @@ __global__ void __launch_bounds__(256) k_filter_axis(Launch L, int axis, const l
     r /= nseg;
     const long long st[3] = {1, I.sy, I.sz};
     const long long sa = st[axis];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // line c -> padded offset of its cell 0 along the axis, or -1 when the line is absent
-    long long line_off[1];
-    (void)line_off;
-    auto line = [&](int c) -> long long {
+    if (tid < 32) {
+        long long off = -1;
+        const int c = tid;
         if (axis == 0) {
             const long long row = r * 32 + c;
-            if (row >= (long long)I.n[1] * I.n[2]) return -1;
-            const int y = (int)(row % I.n[1]), z = (int)(row / I.n[1]);
-            return I.gh[0] + st[1] * (y + I.gh[1]) + st[2] * (z + I.gh[2]);
+            if (row < (long long)I.n[1] * I.n[2]) {
+                const int y = (int)(row % I.n[1]), z = (int)(row / I.n[1]);
+                off = I.gh[0] + st[1] * (y + I.gh[1]) + st[2] * (z + I.gh[2]);
+            }
+        } else {
+            const int ncol = (I.n[0] + 31) / 32;
+            const int x = (int)(r % ncol) * 32 + c;
+            const int other = (int)(r / ncol);  // z for the y axis, y for the z axis
+            if (x < I.n[0])
+                off = axis == 1 ? (x + I.gh[0]) + st[1] * I.gh[1] + st[2] * (other + I.gh[2])
+                                : (x + I.gh[0]) + st[1] * (other + I.gh[1]) + st[2] * I.gh[2];
         }
-        const int ncol = (I.n[0] + 31) / 32;
-        const int x = (int)(r % ncol) * 32 + c;
-        const int other = (int)(r / ncol);  // z for the y axis, y for the z axis
-        if (x >= I.n[0]) return -1;
-        if (axis == 1) return (x + I.gh[0]) + st[1] * I.gh[1] + st[2] * (other + I.gh[2]);
-        return (x + I.gh[0]) + st[1] * (other + I.gh[1]) + st[2] * I.gh[2];
-    };
+        s_line[c] = off;
+    }
+    __syncthreads();
     void *const *src = src_is_jt ? I.Jt : I.J;
     void *const *dst = src_is_jt ? I.J : I.Jt;
     const int len = kPencil + 2 * P;
-    const int tid = threadIdx.x;
+    // (c, s) iteration: x axis: c = warp + 8 m, s = lane + 32 k; y, z: c = lane, s = warp + 8 k
+    const int c_first = axis == 0 ? warp : lane, c_step = axis == 0 ? 8 : 32;
+    const int s_first = axis == 0 ? lane : warp, s_step = axis == 0 ? 32 : 8;
     for (int comp = 0; comp < 3; ++comp) {
         const R *a = (const R *)src[comp];
         R *b = (R *)dst[comp];
-        // load buf[s][c] = line c at axis position q0 + s - P (wrapped, or 0 outside)
-        for (int e = tid; e < len * 32; e += blockDim.x) {
-            int s_, c_;
-            if (axis == 0) { c_ = e / len; s_ = e - c_ * len; } else { s_ = e >> 5; c_ = e & 31; }
-            const long long lo = line(c_);
-            int q = q0 + s_ - P;
-            bool ok = lo >= 0;
-            if (q < 0 || q >= n) {
-                // a ragged last pencil can reach more than one period past the end
-                if (per) q = ((q % n) + n) % n;
-                else ok = false;
+        for (int c = c_first; c < 32; c += c_step) {
+            const long long lo = s_line[c];
+            for (int s_ = s_first; s_ < len; s_ += s_step) {
+                int q = q0 + s_ - P;
+                bool ok = lo >= 0;
+                if (q < 0 || q >= n) {
+                    // a ragged last pencil can reach more than one period past the end
+                    if (per) q = ((q % n) + n) % n;
+                    else ok = false;
+                }
+                buf[0][s_][c] = ok ? a[lo + (long long)q * sa] : R(0);
             }
-            buf[0][s_][c_] = ok ? a[lo + (long long)q * sa] : R(0);
         }
         __syncthreads();
         int cur = 0;
         for (int pass = 0; pass < P; ++pass) {
-            for (int e = tid; e < len * 32; e += blockDim.x) {
-                int s_, c_;
-                if (axis == 0) { c_ = e / len; s_ = e - c_ * len; } else { s_ = e >> 5; c_ = e & 31; }
-                R v = R(0);
-                if (s_ >= 1 && s_ < len - 1) {
-                    v = R(0.25) * buf[cur][s_ - 1][c_] + R(0.5) * buf[cur][s_][c_] + R(0.25) * buf[cur][s_ + 1][c_];
-                    const int q = q0 + s_ - P;
-                    if (!per && (q < 0 || q >= n)) v = R(0);
+            for (int c = c_first; c < 32; c += c_step)
+                for (int s_ = s_first; s_ < len; s_ += s_step) {
+                    R v = R(0);
+                    if (s_ >= 1 && s_ < len - 1) {
+                        v = R(0.25) * buf[cur][s_ - 1][c] + R(0.5) * buf[cur][s_][c] + R(0.25) * buf[cur][s_ + 1][c];
+                        const int q = q0 + s_ - P;
+                        if (!per && (q < 0 || q >= n)) v = R(0);
+                    }
+                    buf[cur ^ 1][s_][c] = v;
                 }
-                buf[cur ^ 1][s_][c_] = v;
-            }
             __syncthreads();
             cur ^= 1;
         }
-        for (int e = tid; e < kPencil * 32; e += blockDim.x) {
-            int s_, c_;
-            if (axis == 0) { c_ = e / kPencil; s_ = e - c_ * kPencil; } else { s_ = e >> 5; c_ = e & 31; }
-            const int q = q0 + s_;
-            const long long lo = line(c_);
-            if (q >= n || lo < 0) continue;
-            b[lo + (long long)q * sa] = buf[cur][s_ + P][c_];
+        for (int c = c_first; c < 32; c += c_step) {
+            const long long lo = s_line[c];
+            if (lo < 0) continue;
+            for (int s_ = s_first; s_ < kPencil; s_ += s_step) {
+                const int q = q0 + s_;
+                if (q < n) b[lo + (long long)q * sa] = buf[cur][s_ + P][c];
+            }
         }
         __syncthreads();
     }

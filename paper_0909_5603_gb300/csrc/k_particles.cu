@@ -7,8 +7,8 @@ namespace pic {
 
 // -------------------------------------------------------------------------------------
 // Tile population scan: one CTA per instance.  mode 0 (step): lays out the output
-// layout (segment starts and chunk bases) from the populations, zeroes them and flips
-// the parity.  mode 1 (read-out): writes the exclusive scan of the populations into
+// layout (segment starts and chunk bases) from the populations, zeroes them, flips the
+// parity and counts the particle phase.  mode 1 (read-out): writes the exclusive scan of the populations into
 // `dst` (one int per tile + total) and the total into *live, changing nothing else.
 // -------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_scan(Launch L, int mode, int *const *dst)
@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(1024) k_scan(Launch L, int mode, int *const *d
             I.chunk_base[out][nt] = s_carry2;
             if (s_carry > I.cap || s_carry2 > I.chunk_cap) atomicOr(I.err, kErrCapacity);
             *I.cur = out;
+            *I.phase += 1;  // one more particle phase (the ion current read the old count)
         } else {
             dst[blockIdx.x][nt] = s_carry;
         }
@@ -97,8 +98,7 @@ __global__ void __launch_bounds__(256) k_readout(Launch L, const int *const *sta
     const int t = g - L.tile_start[ii];
     const int cur = *I.cur;
     const int tx = t % I.nt[0], ty = (t / I.nt[0]) % I.nt[1], tz = t / (I.nt[0] * I.nt[1]);
-    if (threadIdx.x == 0) build_sources(I, cur, tx, ty, tz, S);
-    __syncthreads();
+    build_sources(I, cur, tx, ty, tz, S);
     const int dst0 = start[ii][t];
     for (int p = threadIdx.x; p < S.count; p += blockDim.x) {
         const int pos = slot_position(I, cur, S, p);
@@ -267,7 +267,9 @@ cudaError_t launch_rho(int order, int fp64, const Launch &L, double *rho, cudaSt
         if (fp64) k_rho<2, double><<<L.total_tiles, 256, 0, s>>>(L, rho);
         else k_rho<2, float><<<L.total_tiles, 256, 0, s>>>(L, rho);
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    // plus the ion background of a lab-frame plasma (no-op without one)
+    return e == cudaSuccess ? launch_rho_ion(L, L.total_cells, rho, s) : e;
 }
 
 }  // namespace pic

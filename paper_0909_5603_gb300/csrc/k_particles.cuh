@@ -27,17 +27,50 @@ constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 // move into it, in ascending source-tile order (so the concatenation is the stable
 // order of the previous array).
 // -------------------------------------------------------------------------------------
+constexpr int kMaxSub = 512;  // sub-ranges cached in shared memory per destination tile
+
 struct SrcTable {
-    int n;
-    int count;         // sum of the sources
+    int n;                      // sources (<= 27), ascending source tile
+    int count;                  // particles moving into the tile
     int tile[kDirs];
     int dir[kDirs];
-    int pre[kDirs + 1];
-    int seg[kDirs];    // segment start of the source tile
-    int c0[kDirs];     // first chunk record of the source tile
-    int nch[kDirs];    // chunks of the source tile
-    int pos0[kDirs];   // direct start position when the source has one chunk
+    int pre[kDirs + 1];         // prefix of the sources' particle counts
+    int seg[kDirs];             // segment start of the source tile
+    int c0[kDirs];              // first chunk record of the source tile
+    int nch[kDirs];             // chunks of the source tile
+    int chpre[kDirs + 1];       // prefix of nch: (source, chunk) pair index space
+    int nsub;                   // non-empty (source, chunk) sub-ranges, -1 if > kMaxSub
+    int sub_slot[kMaxSub + 1];  // first destination slot of each sub-range, then count
+    int sub_pos[kMaxSub];       // buffer position of each sub-range's first particle
+    int warp_tmp[2][32];        // two scans back to back need separate warp totals
 };
+
+// Block-wide exclusive scan of one int per thread (blockDim a multiple of 32, at most
+// 1024); returns the exclusive prefix, *total the sum.  Contains two __syncthreads.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *tmp, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < nw ? tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        tmp[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    *total = tmp[nw - 1];
+    return (warp ? tmp[warp - 1] : 0) + x - v;
+}
 
 // Valid (direction, source coordinate) pairs along one axis for destination coordinate
 // T, sorted by source coordinate.  Returns how many.
@@ -95,60 +128,123 @@ __device__ __forceinline__ int axis_dir(int told, int tnew, int nt, int bc)
     return -1;           // d == nt - 1 with nt >= 3
 }
 
-// Built by one thread (thread 0) of the CTA.  `lay` = layout holding the source tiles.
+// Built by the whole CTA (every thread must call it).  `lay` = layout holding the source
+// tiles.  Ends with the table complete and visible to all threads.
 static __device__ void build_sources(const InstDev &I, int lay, int tx, int ty, int tz, SrcTable &S)
 {
-    int dx[3], sx[3], dy[3], sy[3], dz[3], sz[3];
-    const int mx = axis_sources(tx, I.nt[0], I.bc[0], dx, sx);
-    const int my = I.ndim == 3 ? axis_sources(ty, I.nt[1], I.bc[1], dy, sy) : 1;
-    if (I.ndim != 3) { dy[0] = 0; sy[0] = 0; }
-    const int mz = axis_sources(tz, I.nt[2], I.bc[2], dz, sz);
-    int n = 0, acc = 0;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int *seg = I.seg[lay];
     const int *cbase = I.chunk_base[lay];
     const int *tot = I.tot[lay];
     const int *pre = I.chunk_pre[lay];
-    for (int a = 0; a < mz; ++a)
-        for (int b = 0; b < my; ++b)
-            for (int c = 0; c < mx; ++c) {
-                const int st = sx[c] + I.nt[0] * (sy[b] + I.nt[1] * sz[a]);
-                const int d = (dz[a] + 1) * 9 + (dy[b] + 1) * 3 + (dx[c] + 1);
-                const int cnt = tot[st * kBuckets + d];
-                S.tile[n] = st;
-                S.dir[n] = d;
-                S.pre[n] = acc;
-                S.seg[n] = seg[st];
-                S.c0[n] = cbase[st];
-                S.nch[n] = cbase[st + 1] - cbase[st];
-                S.pos0[n] = S.nch[n] == 1 ? seg[st] + pre[cbase[st] * kPre + d] : -1;
-                acc += cnt;
-                ++n;
+    if (tid < 32) {
+        int dx[3], sx[3], dy[3], sy[3], dz[3], sz[3];
+        const int mx = axis_sources(tx, I.nt[0], I.bc[0], dx, sx);
+        const int my = I.ndim == 3 ? axis_sources(ty, I.nt[1], I.bc[1], dy, sy) : 1;
+        if (I.ndim != 3) { dy[0] = 0; sy[0] = 0; }
+        const int mz = axis_sources(tz, I.nt[2], I.bc[2], dz, sz);
+        const int n = mx * my * mz;
+        int cnt = 0, nch = 0;
+        if (lane < n) {
+            const int c = lane % mx, b = (lane / mx) % my, a = lane / (mx * my);
+            const int st = sx[c] + I.nt[0] * (sy[b] + I.nt[1] * sz[a]);
+            const int d = (dz[a] + 1) * 9 + (dy[b] + 1) * 3 + (dx[c] + 1);
+            cnt = tot[st * kBuckets + d];
+            const int c0 = cbase[st];
+            nch = cbase[st + 1] - c0;
+            S.tile[lane] = st;
+            S.dir[lane] = d;
+            S.seg[lane] = seg[st];
+            S.c0[lane] = c0;
+            S.nch[lane] = nch;
+        }
+        int pc = cnt, pn = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int yc = __shfl_up_sync(0xffffffffu, pc, o);
+            const int yn = __shfl_up_sync(0xffffffffu, pn, o);
+            if (lane >= o) { pc += yc; pn += yn; }
+        }
+        if (lane < n) {
+            S.pre[lane] = pc - cnt;
+            S.chpre[lane] = pn - nch;
+        }
+        if (lane == n - 1) {
+            S.pre[n] = pc;
+            S.chpre[n] = pn;
+            S.count = pc;
+            S.n = n;
+        }
+    }
+    __syncthreads();
+    // (source, chunk) pairs -> non-empty sub-ranges, in source then chunk order
+    const int npairs = S.chpre[S.n];
+    int written = 0;  // sub-ranges so far (uniform)
+    int slot_run = 0; // destination slots so far (uniform)
+    bool fits = true;
+    for (int q0 = 0; q0 < npairs; q0 += blockDim.x) {
+        const int q = q0 + tid;
+        int cntq = 0, posq = 0;
+        if (q < npairs) {
+            int s = 0, top = S.n - 1;
+            while (s < top) {
+                const int mid = (s + top + 1) >> 1;
+                if (S.chpre[mid] <= q) s = mid; else top = mid - 1;
             }
-    S.n = n;
-    S.pre[n] = acc;
-    S.count = acc;
+            const int k = q - S.chpre[s];
+            const long long c = S.c0[s] + k;
+            const int d = S.dir[s];
+            const int p0 = pre[c * kPre + d];
+            cntq = pre[c * kPre + d + 1] - p0;
+            posq = S.seg[s] + k * I.R + p0;
+        }
+        int tot_cnt, tot_ne;
+        const int ex_cnt = block_exclusive_scan(cntq, S.warp_tmp[0], &tot_cnt);
+        const int ne = cntq > 0 ? 1 : 0;
+        const int ex_ne = block_exclusive_scan(ne, S.warp_tmp[1], &tot_ne);
+        if (written + tot_ne > kMaxSub) fits = false;
+        if (fits && ne) {
+            S.sub_slot[written + ex_ne] = slot_run + ex_cnt;
+            S.sub_pos[written + ex_ne] = posq;
+        }
+        written += tot_ne;
+        slot_run += tot_cnt;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        S.nsub = fits ? written : -1;
+        if (fits) S.sub_slot[written] = slot_run;
+    }
+    __syncthreads();
 }
 
 // Buffer position of slot p (0 <= p < S.count) of the destination tile.
 __device__ __forceinline__ int slot_position(const InstDev &I, int lay, const SrcTable &S, int p)
 {
-    // the last source whose prefix is <= p (empty sources share their successor's prefix)
+    if (S.nsub >= 0) {
+        // the last sub-range starting at or before p
+        int e = 0, top = S.nsub - 1;
+        while (e < top) {
+            const int mid = (e + top + 1) >> 1;
+            if (S.sub_slot[mid] <= p) e = mid; else top = mid - 1;
+        }
+        return S.sub_pos[e] + (p - S.sub_slot[e]);
+    }
+    // too many sub-ranges to cache: search the source, then its chunk records
     int s = 0, top = S.n - 1;
     while (s < top) {
         const int mid = (s + top + 1) >> 1;
         if (S.pre[mid] <= p) s = mid; else top = mid - 1;
     }
     const int j = p - S.pre[s];
-    if (S.pos0[s] >= 0) return S.pos0[s] + j;
-    // several chunks: the last chunk whose earlier-chunks count of this bucket is <= j
     const int d = S.dir[s];
     const int *cb = I.chunk_cb[lay];
     int lo = 0, hi = S.nch[s] - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (cb[(S.c0[s] + mid) * kBuckets + d] <= j) lo = mid; else hi = mid - 1;
+        if (cb[(long long)(S.c0[s] + mid) * kBuckets + d] <= j) lo = mid; else hi = mid - 1;
     }
-    const int c = S.c0[s] + lo;
+    const long long c = S.c0[s] + lo;
     return S.seg[s] + lo * I.R + I.chunk_pre[lay][c * kPre + d] + (j - cb[c * kBuckets + d]);
 }
 
@@ -244,7 +340,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     __shared__ SrcTable S;
     __shared__ uint64_t bar;
     __shared__ int s_base[kBuckets], s_run[kBuckets];
-    __shared__ int s_cnt[kNW][kBuckets];
+    __shared__ int s_cnt[2][kNW][kBuckets];  // double-buffered per chunk
 
     const int g = blockIdx.x;
     const int ii = find_instance(L.tile_start, L.ninst, g);
@@ -295,11 +391,11 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
         const int z = T0[2] + I.box_lo[2] + I.gh[2];
         for (int c = 0; c < 6; ++c)
             tma_load_3d(sbase + c * box_stride, I.tmap + c, x, y, z, &bar);
-        build_sources(I, in, tx, ty, tz, S);
     }
     for (int e = tid; e < 6 * jvol; e += kNT) sJH[e] = 0;  // zeroes the FP64 tile too
+    for (int e = tid; e < 2 * kNW * kBuckets; e += kNT) (&s_cnt[0][0][0])[e] = 0;
     if (tid < kBuckets) s_run[tid] = 0;
-    __syncthreads();
+    build_sources(I, in, tx, ty, tz, S);  // ends with __syncthreads
     const bool ok = mbar_wait_bounded(&bar, 0, kWaitCycles);
     if (!__syncthreads_and(ok ? 1 : 0)) {
         if (tid == 0) {
@@ -336,7 +432,6 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     int *id_out = I.id[out];
 
     for (int base = 0, r = 0; base < count; base += kChunk, ++r) {
-        for (int e = tid; e < kNW * kBuckets; e += kNT) (&s_cnt[0][0])[e] = 0;
         int bucket = 28;  // 0..26 direction, 27 dead, 28 no particle
         int cell_new = 0, pid = 0;
         R o1[3] = {R(0), R(0), R(0)}, u[3] = {R(0), R(0), R(0)}, w = R(0);
@@ -405,15 +500,18 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             bool bad = false;
             o1[0] = o[0]; o1[1] = o[1]; o1[2] = o[2];
             int kstep[3] = {0, 0, 0};
+            R disp[3] = {R(0), R(0), R(0)};
             R vy;
             if (sizeof(R) == 4) {
                 const float gn = sqrtf(1.f + (float)u[0] * (float)u[0] + (float)u[1] * (float)u[1] + (float)u[2] * (float)u[2]);
                 const float ig = 1.f / gn;
                 float ox = (float)o1[0], oy = (float)o1[1], oz = (float)o1[2];
-                kstep[0] = move_axis(ox, (float)u[0], ig, (float)dtdx[0], bad);
-                if (ND == 3) kstep[1] = move_axis(oy, (float)u[1], ig, (float)dtdx[1], bad);
-                kstep[2] = move_axis(oz, (float)u[2], ig, (float)dtdx[2], bad);
+                float d[3] = {0.f, 0.f, 0.f};
+                kstep[0] = move_axis(ox, (float)u[0], ig, (float)dtdx[0], d[0], bad);
+                if (ND == 3) kstep[1] = move_axis(oy, (float)u[1], ig, (float)dtdx[1], d[1], bad);
+                kstep[2] = move_axis(oz, (float)u[2], ig, (float)dtdx[2], d[2], bad);
                 o1[0] = R(ox); o1[1] = R(oy); o1[2] = R(oz);
+                disp[0] = R(d[0]); disp[1] = R(d[1]); disp[2] = R(d[2]);
                 vy = R((float)u[1] * ig);
             } else {
                 const double gn = gamma_of((double)u[0], (double)u[1], (double)u[2]);
@@ -428,6 +526,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
                 atomicOr(I.err, kErrSpeed);
                 o1[0] = o[0]; o1[1] = o[1]; o1[2] = o[2];
                 kstep[0] = kstep[1] = kstep[2] = 0;
+                disp[0] = disp[1] = disp[2] = R(0);
             }
 
             // ---- Esirkepov deposit into the shared J tile
@@ -435,12 +534,13 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
                 const int l1[3] = {l[0] + kstep[0], l[1] + kstep[1], l[2] + kstep[2]};
                 const R qw = qdv * w;
                 const R fx = -qw * jfx, fy = ND == 3 ? -qw * jfy : qw * vy, fz = -qw * jfz;
+                // FP32: the current follows the computed displacement (see shape_window)
                 if (kFixed)
-                    deposit_esirkepov<ND, ORD, R>(l, o, l1, o1, fx, fy, fz, I.jlo, jlo_y, jd0, jd01, jvol,
-                                                  FixedAcc{sJH, sJL});
+                    deposit_esirkepov<ND, ORD, true, R>(l, o, l1, o1, disp, fx, fy, fz, I.jlo, jlo_y, jd0, jd01,
+                                                        jvol, FixedAcc{sJH, sJL});
                 else
-                    deposit_esirkepov<ND, ORD, R>(l, o, l1, o1, fx, fy, fz, I.jlo, jlo_y, jd0, jd01, jvol,
-                                                  DoubleAcc{sJD});
+                    deposit_esirkepov<ND, ORD, false, R>(l, o, l1, o1, disp, fx, fy, fz, I.jlo, jlo_y, jd0, jd01,
+                                                         jvol, DoubleAcc{sJD});
             }
 
             // ---- new cell, destination tile, bucket
@@ -467,42 +567,46 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             cell_new = cn[0] + I.n[0] * (cn[1] + I.n[1] * cn[2]);
         }
 
-        // ---- stable ranking of the chunk by bucket: order (warp, lane)
+        // ---- stable ranking of the chunk by bucket: order (warp, lane).  s_cnt[cb] was
+        // cleared during the previous chunk (or at the start); two barriers per chunk.
+        const int cbuf = r & 1;
         const unsigned peers = __match_any_sync(0xffffffffu, bucket);
         const int rank = __popc(peers & ((1u << lane) - 1u));
-        __syncthreads();  // s_cnt cleared by every thread before any leader writes
-        if (bucket < kBuckets && lane == __ffs(peers) - 1) s_cnt[warp][bucket] = __popc(peers);
+        if (bucket < kBuckets && lane == __ffs(peers) - 1) s_cnt[cbuf][warp][bucket] = __popc(peers);
         __syncthreads();
-        if (tid < kBuckets) {
-            int run = 0;
-            for (int ww = 0; ww < kNW; ++ww) {
-                const int v = s_cnt[ww][tid];
-                s_cnt[ww][tid] = run;
-                run += v;
+        // every warp is past the previous chunk's reads: clear the other buffer
+        for (int e = tid; e < kNW * kBuckets; e += kNT) (&s_cnt[cbuf ^ 1][0][0])[e] = 0;
+        if (warp == 0) {
+            // lane d: exclusive offsets of bucket d over the warps, then over the buckets
+            int totd = 0;
+            if (lane < kBuckets) {
+                for (int ww = 0; ww < kNW; ++ww) {
+                    const int v = s_cnt[cbuf][ww][lane];
+                    s_cnt[cbuf][ww][lane] = totd;
+                    totd += v;
+                }
             }
-            s_base[tid] = run;  // this chunk's total of the bucket, turned into a base below
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int acc = 0;
+            int incl = totd;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
             const int c = chunk_out + r;
-            int *pre = I.chunk_pre[out] + (long long)c * kPre;
-            int *cb = I.chunk_cb[out] + (long long)c * kBuckets;
-            for (int d = 0; d < kBuckets; ++d) {
-                const int tot = s_base[d];
-                s_base[d] = acc;
-                pre[d] = acc;
-                cb[d] = s_run[d];
-                s_run[d] += tot;
-                acc += tot;
+            if (lane < kBuckets) {
+                const int basev = incl - totd;
+                s_base[lane] = basev;
+                I.chunk_pre[out][(long long)c * kPre + lane] = basev;
+                I.chunk_cb[out][(long long)c * kBuckets + lane] = s_run[lane];
+                s_run[lane] += totd;
+                if (lane == kBuckets - 1) I.chunk_pre[out][(long long)c * kPre + kBuckets] = incl;
             }
-            pre[kBuckets] = acc;
         }
         __syncthreads();
 
         // ---- write the particle out, partitioned by bucket
         if (bucket < kDead) {
-            const int p = seg_out + base + s_base[bucket] + s_cnt[warp][bucket] + rank;
+            const int p = seg_out + base + s_base[bucket] + s_cnt[cbuf][warp][bucket] + rank;
             cell_out[p] = cell_new;
             off_out[0][p] = o1[0];
             if (ND == 3) off_out[1][p] = o1[1];
@@ -518,9 +622,10 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
         if (kFixed && (r + 1) % kFlushChunks == 0 && base + kChunk < count) {
             __syncthreads();
             flush_j_fixed(I, T0, ND, sJH, sJL, jvol, I.jinv, tid, kNT);
+            __syncthreads();
         }
-        __syncthreads();
     }
+    __syncthreads();  // all deposits and bucket totals complete
 
     // ---- tile bookkeeping for the next step
     if (tid < kBuckets) I.tot[out][t * kBuckets + tid] = s_run[tid];

@@ -186,7 +186,7 @@ extern "C" void pic_default_options(pic_options *o)
     o->precision = PIC_PREC_FP32;
     o->pusher = PIC_PUSHER_VAY;
     o->filter_passes = 0;
-    o->threads = 256;
+    o->threads = 0;
     o->absorb_cells = 16;
     o->absorb_strength = 0.1;
     o->charge = -1.0;
@@ -382,8 +382,9 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     c->d_start = (int *)dalloc(c, sizeof(int) * (size_t)nt1);
     c->d_start_ptr = (int **)dalloc(c, sizeof(int *));
     c->d_pencil = (long long *)dalloc(c, 6 * sizeof(long long));
+    h.ion_face = dalloc(c, sizeof(double) * (size_t)c->n[2]);
     if (!F || !small || !tiles || !tm || !c->d_inst || !c->d_tile_start || !c->d_cell_start || !c->d_dense || !c->d_sums ||
-        !c->d_start || !c->d_start_ptr || !c->d_pencil) {
+        !c->d_start || !c->d_start_ptr || !c->d_pencil || !h.ion_face) {
         dfree_all(c);
         delete c;
         return fail(nullptr, PIC_ERR_OOM, "device allocation failed (%zu bytes of fields)", fbytes);
@@ -399,6 +400,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     h.live = small + 2;
     h.jsel = small + 3;
     h.lost = (unsigned long long *)(small + 4);
+    h.phase = small + 6;
     h.seg[0] = tiles;
     h.seg[1] = tiles + nt1;
     h.chunk_base[0] = tiles + 2 * nt1;
@@ -662,9 +664,11 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
         h.jscale = bound > 0.0 ? (float)std::ldexp(1.0, 20 - e) : 1.0f;
         h.jinv = bound > 0.0 ? (float)std::ldexp(1.0, e - 20) : 1.0f;
     }
-    CUDA_OR_FAIL(c, cudaMemset(h.cur, 0, 16 + sizeof(unsigned long long)));
+    // cur, err, live, jsel, lost and the particle-phase counter
+    CUDA_OR_FAIL(c, cudaMemset(h.cur, 0, 16 + sizeof(unsigned long long) + sizeof(int)));
     CUDA_OR_FAIL(c, cudaMemset(h.J[0], 0, 3 * (size_t)h.cstride * c->es));
     c->loaded = true;
+    c->version++;  // a batch holding this instance re-reads its parameters
     c->step = 0;
     c->last_filtered = 0;
     destroy_graph(c);
@@ -678,6 +682,7 @@ extern "C" pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t 
     if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_load_particles on a batch");
     cudaSetDevice(ctx->device);
     CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->h.ion = 0;  // particles loaded directly carry no ion background
     return load_internal(ctx, n, cell, off3, u3, w, id);
 }
 
@@ -737,6 +742,14 @@ extern "C" pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *lase
         if ((st = set_field_internal(ctx, PIC_EX, Ex.data())) != PIC_OK) return st;
         if ((st = set_field_internal(ctx, PIC_BY, By.data())) != PIC_OK) return st;
     }
+    // the plasma's lab-stationary ions: a rigid background streaming at -beta_b
+    InstDev &h = ctx->h;
+    h.ion = plasma && plasma->n0 > 0.0;
+    h.ion_n0 = plasma ? plasma->n0 : 0.0;
+    h.ion_zs = plasma ? plasma->z_start : 0.0;
+    h.ion_ramp = plasma ? plasma->ramp_len : 0.0;
+    h.ion_gb = ctx->gamma_b;
+    h.ion_beta = std::sqrt(1.0 - 1.0 / (ctx->gamma_b * ctx->gamma_b));
     const int64_t np = (int64_t)P.cell.size();
     return load_internal(ctx, np, P.cell.data(), P.off.data(), P.mom.data(), P.weight.data(), P.id.data());
 }
@@ -781,6 +794,12 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
                 CUDA_OR_FAIL(c, cudaMemsetAsync(m->h.J[0], 0, 3 * (size_t)m->h.cstride * m->es, c->stream));
         } else {
             CUDA_OR_FAIL(c, cudaMemsetAsync(c->h.J[0], 0, 3 * (size_t)c->h.cstride * c->es, c->stream));
+        }
+        bool ions = c->h.ion != 0;
+        for (auto m : c->members) ions = ions || m->h.ion != 0;
+        if (ions) {
+            CUDA_OR_FAIL(c, launch_ion_current(fp64, L, c->stream));
+            launches += 2;
         }
         tm.end(4);
         tm.begin(1);

@@ -58,8 +58,17 @@ __device__ __forceinline__ int shape_stag(int l, R o, R w[ORD + 1])
 // with d -- e.g. for order 2 the centre weight gives (3/4 - f1^2) - (3/4 - f0^2) =
 // -d (f0 + f1) -- instead of subtracting two O(1) weights, which in FP32 would lose the
 // small displacement to cancellation.  Entries at and beyond nw are zero.
-template <int ORD, typename R>
-__device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R S0[ORD + 2], R DS[ORD + 2], int &nw)
+//
+// kDisp: take d as `disp`, the displacement the push computed, instead of f1 - f0.  The
+// two differ by the rounding of the stored new offset (at most half an ulp of it): with
+// FP32 offsets that rounding is ~3e-8 of a cell, i.e. a relative current error of
+// 3e-8 / d, 6e-6 for a thermal particle moving 0.005 cells per step.  Taking the computed
+// displacement keeps J at FP32 precision relative to the motion; the rounding then
+// appears only as a charge-conservation residual of at most half an ulp times the shape
+// slope per particle and step.
+template <int ORD, bool kDisp, typename R>
+__device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R disp, R S0[ORD + 2], R DS[ORD + 2],
+                                            int &nw)
 {
     R w0[ORD + 1], w1[ORD + 1];
     const int b0 = shape_nodal<ORD>(l0, o0, w0);
@@ -67,7 +76,7 @@ __device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R S0[ORD
     if (b0 == b1) {
         const R f0 = o0 - R(b0 - l0 + (ORD == 2 ? 1 : 0));
         const R f1 = o1 - R(b1 - l1 + (ORD == 2 ? 1 : 0));
-        const R d = f1 - f0;
+        const R d = kDisp ? disp : f1 - f0;
 #pragma unroll
         for (int i = 0; i <= ORD; ++i) S0[i] = w0[i];
         S0[ORD + 1] = R(0);
@@ -75,10 +84,12 @@ __device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R S0[ORD
             DS[0] = -d;
             DS[1] = d;
         } else {
-            const R s = f0 + f1;
+            const R s = kDisp ? f0 + f0 + d : f0 + f1;
             DS[0] = R(-0.5) * d * (R(1) - s);
             DS[1] = -d * s;
-            DS[2] = R(0.5) * d * (R(1) + s);
+            // = d (1 + s) / 2, taken as -(DS[0] + DS[1]) so the running sum over the
+            // window ends at exactly zero
+            DS[2] = -(DS[0] + DS[1]);
         }
         DS[ORD + 1] = R(0);
         nw = ORD + 1;
@@ -144,35 +155,33 @@ struct DoubleAcc {
 //   Jx(i+1/2) - Jx(i-1/2) = f_x Wx(i),  f_x = -(q w / dV) dx / dt,
 // summed along x from zero at the window start; in 2D3V (x-z plane) Wx = DSx (S0z + DSz/2),
 // Wz = DSz (S0x + DSx/2) and the out-of-plane Jy = f_y' (S0x S0z + DSx S0z / 2 +
-// S0x DSz / 2 + DSx DSz / 3) with f_y' = (q w / dV) v_y.  Only the nw window nodes that
-// can be non-zero are visited; the running sum vanishes at the last node of the window.
+// S0x DSz / 2 + DSx DSz / 3) with f_y' = (q w / dV) v_y.  The loops run over the whole
+// window: entries beyond the nodes a particle touches are exactly zero (the running sum
+// ends at exactly zero too) and are skipped by the accumulator's zero test.
 // ------------------------------------------------------------------------------------
-template <int ND, int ORD, typename R, typename Acc>
-__device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3], const int l1[3], const R o1[3], R fx,
-                                                  R fy, R fz, int jlo, int jlo_y, int jd0, int jd01, int jvol,
-                                                  const Acc &acc)
+template <int ND, int ORD, bool kDisp, typename R, typename Acc>
+__device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3], const int l1[3], const R o1[3],
+                                                  const R disp[3], R fx, R fy, R fz, int jlo, int jlo_y, int jd0,
+                                                  int jd01, int jvol, const Acc &acc)
 {
     constexpr int W = ORD + 2;
     R S0x[W], DSx[W], S0y[W], DSy[W], S0z[W], DSz[W];
     int nwx, nwy = 1, nwz;
-    const int wsx = shape_window<ORD>(l0[0], o0[0], l1[0], o1[0], S0x, DSx, nwx) - jlo;
-    const int wsz = shape_window<ORD>(l0[2], o0[2], l1[2], o1[2], S0z, DSz, nwz) - jlo;
+    const int wsx = shape_window<ORD, kDisp>(l0[0], o0[0], l1[0], o1[0], disp[0], S0x, DSx, nwx) - jlo;
+    const int wsz = shape_window<ORD, kDisp>(l0[2], o0[2], l1[2], o1[2], disp[2], S0z, DSz, nwz) - jlo;
     const R half = R(0.5), third = R(1.0 / 3.0);
     if (ND == 3) {
-        const int wsy = shape_window<ORD>(l0[1], o0[1], l1[1], o1[1], S0y, DSy, nwy) - jlo_y;
+        const int wsy = shape_window<ORD, kDisp>(l0[1], o0[1], l1[1], o1[1], disp[1], S0y, DSy, nwy) - jlo_y;
         const int base = wsx + jd0 * wsy + jd01 * wsz;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            if (k >= nwz) break;
 #pragma unroll
             for (int j = 0; j < W; ++j) {
-                if (j >= nwy) break;
                 const R Y = S0y[j] * S0z[k] + half * (DSy[j] * S0z[k] + S0y[j] * DSz[k]) + third * DSy[j] * DSz[k];
                 const R fY = fx * Y;
                 R run = R(0);
 #pragma unroll
                 for (int i = 0; i < W - 1; ++i) {
-                    if (i >= nwx - 1) break;
                     run += DSx[i];
                     const R v = fY * run;
                     if (v != R(0)) acc.add(base + i + jd0 * j + jd01 * k, v);
@@ -181,16 +190,13 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
         }
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            if (k >= nwz) break;
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                if (i >= nwx) break;
                 const R X = S0x[i] * S0z[k] + half * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) + third * DSx[i] * DSz[k];
                 const R fX = fy * X;
                 R run = R(0);
 #pragma unroll
                 for (int j = 0; j < W - 1; ++j) {
-                    if (j >= nwy - 1) break;
                     run += DSy[j];
                     const R v = fX * run;
                     if (v != R(0)) acc.add(jvol + base + i + jd0 * j + jd01 * k, v);
@@ -199,16 +205,13 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
         }
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-            if (j >= nwy) break;
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                if (i >= nwx) break;
                 const R X = S0x[i] * S0y[j] + half * (DSx[i] * S0y[j] + S0x[i] * DSy[j]) + third * DSx[i] * DSy[j];
                 const R fX = fz * X;
                 R run = R(0);
 #pragma unroll
                 for (int k = 0; k < W - 1; ++k) {
-                    if (k >= nwz - 1) break;
                     run += DSz[k];
                     const R v = fX * run;
                     if (v != R(0)) acc.add(2 * jvol + base + i + jd0 * j + jd01 * k, v);
@@ -220,12 +223,10 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
         const int base = wsx + jd01 * wsz;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            if (k >= nwz) break;
             const R fY = fx * (S0z[k] + half * DSz[k]);
             R run = R(0);
 #pragma unroll
             for (int i = 0; i < W - 1; ++i) {
-                if (i >= nwx - 1) break;
                 run += DSx[i];
                 const R v = fY * run;
                 if (v != R(0)) acc.add(base + i + jd01 * k, v);
@@ -233,12 +234,10 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
         }
 #pragma unroll
         for (int i = 0; i < W; ++i) {
-            if (i >= nwx) break;
             const R fX = fz * (S0x[i] + half * DSx[i]);
             R run = R(0);
 #pragma unroll
             for (int k = 0; k < W - 1; ++k) {
-                if (k >= nwz - 1) break;
                 run += DSz[k];
                 const R v = fX * run;
                 if (v != R(0)) acc.add(2 * jvol + base + i + jd01 * k, v);
@@ -246,10 +245,8 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
         }
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            if (k >= nwz) break;
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                if (i >= nwx) break;
                 const R v = fy * (S0x[i] * S0z[k] + half * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) + third * DSx[i] * DSz[k]);
                 if (v != R(0)) acc.add(jvol + base + i + jd01 * k, v);
             }
@@ -343,9 +340,10 @@ __device__ __forceinline__ void push_boris(R u[3], const R E[3], const R B[3], R
 // outside (-1, 2) (impossible below the Courant limit unless values are not finite)
 // leaves the particle in place and sets *bad.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ int move_axis(float &o, float u, float ig, float dt_dx, bool &bad)
+__device__ __forceinline__ int move_axis(float &o, float u, float ig, float dt_dx, float &disp, bool &bad)
 {
-    float x = __fadd_rn(o, __fmul_rn(dt_dx, __fmul_rn(u, ig)));
+    disp = __fmul_rn(dt_dx, __fmul_rn(u, ig));
+    float x = __fadd_rn(o, disp);
     if (!(x > -1.f && x < 2.f)) {
         bad = true;
         return 0;

@@ -92,6 +92,12 @@ struct InstDev {
                               // (working precision; null on periodic / inactive axes)
     FastDiv div_n0, div_n1;   // cell index -> (i, j, k)
     float jscale, jinv;       // FP32 fixed-point current: scale (a power of two) and 1/scale
+    // ion background of a lab-frame plasma load: lab-stationary ions, i.e. in this frame
+    // a rigid density gamma_b n0 p(gamma_b (z + beta_b t)) of charge -q on [0, Lz) at t = 0
+    int ion;            // 0: none
+    double ion_n0, ion_zs, ion_ramp, ion_gb, ion_beta;
+    void *ion_face;     // [n[2]] this step's ion current on the Jz faces (working precision)
+    int *phase;         // particle phases run since the last load (device counter)
     int box[3];         // TMA box extents (elements)
     int box_lo[3];      // box origin relative to the tile origin (cells, <= 0)
     int jlo;            // J tile origin relative to the tile origin (-1 or -2)
@@ -129,6 +135,8 @@ __device__ __forceinline__ int find_instance_ll(const long long *start, int nins
 }
 
 // host-side launchers
+cudaError_t launch_ion_current(int fp64, const Launch &L, cudaStream_t s);
+cudaError_t launch_rho_ion(const Launch &L, long long ncell, double *rho, cudaStream_t s);
 cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, const Launch &L, size_t smem, cudaStream_t s);
 int particle_chunk();
 int particle_threads();

@@ -60,3 +60,25 @@ def smooth_fields(n, ndim, amp, seed, modes=3):
             f += rng.normal() * np.cos(2 * np.pi * (m[0] * i / n[0] + m[1] * j / n[1] + m[2] * k / n[2]) + ph)
         out.append(f32(amp * f))
     return out
+
+
+def lwfa_stage(n=(128, 128, 1024), gamma_boost=13.0, ppc=2, seed=3, lambda0=1.0):
+    """Lab-frame inputs of the boosted laser-wakefield stage (normalised units, c = 1):
+    plasma at n/n_c = 1/900 behind a linear up-ramp two boosted cells long (in lab length,
+    2 dz gamma_b), Gaussian laser a0 = 2, waist 20 lambda0, 10 periods long, centred two
+    durations ahead of the plasma.  The boosted grid resolves the Doppler-stretched laser
+    wavelength gamma_b (1 + beta_b) lambda0 with 16 cells; transverse cells are 2 lambda0
+    (10 across the waist); dt = dz / 2, capped at 0.9 of the 3D Yee Courant limit (the cap
+    binds from gamma_b ~ 25 on, where dz outgrows the transverse cells).  Returns the grid
+    and the tuples that Simulation.load_lab_frame takes."""
+    b = np.sqrt(1.0 - 1.0 / gamma_boost ** 2)
+    dz = gamma_boost * (1.0 + b) * lambda0 / 16.0
+    dx = 2.0 * lambda0
+    k0 = 2.0 * np.pi / lambda0
+    n_c = k0 * k0  # critical density for q = m = eps0 = c = 1
+    duration = 10.0 * lambda0
+    laser = (2.0, lambda0, 20.0 * lambda0, duration, 2.0 * duration)
+    plasma = (n_c / 900.0, 0.0, 2.0 * dz * gamma_boost, ppc, (0.0, 0.0, 0.0), seed)
+    courant = 1.0 / np.sqrt(2.0 / dx ** 2 + 1.0 / dz ** 2)
+    dt = min(0.5 * dz, 0.9 * courant)
+    return dict(n=tuple(n), dx=(dx, dx, dz), dt=dt, gamma_boost=gamma_boost, laser=laser, plasma=plasma)
