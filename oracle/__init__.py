@@ -101,6 +101,8 @@ def lib():
         L.orc_diagnostics.argtypes = [vp, _f64p]
         L.orc_load_lab_frame.restype = ctypes.c_int
         L.orc_load_lab_frame.argtypes = [vp, ctypes.c_double, vp, vp, vp]
+        L.orc_beam_self_field.restype = ctypes.c_int
+        L.orc_beam_self_field.argtypes = [vp, _f64p, ctypes.c_double, ctypes.c_double]
         L.orc_ion_integral.restype = ctypes.c_double
         L.orc_ion_integral.argtypes = [vp, ctypes.c_double, ctypes.c_double]
         _lib = L
@@ -229,6 +231,11 @@ class Sim:
         out = np.zeros(self.ncell)
         lib().orc_rho(self._h, out)
         return out.reshape(self.n[2], self.n[1], self.n[0])
+
+    def beam_self_field(self, rho, gamma, beta):
+        """Adds the self-field of node charge density rho (n2, n1, n0) moving at beta z."""
+        r = np.ascontiguousarray(np.asarray(rho, np.float64).ravel())
+        lib().orc_beam_self_field(self._h, r, float(gamma), float(beta))
 
     def ion_integral(self, a, b):
         """Ion-background charge between box coordinates a < b at t' = 0 (per unit area)."""

@@ -818,11 +818,10 @@ void orc_step(orc_sim *s, int nsteps)
 /* ------------------------------------------------------------------------------------
  * Charge density on nodes: rho_ijk = sum_p (q w_p / dV) S(x_p - i) S(y_p - j) S(z_p - k).
  * ---------------------------------------------------------------------------------- */
-void orc_rho(const orc_sim *s, double *out)
+static void deposit_rho(const orc_sim *s, int64_t p0, int64_t p1, double *out)
 {
-    memset(out, 0, (size_t)s->ncell * sizeof(double));
     double dV = s->dx[0] * s->dx[1] * s->dx[2];
-    for (int64_t p = 0; p < s->np; ++p) {
+    for (int64_t p = p0; p < p1; ++p) {
         int c[3], lo[3], cnt[3];
         cell_coords(s, s->cell[p], c);
         const double *o = &s->off[3 * p];
@@ -838,6 +837,12 @@ void orc_rho(const orc_sim *s, double *out)
                     if (idx >= 0) out[idx] += s->q * s->w[p] / dV * wt;
                 }
     }
+}
+
+void orc_rho(const orc_sim *s, double *out)
+{
+    memset(out, 0, (size_t)s->ncell * sizeof(double));
+    deposit_rho(s, 0, s->np, out);
     if (s->ion && s->active[2]) { /* plus the ion background on its dual cells */
         double t = (double)s->n_pp * s->dt, dz = s->dx[2];
         for (int k = 0; k < s->n[2]; ++k) {
@@ -901,9 +906,137 @@ void orc_diagnostics(const orc_sim *s, double out[8])
  *   t = 0: x = xc + sigma_r N(10,11), y = yc + sigma_r N(12,13), z = z0 + sigma_z N(14,15),
  *   u = (0,0,gamma beta) + rel_spread * gamma beta * (N(16,17), N(18,19), N(20,21)),
  *   w = total_weight / n; boosted, then drifted ballistically to t' = 0; particles
- *   outside the box are dropped.
+ *   outside the box are dropped.  The beam's self-field (orc_beam_self_field) is added
+ *   to the fields, for its centroid velocity in this frame.
  * Returns the number of particles loaded.
  * ---------------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------------------
+ * Self-field of a beam moving rigidly at beta along z (the field the beam carries when
+ * it enters, so that the field it applies to itself is the one Sec. 2 discusses: a
+ * radial E almost cancelled by the azimuthal B).  For a charge density rho moving
+ * rigidly at v = beta z, the Lorenz-gauge potentials are phi and A = beta phi z, with
+ *   d2phi/dx2 + d2phi/dy2 + (1/gamma^2) d2phi/dz2 = -rho,
+ *   E = (-dphi/dx, -dphi/dy, -(1/gamma^2) dphi/dz),   B = curl A = beta z x E.
+ * Discretely: rho on the nodes (the particles' shape, as orc_rho), the 3- / 5- / 7-point
+ * second differences on the nodes (phi = 0 one node beyond an absorbing face, wrap on a
+ * periodic axis), E as the Yee differences of phi, and B_x = -beta E_y, B_y = beta E_x
+ * with E averaged over the two z nodes around B's half-integer z.  The linear system is
+ * solved exactly by expanding in the eigenvectors of each axis's second difference
+ * (sines for Dirichlet, real Fourier modes for periodic); on an all-periodic grid the
+ * mean of rho is dropped (a neutralising background).
+ * ---------------------------------------------------------------------------------- */
+static void axis_modes(int n, int periodic, double dx, double *Q, double *lam)
+{
+    /* Q[m * n + i]: orthonormal eigenvector m of the second difference (1/dx^2) */
+    const double pi = 3.141592653589793;
+    for (int m = 0; m < n; ++m) {
+        double theta;
+        if (!periodic) {
+            theta = pi * (m + 1) / (n + 1);
+            for (int i = 0; i < n; ++i) Q[m * n + i] = sqrt(2.0 / (n + 1)) * sin(theta * (i + 1));
+        } else {
+            int k = (m + 1) / 2; /* m = 0: constant; then cos, sin pairs */
+            theta = 2.0 * pi * k / n;
+            for (int i = 0; i < n; ++i) {
+                if (m == 0)
+                    Q[m * n + i] = 1.0 / sqrt((double)n);
+                else if (2 * k == n)
+                    Q[m * n + i] = (i % 2 ? -1.0 : 1.0) / sqrt((double)n);
+                else if (m % 2 == 1)
+                    Q[m * n + i] = sqrt(2.0 / n) * cos(theta * i);
+                else
+                    Q[m * n + i] = sqrt(2.0 / n) * sin(theta * i);
+            }
+        }
+        lam[m] = -(2.0 - 2.0 * cos(theta)) / (dx * dx);
+    }
+}
+
+/* v <- Q v (forward, coefficients) or Q^T v (back) along axis a of an n0 x n1 x n2 array */
+static void apply_modes(const orc_sim *s, int a, const double *Q, int forward, double *v)
+{
+    int n = s->n[a];
+    double *line = (double *)malloc((size_t)n * sizeof(double));
+    double *res = (double *)malloc((size_t)n * sizeof(double));
+    int64_t stride = a == 0 ? 1 : (a == 1 ? s->n[0] : (int64_t)s->n[0] * s->n[1]);
+    for (int64_t base = 0; base < s->ncell; ++base) {
+        int c[3];
+        cell_coords(s, (int32_t)base, c);
+        if (c[a] != 0) continue; /* one line per start node */
+        for (int i = 0; i < n; ++i) line[i] = v[base + i * stride];
+        for (int m = 0; m < n; ++m) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) acc += (forward ? Q[m * n + i] * line[i] : Q[i * n + m] * line[i]);
+            res[m] = acc;
+        }
+        for (int i = 0; i < n; ++i) v[base + i * stride] = res[i];
+    }
+    free(line);
+    free(res);
+}
+
+int orc_beam_self_field(orc_sim *s, const double *rho, double gamma, double beta)
+{
+    double *phi = (double *)malloc((size_t)s->ncell * sizeof(double));
+    double *Q[3] = {NULL, NULL, NULL}, *lam[3] = {NULL, NULL, NULL};
+    int all_periodic = 1;
+    memcpy(phi, rho, (size_t)s->ncell * sizeof(double));
+    for (int a = 0; a < 3; ++a) {
+        if (!s->active[a]) continue;
+        if (s->bc[a] == ORC_ABSORBING) all_periodic = 0;
+        Q[a] = (double *)malloc((size_t)s->n[a] * s->n[a] * sizeof(double));
+        lam[a] = (double *)malloc((size_t)s->n[a] * sizeof(double));
+        axis_modes(s->n[a], s->bc[a] == ORC_PERIODIC, s->dx[a], Q[a], lam[a]);
+        apply_modes(s, a, Q[a], 1, phi);
+    }
+    for (int64_t idx = 0; idx < s->ncell; ++idx) {
+        int c[3];
+        cell_coords(s, (int32_t)idx, c);
+        double L = 0.0;
+        for (int a = 0; a < 3; ++a)
+            if (s->active[a]) L += (a == 2 ? 1.0 / (gamma * gamma) : 1.0) * lam[a][c[a]];
+        /* the (0,0,0) mode of an all-periodic grid has L = 0: dropped */
+        phi[idx] = (all_periodic && c[0] == 0 && c[1] == 0 && c[2] == 0) ? 0.0 : -phi[idx] / L;
+    }
+    for (int a = 0; a < 3; ++a)
+        if (s->active[a]) apply_modes(s, a, Q[a], 0, phi);
+    /* fields from phi (added to what is there, e.g. a laser) */
+    for (int k = 0; k < s->n[2]; ++k)
+        for (int j = 0; j < s->n[1]; ++j)
+            for (int i = 0; i < s->n[0]; ++i) {
+                int64_t id = node_index(s, i, j, k);
+                double p0 = phi[id];
+                double px = node_index(s, i + 1, j, k) < 0 ? 0.0 : phi[node_index(s, i + 1, j, k)];
+                double py = node_index(s, i, j + 1, k) < 0 ? 0.0 : phi[node_index(s, i, j + 1, k)];
+                double pz = node_index(s, i, j, k + 1) < 0 ? 0.0 : phi[node_index(s, i, j, k + 1)];
+                s->f[ORC_EX][id] += -(px - p0) / s->dx[0];
+                if (s->active[1]) s->f[ORC_EY][id] += -(py - p0) / s->dx[1];
+                s->f[ORC_EZ][id] += -(pz - p0) / (s->dx[2] * gamma * gamma);
+            }
+    /* B from the beam's E alone, averaged over the two z nodes around k + 1/2 */
+    for (int k = 0; k < s->n[2]; ++k)
+        for (int j = 0; j < s->n[1]; ++j)
+            for (int i = 0; i < s->n[0]; ++i) {
+                int64_t id = node_index(s, i, j, k);
+                double ex[2], ey[2];
+                for (int h = 0; h < 2; ++h) {
+                    int64_t c0 = node_index(s, i, j, k + h);
+                    int64_t cx = node_index(s, i + 1, j, k + h), cy = node_index(s, i, j + 1, k + h);
+                    double p0 = c0 < 0 ? 0.0 : phi[c0];
+                    ex[h] = c0 < 0 ? 0.0 : -((cx < 0 ? 0.0 : phi[cx]) - p0) / s->dx[0];
+                    ey[h] = (c0 < 0 || !s->active[1]) ? 0.0 : -((cy < 0 ? 0.0 : phi[cy]) - p0) / s->dx[1];
+                }
+                s->f[ORC_BX][id] += -beta * 0.5 * (ey[0] + ey[1]);
+                s->f[ORC_BY][id] += beta * 0.5 * (ex[0] + ex[1]);
+            }
+    for (int a = 0; a < 3; ++a) {
+        free(Q[a]);
+        free(lam[a]);
+    }
+    free(phi);
+    return 0;
+}
+
 static void append_particle(orc_sim *s, const double pos[3], const double u[3], double w, int32_t id)
 {
     int c[3];
@@ -1001,6 +1134,7 @@ int orc_load_lab_frame(orc_sim *s, double gb, const double *laser, const double 
         }
     }
     if (beam) {
+        int64_t first = s->np;
         int64_t nb = (int64_t)beam[0];
         double gam = beam[1], spread = beam[2], sr = beam[3], sz = beam[4], z0 = beam[5];
         double wb = beam[6] / (double)nb;
@@ -1019,6 +1153,16 @@ int orc_load_lab_frame(orc_sim *s, double gb, const double *laser, const double 
             double pos[3] = {txp[1] + up[0] / gp * dtp, txp[2] + up[1] / gp * dtp, txp[3] + up[2] / gp * dtp};
             if (!s->active[1]) pos[1] = 0.0;
             append_particle(s, pos, up, wb, next_id++);
+        }
+        if (s->np > first) {
+            /* the beam enters with its self-field, moving at the centroid velocity of this
+             * frame: beta' = (beta - b) / (1 - beta b), gamma' = gb gamma (1 - beta b) */
+            double bl = gb0 / gam;
+            double gp = gb * gam * (1.0 - bl * b), bp = (bl - b) / (1.0 - bl * b);
+            double *rho = (double *)calloc((size_t)s->ncell, sizeof(double));
+            deposit_rho(s, first, s->np, rho);
+            orc_beam_self_field(s, rho, gp, bp);
+            free(rho);
         }
     }
     orc_sort(s);

@@ -67,6 +67,10 @@ int orc_load_lab_frame(orc_sim *s, double gamma_b, const double *laser, const do
 /* Charge of the lab-frame plasma's ion background between box coordinates a < b at
  * t' = 0 (per unit transverse area); 0 when the last load had no plasma. */
 double orc_ion_integral(const orc_sim *s, double a, double b);
+/* Adds the self-field of the node charge density rho[n0 n1 n2] moving rigidly at beta
+ * (Lorentz factor gamma) along z: relativistic Poisson solve, E = -grad phi with the z
+ * part over gamma^2, B = beta z x E.  Returns 0. */
+int orc_beam_self_field(orc_sim *s, const double *rho, double gamma, double beta);
 
 #ifdef __cplusplus
 }
