@@ -192,7 +192,14 @@ typedef struct {
  * (wrapping when z is periodic, leaving through the -z face when absorbing).  Every
  * step adds their current on the Jz faces -- the charge of the profile crossing each
  * face during the step, over dt -- and PIC_RHO adds their charge on each node's dual
- * cell, so div E - rho stays constant for the ions too. */
+ * cell, so div E - rho stays constant for the ions too.
+ * Beam self-field: a beam enters with the field of its own charge moving rigidly at its
+ * centroid velocity in this frame (beta', gamma'), the field whose action on the beam
+ * itself Sec. 2 discusses: phi from phi_xx + phi_yy + phi_zz / gamma'^2 = -rho (rho on
+ * the nodes with the particle shape; phi = 0 one node beyond absorbing faces, periodic
+ * axes wrap; on an all-periodic grid the mean charge is dropped), solved exactly on the
+ * host in FP64; E = -(phi_x, phi_y, phi_z / gamma'^2) at the Yee positions and
+ * B = beta' z x E (E averaged over the two z nodes around B's half-integer z). */
 pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *laser, const pic_plasma_lab *plasma,
                               const pic_beam_lab *beam);
 

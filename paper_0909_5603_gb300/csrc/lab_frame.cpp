@@ -1,7 +1,8 @@
 // lab_frame.cpp -- host FP64 transformation of laboratory-frame inputs into the boosted
 // frame (Sec. 2 of Vay et al., arXiv:0909.5603): the laser is Doppler-shifted, the
 // plasma becomes denser and drifts, beam particles are boosted and then drifted
-// ballistically to a common boosted time ("frozen" drifting macro-particles).
+// ballistically to a common boosted time ("frozen" drifting macro-particles) and bring
+// their self-field (beam_field.cpp).
 //
 // Random draws use SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) as a counter-based
 // generator: value(seed, stream, counter) = finaliser(seed ^ stream << 40 ^ counter +
@@ -84,7 +85,7 @@ void LabParticles::add(const Geometry &G, const double pos[3], const double u[3]
 }
 
 void transform_lab_inputs(const Geometry &G, double gamma_b, const pic_laser_lab *laser, const pic_plasma_lab *plasma,
-                          const pic_beam_lab *beam, LabParticles &P, std::vector<double> &Ex, std::vector<double> &By)
+                          const pic_beam_lab *beam, LabParticles &P, LabFields &F)
 {
     const Boost bst(gamma_b);
     const double doppler = bst.g * (1.0 + bst.b);
@@ -92,6 +93,8 @@ void transform_lab_inputs(const Geometry &G, double gamma_b, const pic_laser_lab
     const double xc = 0.5 * (G.n[0] * G.dx[0]);
     const double yc = has_y ? 0.5 * (G.n[1] * G.dx[1]) : 0.0;
     const long long ncell = (long long)G.n[0] * G.n[1] * G.n[2];
+    for (auto &c : F.comp) c.clear();
+    std::vector<double> &Ex = F.comp[0], &By = F.comp[4];
     Ex.assign(laser ? ncell : 0, 0.0);
     By.assign(laser ? ncell : 0, 0.0);
 
@@ -153,6 +156,7 @@ void transform_lab_inputs(const Geometry &G, double gamma_b, const pic_laser_lab
         }
     }
     if (beam) {
+        const size_t first = P.cell.size();
         const Rng rng{beam->seed};
         const double g0 = std::sqrt(beam->gamma * beam->gamma - 1.0);
         const double wb = beam->total_weight / (double)beam->n;
@@ -170,6 +174,16 @@ void transform_lab_inputs(const Geometry &G, double gamma_b, const pic_laser_lab
             double pos[3] = {evp[1] + up[0] / gp * back, evp[2] + up[1] / gp * back, evp[3] + up[2] / gp * back};
             if (!has_y) pos[1] = 0.0;
             P.add(G, pos, up, wb, next_id++);
+        }
+        if (P.cell.size() > first) {
+            // the beam's self-field for its centroid velocity in this frame:
+            // rapidities subtract, gamma' = gb gamma (1 - beta b)
+            const double bl = g0 / beam->gamma;
+            const double gp = bst.g * beam->gamma * (1.0 - bl * bst.b);
+            const double bp = (bl - bst.b) / (1.0 - bl * bst.b);
+            std::vector<double> rho;
+            deposit_node_charge(G, P, first, rho);
+            add_beam_self_field(G, rho, gp, bp, F);
         }
     }
 }

@@ -13,6 +13,15 @@ struct Geometry {
     int ndim;
     int n[3];
     double dx[3];
+    int bc[3] = {PIC_PERIODIC, PIC_PERIODIC, PIC_PERIODIC};
+    int order = 1;        // particle shape order (charge deposit for the beam field)
+    double charge = -1.0; // macro-particle charge per unit weight
+};
+
+// Boosted-frame fields at t' = 0 set by a load: Ex Ey Ez Bx By Bz, each n0*n1*n2 values
+// (x fastest) or empty when zero.
+struct LabFields {
+    std::vector<double> comp[6];
 };
 
 // Particles in FP64 as produced by the transform (cell index, offsets, momenta: 3 per
@@ -32,9 +41,16 @@ struct LabParticles {
     void add(const Geometry &G, const double pos[3], const double u[3], double w, int32_t idv);
 };
 
-// Fills P with the plasma and beam macro-particles and Ex / By (n0*n1*n2, empty without
-// a laser) with the boosted-frame laser at t' = 0.
+// Fills P with the plasma and beam macro-particles and F with the boosted-frame laser
+// (Ex, By) plus the beam's self-field at t' = 0.
 void transform_lab_inputs(const Geometry &G, double gamma_b, const pic_laser_lab *laser, const pic_plasma_lab *plasma,
-                          const pic_beam_lab *beam, LabParticles &P, std::vector<double> &Ex, std::vector<double> &By);
+                          const pic_beam_lab *beam, LabParticles &P, LabFields &F);
+
+// rho on the nodes (n0*n1*n2) of particles first .. end of P, with the order-G.order shape.
+void deposit_node_charge(const Geometry &G, const LabParticles &P, size_t first, std::vector<double> &rho);
+
+// Adds to F the self-field of node charge rho moving rigidly at beta along z (Lorentz
+// factor gamma): E from the relativistic Poisson equation, B = beta z x E.
+void add_beam_self_field(const Geometry &G, const std::vector<double> &rho, double gamma, double beta, LabFields &F);
 
 }  // namespace pic

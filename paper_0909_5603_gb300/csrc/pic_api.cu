@@ -732,16 +732,17 @@ extern "C" pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *lase
     cudaSetDevice(ctx->device);
     CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
     Geometry G{ctx->ndim, {ctx->n[0], ctx->n[1], ctx->n[2]}, {ctx->dx[0], ctx->dx[1], ctx->dx[2]}};
+    for (int a = 0; a < 3; ++a) G.bc[a] = ctx->bc[a];
+    G.order = ctx->order;
+    G.charge = ctx->opt.charge;
     LabParticles P;
-    std::vector<double> Ex, By;
-    transform_lab_inputs(G, ctx->gamma_b, laser, plasma, beam, P, Ex, By);
-    // fields: all zero except the laser
+    LabFields F;
+    transform_lab_inputs(G, ctx->gamma_b, laser, plasma, beam, P, F);
+    // fields: zero except the laser and the beam's self-field
     CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->h.E[0], 0, 12 * (size_t)ctx->h.cstride * ctx->es, ctx->stream));
     pic_status st;
-    if (laser) {
-        if ((st = set_field_internal(ctx, PIC_EX, Ex.data())) != PIC_OK) return st;
-        if ((st = set_field_internal(ctx, PIC_BY, By.data())) != PIC_OK) return st;
-    }
+    for (int c = 0; c < 6; ++c)
+        if (!F.comp[c].empty() && (st = set_field_internal(ctx, PIC_EX + c, F.comp[c].data())) != PIC_OK) return st;
     // the plasma's lab-stationary ions: a rigid background streaming at -beta_b
     InstDev &h = ctx->h;
     h.ion = plasma && plasma->n0 > 0.0;

@@ -266,7 +266,7 @@ def test_lab_frame_load(ndim, prec):
     if prec == FP64:
         for k in ("off", "u", "w"):
             assert np.array_equal(pg[k], po[k]), k
-        tol = 1e-15
+        tol = 1e-13  # the beam's self-field solve sums in its own order on each side
     else:
         # FP32 storage: the oracle's FP64 values rounded to FP32, offsets kept below 1
         below_one = np.nextafter(np.float32(1), np.float32(0))
@@ -276,8 +276,10 @@ def test_lab_frame_load(ndim, prec):
                 ref = np.minimum(ref, below_one)
             assert np.array_equal(pg[k], ref.astype(np.float64)), k
         tol = 6e-8
-    for c in (pic.PIC_EX, pic.PIC_BY):
-        assert rel(g.get_field(c), o.get_field(c)) <= tol
+    for c in COMPS:  # laser (Ex, By) plus the beam's self-field
+        fo = o.get_field(c)
+        if np.abs(fo).max() > 0:
+            assert rel(g.get_field(c), fo) <= tol, c
 
 
 def test_rho_dive_and_diagnostics_fp64():
