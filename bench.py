@@ -262,6 +262,7 @@ def run_ours(args, rank, world):
 
     # ---- end to end through the C ABI with host buffers
     e2e = None if args.skip_e2e else end_to_end(pic, w, args, torch)
+    scan = None if args.skip_scan else batched_scan(pic, torch)
 
     if rank != 0:
         return
@@ -278,7 +279,7 @@ def run_ours(args, rank, world):
                        "particles": n0, "cells": ncell, "l2": "inputs larger than L2 (1.07 GB of particles)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "cell_updates_per_s": ncell * args.steps * world / (ms_max * 1e-3),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64, "batched_scan": scan,
             "gpu_launches": int(tm["launches"]),
             "phase_ms_per_step": {k: tm[k] / max(tm["steps"], 1) for k in
                                   ("ms_particles", "ms_scan", "ms_filter", "ms_maxwell", "ms_other")},
@@ -326,6 +327,65 @@ def end_to_end(pic, w, args, torch):
                                             "diagnostics read-back, final particle read-back"}
 
 
+def batched_scan(pic, torch, count=256, steps=10, steps64=3, warmup=3):
+    """The batched 2D3V boosted-frame scan: `count` independent instances (seeded recipe
+    tests/synth.py scan_instance: N x N with log2 N in [6, 9], 1-16 electrons per cell,
+    gamma_b in [1, 50], n/n_c in [1e-4, 1e-2]) advanced as one batch in FP32 with the FP64
+    gamma solve (one launch per phase over all instances, replayed from one CUDA graph),
+    against the same instances in FP64 stepped one at a time on one stream."""
+    ds = [synth.scan_instance(i) for i in range(count)]
+
+    def make(d, prec, stream=None):
+        s = pic.Simulation(2, d["n"], (0, 0, 0), d["dx"], d["dt"], gamma_boost=d["gamma_boost"], order=2,
+                           precision=prec, filter_passes=3, tile=(16, 1, 16), track_ids=False, stream=stream)
+        s.load_lab_frame(laser=d["laser"], plasma=d["plasma"])
+        return s
+
+    t = time.perf_counter()
+    sims = [make(d, pic.PIC_PREC_FP32) for d in ds]
+    load_s = time.perf_counter() - t
+    cells = sum(d["n"][0] * d["n"][2] for d in ds)
+    batch = pic.Batch(sims)
+    batch.step(warmup)
+    batch.synchronize()
+    nb = sum(s.num_particles() for s in sims)
+    stream = sims[0].stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch.step(steps)
+    e1.record(stream)
+    batch.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    na = sum(s.num_particles() for s in sims)
+    out = {"instances": count, "particles": int(nb), "cells": int(cells), "steps": steps,
+           "load_seconds": round(load_s, 2), "ms_per_step": ms,
+           "particle_steps_per_s": 0.5 * (nb + na) / (ms * 1e-3),
+           "cell_updates_per_s": cells / (ms * 1e-3), "dtype": "f32"}
+    batch.close()
+    del sims, batch
+    torch.cuda.empty_cache()
+    # FP64, one instance after the other on one stream (each its own launches and graph)
+    common = torch.cuda.Stream()
+    sims64 = [make(d, pic.PIC_PREC_FP64, common) for d in ds]
+    for s in sims64:
+        s.step(1)
+    torch.cuda.synchronize()
+    n64 = sum(s.num_particles() for s in sims64)
+    e0.record(common)
+    for _ in range(steps64):
+        for s in sims64:
+            s.step(1)
+    e1.record(common)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / steps64
+    out["fp64_one_at_a_time"] = {"ms_per_step": ms64, "particle_steps_per_s": n64 / (ms64 * 1e-3),
+                                 "steps": steps64}
+    del sims64
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,6 +395,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-scan", action="store_true", help="skip the 256-instance batched scan")
     ap.add_argument("--nz", type=int, default=N_GRID[2],
                     help="cells along z (a shorter slab of the same workload, for profiling captures)")
     args = ap.parse_args()

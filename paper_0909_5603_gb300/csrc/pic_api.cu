@@ -550,80 +550,61 @@ static pic_status ensure_particle_capacity(pic_ctx *c, int64_t n)
     return PIC_OK;
 }
 
-// Converts to the storage precision in canonical order.  In-cell offsets (unit_interval)
-// stay below 1: an FP64 offset within half an FP32 ulp of 1 would round to 1.0f, so it
-// is stored as the largest float below 1 (same cell, error below 6e-8).
-template <typename R>
-static void fill_typed(std::vector<unsigned char> &buf, const std::vector<double> &src, const std::vector<int64_t> &perm,
-                       int stride, int comp, bool unit_interval)
+// Tile of a cell index (linear, x fastest).
+static int tile_of_cell(const pic_ctx *c, int cell)
 {
-    buf.resize(perm.size() * sizeof(R));
-    R *d = (R *)buf.data();
-    const R below_one = std::nextafter(R(1), R(0));
-    for (size_t i = 0; i < perm.size(); ++i) {
-        R v = (R)src[(size_t)perm[i] * stride + comp];
-        if (unit_interval && v >= R(1)) v = below_one;
-        d[i] = v;
-    }
+    const InstDev &h = c->h;
+    const int ci = cell % c->n[0], cj = (cell / c->n[0]) % c->n[1], ck = cell / (c->n[0] * c->n[1]);
+    return ci / h.ts[0] + h.nt[0] * (cj / h.ts[1] + h.nt[1] * (ck / h.ts[2]));
 }
 
-static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, const double *off, const double *u,
-                                const double *w, const int32_t *id)
+// Device scratch for a load, released when it goes out of scope.
+struct LoadScratch {
+    pic_ctx *c;
+    std::vector<void *> ps;
+    void *get(size_t bytes)
+    {
+        void *p = dalloc(c, bytes);
+        if (p) ps.push_back(p);
+        return p;
+    }
+    ~LoadScratch()
+    {
+        for (void *p : ps) dfree(c, p);
+    }
+};
+
+// Uploads n FP64 particles (host arrays, any order) with their canonical slots and places
+// them on the device in the storage precision (k_place).
+static pic_status place_from_host(pic_ctx *c, int64_t n, const int32_t *cell, const double *off, const double *u,
+                                  const double *w, const int32_t *id, long long id_base, const std::vector<int> &slot)
+{
+    if (n <= 0) return PIC_OK;
+    LoadScratch S{c, {}};
+    int *d_cell = (int *)S.get(sizeof(int) * n), *d_slot = (int *)S.get(sizeof(int) * n);
+    double *d_off = (double *)S.get(sizeof(double) * 3 * n), *d_u = (double *)S.get(sizeof(double) * 3 * n);
+    double *d_w = (double *)S.get(sizeof(double) * n);
+    int *d_id = id ? (int *)S.get(sizeof(int) * n) : nullptr;
+    if (!d_cell || !d_slot || !d_off || !d_u || !d_w || (id && !d_id))
+        return fail(c, PIC_ERR_OOM, "no device memory to stage %lld particles", (long long)n);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_cell, cell, sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_slot, slot.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_off, off, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_u, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_w, w, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    if (id) CUDA_OR_FAIL(c, cudaMemcpyAsync(d_id, id, sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+    PlaceSrc src{d_cell, d_off, d_u, d_w, d_id, d_slot, (long long)n, id_base};
+    CUDA_OR_FAIL(c, launch_place(c->fp64, c->h, src, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));  // before the scratch is released
+    return PIC_OK;
+}
+
+// After the particles are in place: the initial tile layout (every tile's particles in
+// its own segment, all in the "stays" bucket), the FP32 current scale, and a reset of
+// the step state.
+static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg, double wmax)
 {
     InstDev &h = c->h;
-    if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", (long long)n);
-    if (n > 0 && (!cell || !off || !u || !w)) return fail(c, PIC_ERR_ARG, "particle arrays must not be NULL");
-    for (int64_t p = 0; p < n; ++p) {
-        if (cell[p] < 0 || cell[p] >= c->ncell) return fail(c, PIC_ERR_ARG, "particle %lld: cell %d outside the grid", (long long)p, cell[p]);
-        for (int a = 0; a < 3; ++a) {
-            if (!activeaxis(c->ndim, a)) continue;
-            const double o = off[3 * p + a];
-            if (!(o >= 0.0 && o < 1.0)) return fail(c, PIC_ERR_ARG, "particle %lld: offset %g outside [0,1)", (long long)p, o);
-        }
-        if (!finite3(u + 3 * p) || !std::isfinite(w[p])) return fail(c, PIC_ERR_NAN, "particle %lld: non-finite momentum or weight", (long long)p);
-    }
-    // stable counting sort by tile id
-    std::vector<int> tcount(h.ntiles + 1, 0);
-    std::vector<int> tile_of(n > 0 ? n : 1);
-    for (int64_t p = 0; p < n; ++p) {
-        const int ci = cell[p] % c->n[0], cj = (cell[p] / c->n[0]) % c->n[1], ck = cell[p] / (c->n[0] * c->n[1]);
-        const int t = ci / h.ts[0] + h.nt[0] * (cj / h.ts[1] + h.nt[1] * (ck / h.ts[2]));
-        tile_of[p] = t;
-        tcount[t + 1]++;
-    }
-    for (int t = 0; t < h.ntiles; ++t) tcount[t + 1] += tcount[t];
-    std::vector<int> seg(tcount);
-    std::vector<int64_t> perm(n);
-    {
-        std::vector<int> fillp(tcount.begin(), tcount.end() - 1);
-        for (int64_t p = 0; p < n; ++p) perm[fillp[tile_of[p]]++] = p;
-    }
-    pic_status st = ensure_particle_capacity(c, n);
-    if (st != PIC_OK) return st;
-    // host arrays in canonical order, storage precision
-    std::vector<int> hcell(n), hid(n);
-    for (int64_t i = 0; i < n; ++i) {
-        hcell[i] = cell[perm[i]];
-        hid[i] = id ? id[perm[i]] : (int)perm[i];
-    }
-    std::vector<double> voff(off, off + 3 * n), vu(u, u + 3 * n), vw(w, w + n);
-    std::vector<unsigned char> buf;
-    auto put = [&](void *dst, const std::vector<double> &src, int stride, int comp, bool unit) -> pic_status {
-        if (c->fp64) fill_typed<double>(buf, src, perm, stride, comp, unit);
-        else fill_typed<float>(buf, src, perm, stride, comp, unit);
-        if (n > 0) CUDA_OR_FAIL(c, cudaMemcpy(dst, buf.data(), buf.size(), cudaMemcpyHostToDevice));
-        return PIC_OK;
-    };
-    if (n > 0) {
-        CUDA_OR_FAIL(c, cudaMemcpy(h.cell[0], hcell.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
-        if (h.id[0]) CUDA_OR_FAIL(c, cudaMemcpy(h.id[0], hid.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
-    }
-    for (int a = 0; a < 3; ++a) {
-        if (h.off[0][a] && (st = put(h.off[0][a], voff, 3, a, true)) != PIC_OK) return st;
-        if ((st = put(h.u[0][a], vu, 3, a, false)) != PIC_OK) return st;
-    }
-    if ((st = put(h.w[0], vw, 1, 0, false)) != PIC_OK) return st;
-    // initial layout 0
     const int R = h.R;
     std::vector<int> cbase(h.ntiles + 1, 0), tot((size_t)h.ntiles * kBuckets, 0), pop(h.ntiles, 0);
     for (int t = 0; t < h.ntiles; ++t) {
@@ -653,8 +634,6 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
     // FP32 fixed-point current scale: the power of two that maps the bound |q| max(w) / dV
     // on any single current contribution to at most 2^20
     {
-        double wmax = 0.0;
-        for (int64_t p = 0; p < n; ++p) wmax = std::max(wmax, std::fabs(w[p]));
         const double bound = std::fabs(c->opt.charge) * wmax / (c->dx[0] * c->dx[1] * c->dx[2]);
         int e = 0;
         if (bound > 0.0) {
@@ -673,6 +652,42 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
     c->last_filtered = 0;
     destroy_graph(c);
     return upload_inst(c);
+}
+
+// Host particles (FP64, any order): validated, laid out in the canonical order with a
+// stable counting sort by tile on the host, then converted and placed on the device.
+static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, const double *off, const double *u,
+                                const double *w, const int32_t *id)
+{
+    InstDev &h = c->h;
+    if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", (long long)n);
+    if (n > 0 && (!cell || !off || !u || !w)) return fail(c, PIC_ERR_ARG, "particle arrays must not be NULL");
+    double wmax = 0.0;
+    for (int64_t p = 0; p < n; ++p) {
+        if (cell[p] < 0 || cell[p] >= c->ncell) return fail(c, PIC_ERR_ARG, "particle %lld: cell %d outside the grid", (long long)p, cell[p]);
+        for (int a = 0; a < 3; ++a) {
+            if (!activeaxis(c->ndim, a)) continue;
+            const double o = off[3 * p + a];
+            if (!(o >= 0.0 && o < 1.0)) return fail(c, PIC_ERR_ARG, "particle %lld: offset %g outside [0,1)", (long long)p, o);
+        }
+        if (!finite3(u + 3 * p) || !std::isfinite(w[p])) return fail(c, PIC_ERR_NAN, "particle %lld: non-finite momentum or weight", (long long)p);
+        wmax = std::max(wmax, std::fabs(w[p]));
+    }
+    // stable counting sort by tile id: seg (segment starts) and each particle's slot
+    std::vector<int> seg(h.ntiles + 1, 0), slot(n > 0 ? n : 1);
+    for (int64_t p = 0; p < n; ++p) {
+        slot[p] = tile_of_cell(c, cell[p]);
+        seg[slot[p] + 1]++;
+    }
+    for (int t = 0; t < h.ntiles; ++t) seg[t + 1] += seg[t];
+    {
+        std::vector<int> fill(seg.begin(), seg.end() - 1);
+        for (int64_t p = 0; p < n; ++p) slot[p] = fill[slot[p]]++;
+    }
+    pic_status st = ensure_particle_capacity(c, n);
+    if (st != PIC_OK) return st;
+    if ((st = place_from_host(c, n, cell, off, u, w, id, 0, slot)) != PIC_OK) return st;
+    return finish_load(c, seg, wmax);
 }
 
 extern "C" pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3, const double *u3,
@@ -735,14 +750,6 @@ extern "C" pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *lase
     for (int a = 0; a < 3; ++a) G.bc[a] = ctx->bc[a];
     G.order = ctx->order;
     G.charge = ctx->opt.charge;
-    LabParticles P;
-    LabFields F;
-    transform_lab_inputs(G, ctx->gamma_b, laser, plasma, beam, P, F);
-    // fields: zero except the laser and the beam's self-field
-    CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->h.E[0], 0, 12 * (size_t)ctx->h.cstride * ctx->es, ctx->stream));
-    pic_status st;
-    for (int c = 0; c < 6; ++c)
-        if (!F.comp[c].empty() && (st = set_field_internal(ctx, PIC_EX + c, F.comp[c].data())) != PIC_OK) return st;
     // the plasma's lab-stationary ions: a rigid background streaming at -beta_b
     InstDev &h = ctx->h;
     h.ion = plasma && plasma->n0 > 0.0;
@@ -751,8 +758,99 @@ extern "C" pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *lase
     h.ion_ramp = plasma ? plasma->ramp_len : 0.0;
     h.ion_gb = ctx->gamma_b;
     h.ion_beta = std::sqrt(1.0 - 1.0 / (ctx->gamma_b * ctx->gamma_b));
-    const int64_t np = (int64_t)P.cell.size();
-    return load_internal(ctx, np, P.cell.data(), P.off.data(), P.mom.data(), P.weight.data(), P.id.data());
+    // the plasma is drawn on the device (k_load.cu); laser, beam and the beam's field on
+    // the host.  Plasma ids come first, as in the host transform.
+    std::vector<int> counts;
+    long long plasma_ids = 0;
+    bool on_device = plasma != nullptr;
+    PlasmaGen PG{};
+    if (plasma) {
+        PG.ndim = ctx->ndim;
+        for (int a = 0; a < 3; ++a) PG.n[a] = ctx->n[a], PG.dx[a] = ctx->dx[a], PG.uth[a] = plasma->u_th[a];
+        PG.ncell = ctx->ncell;
+        PG.gb = ctx->gamma_b;
+        PG.beta = std::sqrt(1.0 - 1.0 / (ctx->gamma_b * ctx->gamma_b));
+        PG.n0 = plasma->n0;
+        PG.zs = plasma->z_start;
+        PG.ramp = plasma->ramp_len;
+        PG.dV = ctx->dx[0] * ctx->dx[1] * ctx->dx[2];
+        PG.ppc = plasma->ppc;
+        PG.seed = plasma->seed;
+        if (plasma->ppc >= (1 << 15)) on_device = false;
+        int *d_count = on_device ? (int *)dalloc(ctx, sizeof(int) * ((size_t)ctx->ncell + 1)) : nullptr;
+        if (d_count) {
+            counts.resize(ctx->ncell + 1);
+            cudaError_t e = cudaMemsetAsync(d_count + ctx->ncell, 0, sizeof(int), ctx->stream);
+            if (e == cudaSuccess) e = launch_plasma_count(PG, d_count, ctx->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(counts.data(), d_count, sizeof(int) * counts.size(), cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            dfree(ctx, d_count);
+            if (e != cudaSuccess) return fail(ctx, PIC_ERR_CUDA, "plasma count: %s", cudaGetErrorString(e));
+            if (counts[ctx->ncell] != 0) on_device = false;  // rare: take the host path
+        } else {
+            on_device = false;
+        }
+    }
+    LabParticles P;
+    LabFields F;
+    transform_lab_inputs(G, ctx->gamma_b, laser, on_device ? nullptr : plasma, beam, P, F);
+    // fields: zero except the laser and the beam's self-field
+    CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->h.E[0], 0, 12 * (size_t)ctx->h.cstride * ctx->es, ctx->stream));
+    pic_status st;
+    for (int c = 0; c < 6; ++c)
+        if (!F.comp[c].empty() && (st = set_field_internal(ctx, PIC_EX + c, F.comp[c].data())) != PIC_OK) return st;
+    if (!on_device) {
+        const int64_t np = (int64_t)P.cell.size();
+        return load_internal(ctx, np, P.cell.data(), P.off.data(), P.mom.data(), P.weight.data(), P.id.data());
+    }
+    // canonical layout: per tile the plasma particles (cells in linear order), then the
+    // beam particles (in their order)
+    const long long ncell = ctx->ncell;
+    std::vector<int> seg(h.ntiles + 1, 0), plasma_in_tile(h.ntiles, 0);
+    long long n_plasma = 0;
+    for (long long cidx = 0; cidx < ncell; ++cidx) {
+        const int placed = counts[cidx] & 0xffff;
+        plasma_in_tile[tile_of_cell(ctx, (int)cidx)] += placed;
+        n_plasma += placed;
+    }
+    const int64_t nb = (int64_t)P.cell.size();
+    std::vector<int> beam_slot(nb > 0 ? nb : 1);
+    for (int64_t p = 0; p < nb; ++p) seg[tile_of_cell(ctx, P.cell[p]) + 1]++;
+    for (int t = 0; t < h.ntiles; ++t) seg[t + 1] += plasma_in_tile[t];
+    for (int t = 0; t < h.ntiles; ++t) seg[t + 1] += seg[t];
+    const long long n_total = seg[h.ntiles];
+    if (n_total >= (1LL << 31) - 1) return fail(ctx, PIC_ERR_ARG, "particle count %lld out of range", n_total);
+    std::vector<int> slot0(ncell), id0(ncell);
+    {
+        std::vector<int> fill(seg.begin(), seg.end() - 1);
+        for (long long cidx = 0; cidx < ncell; ++cidx) {
+            const int t = tile_of_cell(ctx, (int)cidx);
+            slot0[cidx] = fill[t];
+            fill[t] += counts[cidx] & 0xffff;
+            id0[cidx] = (int)plasma_ids;
+            plasma_ids += counts[cidx] >> 16;
+        }
+        for (int64_t p = 0; p < nb; ++p) beam_slot[p] = fill[tile_of_cell(ctx, P.cell[p])]++;
+    }
+    if ((st = ensure_particle_capacity(ctx, n_total)) != PIC_OK) return st;
+    {
+        LoadScratch S{ctx, {}};
+        int *d_slot0 = (int *)S.get(sizeof(int) * (size_t)ncell), *d_id0 = (int *)S.get(sizeof(int) * (size_t)ncell);
+        if (!d_slot0 || !d_id0) return fail(ctx, PIC_ERR_OOM, "no device memory for the plasma layout");
+        CUDA_OR_FAIL(ctx, cudaMemcpyAsync(d_slot0, slot0.data(), sizeof(int) * ncell, cudaMemcpyHostToDevice, ctx->stream));
+        CUDA_OR_FAIL(ctx, cudaMemcpyAsync(d_id0, id0.data(), sizeof(int) * ncell, cudaMemcpyHostToDevice, ctx->stream));
+        CUDA_OR_FAIL(ctx, launch_plasma_write(ctx->fp64, h, PG, d_slot0, d_id0, ctx->stream));
+        CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    for (auto &v : P.id) v += (int32_t)plasma_ids;  // beam ids follow the plasma's
+    if ((st = place_from_host(ctx, nb, P.cell.data(), P.off.data(), P.mom.data(), P.weight.data(), P.id.data(), 0,
+                              beam_slot)) != PIC_OK)
+        return st;
+    // weight bound: the plateau weight (the profile never exceeds 1) and the beam's
+    double wmax = n_plasma > 0 ? PG.gb * PG.n0 * 1.0 * PG.dV / PG.ppc : 0.0;
+    for (int64_t p = 0; p < nb; ++p) wmax = std::max(wmax, std::fabs(P.weight[p]));
+    return finish_load(ctx, seg, wmax);
 }
 
 // ------------------------------------------------------------------------------------

@@ -134,7 +134,34 @@ __device__ __forceinline__ int find_instance_ll(const long long *start, int nins
     return lo;
 }
 
+// FP64 particles to place in the canonical order (device arrays, 3 values per particle
+// for off and u); slot[i] is particle i's position in the sorted buffer.
+struct PlaceSrc {
+    const int *cell;
+    const double *off, *u, *w;
+    const int *id;  // null: ids id_base + i
+    const int *slot;
+    long long n;
+    long long id_base;
+};
+
+// Lab-frame plasma drawn on the device (see k_load.cu)
+struct PlasmaGen {
+    int ndim;
+    int n[3];
+    long long ncell;
+    double dx[3];
+    double gb, beta, n0, zs, ramp, dV;
+    double uth[3];
+    int ppc;
+    uint64_t seed;
+};
+
 // host-side launchers
+cudaError_t launch_place(int fp64, const InstDev &I, const PlaceSrc &s, cudaStream_t st);
+cudaError_t launch_plasma_count(const PlasmaGen &G, int *count, cudaStream_t st);
+cudaError_t launch_plasma_write(int fp64, const InstDev &I, const PlasmaGen &G, const int *slot0, const int *id0,
+                                cudaStream_t st);
 cudaError_t launch_ion_current(int fp64, const Launch &L, cudaStream_t s);
 cudaError_t launch_rho_ion(const Launch &L, long long ncell, double *rho, cudaStream_t s);
 cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, const Launch &L, size_t smem, cudaStream_t s);

@@ -82,3 +82,28 @@ def lwfa_stage(n=(128, 128, 1024), gamma_boost=13.0, ppc=2, seed=3, lambda0=1.0)
     courant = 1.0 / np.sqrt(2.0 / dx ** 2 + 1.0 / dz ** 2)
     dt = min(0.5 * dz, 0.9 * courant)
     return dict(n=tuple(n), dx=(dx, dx, dz), dt=dt, gamma_boost=gamma_boost, laser=laser, plasma=plasma)
+
+
+def scan_instance(i, seed_base=5000, tile=16):
+    """Instance i of the batched 2D3V boosted-frame scan (seeded with seed_base + i):
+    N x N cells with log2 N uniform in [6, 9] (N rounded to a multiple of the tile),
+    1-16 electrons per cell, gamma_b uniform in [1, 50], n/n_c uniform in [1e-4, 1e-2];
+    a cold plasma filling the periodic box with its ions and an a0 = 1 laser pulse two
+    wavelengths long in the middle; cells and step as in lwfa_stage (dz = lambda' / 16,
+    dx = 2 lambda0, dt = dz / 2 capped at 0.9 of the 2D Courant limit)."""
+    rng = np.random.default_rng(seed_base + i)
+    n_side = int(max(tile, round(2.0 ** rng.uniform(6.0, 9.0) / tile) * tile))
+    ppc = int(rng.integers(1, 17))
+    gb = float(rng.uniform(1.0, 50.0))
+    dens = float(rng.uniform(1e-4, 1e-2))
+    b = np.sqrt(1.0 - 1.0 / gb ** 2)
+    doppler = gb * (1.0 + b)
+    dz = doppler / 16.0
+    dx = 2.0
+    dt = min(0.5 * dz, 0.9 / np.sqrt(1.0 / dx ** 2 + 1.0 / dz ** 2))
+    n_c = (2.0 * np.pi) ** 2
+    lz = n_side * dz
+    laser = (1.0, 1.0, 0.25 * n_side * dx, 2.0, 0.5 * lz / doppler)
+    plasma = (dens * n_c, -1e9, 0.0, ppc, (0.0, 0.0, 0.0), seed_base + i)
+    return dict(n=(n_side, 1, n_side), dx=(dx, 1.0, dz), dt=dt, gamma_boost=gb, laser=laser, plasma=plasma,
+                ppc=ppc)
