@@ -386,6 +386,47 @@ def batched_scan(pic, torch, count=256, steps=10, steps64=3, warmup=3):
     return out
 
 
+def precision_sweep(pic, torch, args):
+    """The LWFA stage at scale for several boosts (256 x 256 x 2048 cells, 4 electrons per
+    cell, about 5.4e8 particles): the FP32 path (FP64 gamma solve) against the all-FP64 GPU
+    path after `--sweep-steps` steps.  Reports per boost the normwise relative difference
+    of the wake field E_z and of E_x, the relative difference of the field and kinetic
+    energies, and both paths' particle-steps/s."""
+    out = []
+    gammas = [float(g) for g in args.sweep_gammas.split(",")]
+    for gb in gammas:
+        w = synth.lwfa_stage((256, 256, 2048), gb, 4, seed=4 + gammas.index(gb))
+        res = {"gamma_boost": gb}
+        fields, diags = {}, {}
+        for prec, name in ((pic.PIC_PREC_FP32, "fp32"), (pic.PIC_PREC_FP64, "fp64")):
+            sim = pic.Simulation(3, w["n"], (1, 1, 1), w["dx"], w["dt"], gamma_boost=gb, order=2, precision=prec,
+                                 filter_passes=3, tile=(8, 8, 8), track_ids=False)
+            sim.load_lab_frame(laser=w["laser"], plasma=w["plasma"])
+            n = sim.num_particles()
+            sim.step(2)
+            sim.synchronize()
+            sim.set_profiling(True, reset=True)
+            sim.step(args.sweep_steps - 2)
+            sim.synchronize()
+            t = sim.timings()
+            ms = sum(t[k] for k in ("ms_particles", "ms_scan", "ms_filter", "ms_maxwell", "ms_other")) / t["steps"]
+            res[name] = {"particles": n, "ms_per_step": ms, "particle_steps_per_s": n / (ms * 1e-3),
+                         "particle_kernel_ms": t["ms_particles"] / t["steps"]}
+            fields[name] = {c: sim.get_field(c) for c in (pic.PIC_EZ, pic.PIC_EX)}
+            diags[name] = sim.diagnostics()
+            del sim
+            torch.cuda.empty_cache()
+        for c, key in ((pic.PIC_EZ, "Ez"), (pic.PIC_EX, "Ex")):
+            a, b = fields["fp32"][c], fields["fp64"][c]
+            res[f"rel_err_{key}"] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        for k in ("field_energy", "kinetic_energy"):
+            res[f"rel_err_{k}"] = abs(diags["fp32"][k] - diags["fp64"][k]) / max(abs(diags["fp64"][k]), 1e-300)
+        res["steps"] = args.sweep_steps
+        out.append(res)
+        print(json.dumps(res), flush=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,13 +437,23 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-scan", action="store_true", help="skip the 256-instance batched scan")
+    ap.add_argument("--precision-sweep", action="store_true",
+                    help="instead of the benchmark: FP32 vs FP64 on the LWFA stage at 256x256x2048, 4 ppc, per boost")
+    ap.add_argument("--sweep-gammas", default="2,5,13,30,100")
+    ap.add_argument("--sweep-steps", type=int, default=100)
     ap.add_argument("--nz", type=int, default=N_GRID[2],
                     help="cells along z (a shorter slab of the same workload, for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     rank, world = dist_init()
-    if args.impl == "reference":
+    if args.precision_sweep:
+        import torch
+
+        import paper_0909_5603_gb300 as pic
+        pic.build()
+        print(json.dumps({"precision_sweep": precision_sweep(pic, torch, args)}))
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world)

@@ -252,6 +252,21 @@ pic_status pic_synchronize(pic_ctx *ctx);
  * pic_set_profiling, pic_get_timings and pic_destroy accept a batch. */
 pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx **batch);
 
+/* Autotuner: picks the particle tile shape for a workload by measurement (the paper has
+ * no counterpart; it tunes this implementation).  For every candidate tile (3D: 8^3,
+ * 16x8x8, 8x8x16, 8x16x8, 16x16x4, 16x8x4, 8x8x4, 4x8x8, 16x16x8, 32x8x4; 2D: 16x16,
+ * 32x8, 8x32, 32x16, 16x32, 32x32, 64x8) it creates a context with `base` (NULL =
+ * defaults) and that tile, loads the lab-frame inputs, runs 2 warm-up steps, times
+ * `steps` >= 1 steps with the library's per-phase CUDA events and destroys it.  The
+ * fastest candidate's options go to *best (its tile set, everything else from base) and
+ * its time per step (ms, all phases) to *ms_per_step (may be NULL).  Candidates that
+ * pic_create rejects are skipped; if none runs, the last error is returned.  Device
+ * memory for one candidate at a time; a slab of the workload (fewer z cells) gives the
+ * same per-particle ranking at a fraction of the cost. */
+pic_status pic_autotune(const pic_grid *grid, const double dx[3], double dt, double gamma_boost, int shape_order,
+                        const pic_options *base, const pic_laser_lab *laser, const pic_plasma_lab *plasma,
+                        const pic_beam_lab *beam, int steps, pic_options *best, double *ms_per_step);
+
 /* Charge density read-out that allocates no device memory.  The paper has no counterpart:
  * this is a service of the library, not a step of the method.
  *

@@ -103,6 +103,8 @@ def lib():
         L.orc_load_lab_frame.argtypes = [vp, ctypes.c_double, vp, vp, vp]
         L.orc_beam_self_field.restype = ctypes.c_int
         L.orc_beam_self_field.argtypes = [vp, _f64p, ctypes.c_double, ctypes.c_double]
+        L.orc_round_state_fp32.restype = None
+        L.orc_round_state_fp32.argtypes = [vp]
         L.orc_ion_integral.restype = ctypes.c_double
         L.orc_ion_integral.argtypes = [vp, ctypes.c_double, ctypes.c_double]
         _lib = L
@@ -236,6 +238,10 @@ class Sim:
         """Adds the self-field of node charge density rho (n2, n1, n0) moving at beta z."""
         r = np.ascontiguousarray(np.asarray(rho, np.float64).ravel())
         lib().orc_beam_self_field(self._h, r, float(gamma), float(beta))
+
+    def round_state_fp32(self):
+        """Rounds the stored state to FP32 (the storage of an FP32 implementation)."""
+        lib().orc_round_state_fp32(self._h)
 
     def ion_integral(self, a, b):
         """Ion-background charge between box coordinates a < b at t' = 0 (per unit area)."""

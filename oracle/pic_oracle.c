@@ -863,6 +863,25 @@ void orc_div_e(const orc_sim *s, double *out)
                                               dbwd(s, ORC_EZ, 2, i, j, k);
 }
 
+/* Test helper: rounds the stored state (offsets, momenta, weights, E, B) to FP32, as an
+ * FP32 implementation stores it between steps; offsets that round to 1 keep the largest
+ * float below 1 (same cell).  Calling it after every step gives the error floor that FP32
+ * storage alone imposes, with FP64 arithmetic everywhere else. */
+void orc_round_state_fp32(orc_sim *s)
+{
+    const double below_one = (double)nextafterf(1.0f, 0.0f);
+    for (int64_t p = 0; p < s->np; ++p) {
+        for (int a = 0; a < 3; ++a) {
+            double o = (double)(float)s->off[3 * p + a];
+            s->off[3 * p + a] = o >= 1.0 ? below_one : o;
+            s->u[3 * p + a] = (double)(float)s->u[3 * p + a];
+        }
+        s->w[p] = (double)(float)s->w[p];
+    }
+    for (int c = ORC_EX; c <= ORC_BZ; ++c)
+        for (int64_t i = 0; i < s->ncell; ++i) s->f[c][i] = (double)(float)s->f[c][i];
+}
+
 /* out: field energy (1/2) sum (E^2 + B^2) dV, kinetic energy sum w m (gamma - 1),
  * total charge sum q w, particle count, lost count, step, 0, 0. */
 void orc_diagnostics(const orc_sim *s, double out[8])

@@ -71,6 +71,8 @@ double orc_ion_integral(const orc_sim *s, double a, double b);
  * (Lorentz factor gamma) along z: relativistic Poisson solve, E = -grad phi with the z
  * part over gamma^2, B = beta z x E.  Returns 0. */
 int orc_beam_self_field(orc_sim *s, const double *rho, double gamma, double beta);
+/* Test helper: rounds offsets (kept below 1), momenta, weights, E and B to FP32. */
+void orc_round_state_fp32(orc_sim *s);
 
 #ifdef __cplusplus
 }

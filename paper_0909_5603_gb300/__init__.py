@@ -32,7 +32,7 @@ PIC_PHASE_PARTICLES, PIC_PHASE_FILTER, PIC_PHASE_MAXWELL, PIC_PHASE_ALL = 1, 2, 
 EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error", "pic_load_lab_frame",
             "pic_load_particles", "pic_set_field", "pic_step", "pic_run_phases", "pic_get_field",
             "pic_num_particles", "pic_get_particles", "pic_get_diagnostics", "pic_set_profiling",
-            "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc"]
+            "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc", "pic_autotune"]
 PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
@@ -141,6 +141,10 @@ def lib():
         L.pic_batch_create.argtypes = [ctypes.c_int, P(vp), P(vp)]
         L.pic_get_rho_noalloc.restype = st
         L.pic_get_rho_noalloc.argtypes = [vp, vp, ctypes.c_size_t]
+        L.pic_autotune.restype = st
+        L.pic_autotune.argtypes = [P(pic_grid), P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   P(pic_options), P(pic_laser_lab), P(pic_plasma_lab), P(pic_beam_lab), ctypes.c_int,
+                                   P(pic_options), P(ctypes.c_double)]
         _lib = L
     return _lib
 
@@ -194,6 +198,46 @@ def pic_batch_create(handles):
 
 
 # ---- convenience object ---------------------------------------------------------------
+def _lab_structs(laser, plasma, beam):
+    """Tuples (as in Simulation.load_lab_frame) -> the pic.h structs (or None)."""
+    la = pic_laser_lab(*laser) if laser is not None else None
+    if plasma is not None:
+        n0, zs, ramp, ppc, uth, seed = plasma
+        pl = pic_plasma_lab(n0, zs, ramp, int(ppc), (ctypes.c_double * 3)(*uth), int(seed))
+    else:
+        pl = None
+    if beam is not None:
+        nb, gam, spread, sr, sz, z0, tw, seed = beam
+        be = pic_beam_lab(int(nb), gam, spread, sr, sz, z0, tw, int(seed))
+    else:
+        be = None
+    return la, pl, be
+
+
+def autotune(ndim, n, bc, dx, dt, gamma_boost=1.0, order=1, precision=PIC_PREC_FP32, pusher=PIC_PUSHER_VAY,
+             filter_passes=0, laser=None, plasma=None, beam=None, steps=5, track_ids=False):
+    """pic_autotune: the fastest particle tile for this workload.  Returns (tile, ms per
+    step of the winner)."""
+    opt = pic_default_options()
+    opt.precision = precision
+    opt.pusher = pusher
+    opt.filter_passes = filter_passes
+    opt.track_ids = 1 if track_ids else 0
+    n = list(n)
+    if ndim == 2:
+        n[1] = 1
+    grid = pic_grid(ndim, (ctypes.c_int * 3)(*[int(v) for v in n]), (ctypes.c_int * 3)(*bc))
+    d = (ctypes.c_double * 3)(*dx)
+    la, pl, be = _lab_structs(laser, plasma, beam)
+    best = pic_options()
+    ms = ctypes.c_double(0.0)
+    st = lib().pic_autotune(ctypes.byref(grid), d, dt, gamma_boost, order, ctypes.byref(opt),
+                            ctypes.byref(la) if la else None, ctypes.byref(pl) if pl else None,
+                            ctypes.byref(be) if be else None, int(steps), ctypes.byref(best), ctypes.byref(ms))
+    _check(st)
+    return tuple(best.tile), ms.value
+
+
 class Simulation:
     """One boosted-frame PIC instance (a pic_ctx) with torch-provided device memory.
 
@@ -273,17 +317,7 @@ class Simulation:
         _check(lib().pic_load_particles(self.h, npart, _ptr(cell), _ptr(off), _ptr(u), _ptr(w), _ptr(ids)), self.h)
 
     def load_lab_frame(self, laser=None, plasma=None, beam=None):
-        la = pic_laser_lab(*laser) if laser is not None else None
-        if plasma is not None:
-            n0, zs, ramp, ppc, uth, seed = plasma
-            pl = pic_plasma_lab(n0, zs, ramp, int(ppc), (ctypes.c_double * 3)(*uth), int(seed))
-        else:
-            pl = None
-        if beam is not None:
-            nb, gam, spread, sr, sz, z0, tw, seed = beam
-            be = pic_beam_lab(int(nb), gam, spread, sr, sz, z0, tw, int(seed))
-        else:
-            be = None
+        la, pl, be = _lab_structs(laser, plasma, beam)
         _check(lib().pic_load_lab_frame(self.h, ctypes.byref(la) if la else None, ctypes.byref(pl) if pl else None,
                                         ctypes.byref(be) if be else None), self.h)
 

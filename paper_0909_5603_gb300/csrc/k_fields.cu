@@ -73,8 +73,9 @@ __global__ void __launch_bounds__(256) k_bhalf(Launch L, int damp)
     neighbour_offsets(I, c, up, dn);
     const R *Ex = (const R *)I.E[0], *Ey = (const R *)I.E[1], *Ez = (const R *)I.E[2];
     R *Bx = (R *)I.B[0], *By = (R *)I.B[1], *Bz = (R *)I.B[2];
-    const R h = R(0.5 * I.dt);
-    const R ix = R(1.0 / I.dx[0]), iy = R(1.0 / I.dx[1]), iz = R(1.0 / I.dx[2]);
+    const StepCoef<R> &K = coef<R>(I);
+    const R h = K.half_dt;
+    const R ix = K.inv_dx[0], iy = K.inv_dx[1], iz = K.inv_dx[2];
     const long long p = c.p;
     const R ex = Ex[p], ey = Ey[p], ez = Ez[p];
     R dEz_dy = R(0), dEy_dz = (Ey[p + up[2]] - ey) * iz, dEx_dz = (Ex[p + up[2]] - ex) * iz;
@@ -114,8 +115,9 @@ __global__ void __launch_bounds__(256) k_efull(Launch L, int filtered)
     const int nsweeps = I.filter_passes > 0 ? (I.ndim == 3 ? 3 : 2) : 0;
     void *const *Jsrc = (filtered && (nsweeps & 1)) ? I.Jt : I.J;
     const R *Jx = (const R *)Jsrc[0], *Jy = (const R *)Jsrc[1], *Jz = (const R *)Jsrc[2];
-    const R dt = R(I.dt);
-    const R ix = R(1.0 / I.dx[0]), iy = R(1.0 / I.dx[1]), iz = R(1.0 / I.dx[2]);
+    const StepCoef<R> &K = coef<R>(I);
+    const R dt = K.dt;
+    const R ix = K.inv_dx[0], iy = K.inv_dx[1], iz = K.inv_dx[2];
     const long long p = c.p;
     const R bx = Bx[p], by = By[p], bz = Bz[p];
     R dBz_dy = R(0), dBy_dz = (by - By[p + dn[2]]) * iz, dBx_dz = (bx - Bx[p + dn[2]]) * iz;

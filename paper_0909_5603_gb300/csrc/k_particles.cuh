@@ -406,13 +406,13 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     }
     if (tid == 0 && S.count != count) atomicOr(I.err, kErrInternal);
 
-    // per-instance constants in the working precision; in FP32 mode the current factors
-    // carry the fixed-point scale (see FixedAcc)
-    const R h = R(0.5 * I.q / I.m * I.dt);
-    const double dV = I.dx[0] * I.dx[1] * I.dx[2];
-    const R qdv = R(I.q / dV) * (kFixed ? R(I.jscale) : R(1));
-    const R jfx = R(I.dx[0] / I.dt), jfy = R(I.dx[1] / I.dt), jfz = R(I.dx[2] / I.dt);
-    const R dtdx[3] = {R(I.dt / I.dx[0]), R(I.dt / I.dx[1]), R(I.dt / I.dx[2])};
+    // per-instance constants in the working precision (host-formed); in FP32 mode the
+    // current factor qdv carries the fixed-point scale (see FixedAcc)
+    const StepCoef<R> &K = coef<R>(I);
+    const R h = K.h;
+    const R qdv = K.qdv;
+    const R jfx = K.jf[0], jfy = K.jf[1], jfz = K.jf[2];
+    const R dtdx[3] = {K.dtdx[0], K.dtdx[1], K.dtdx[2]};
     const int bx = I.box[0], bxy = I.box[0] * I.box[1];
     const int jd0 = I.jdim[0], jd01 = I.jdim[0] * I.jdim[1];
     const int jlo_y = ND == 3 ? I.jlo : 0;

@@ -202,6 +202,35 @@ extern "C" const char *pic_last_error(const pic_ctx *ctx)
 
 static int activeaxis(int ndim, int a) { return !(ndim == 2 && a == 1); }
 
+// The instance's step constants in both precisions (see StepCoef), from dt, dx, q, m and
+// the FP32 current scale.
+static void fill_step_coef(InstDev &h)
+{
+    const double dV = h.dx[0] * h.dx[1] * h.dx[2];
+    StepCoef<double> d;
+    d.h = 0.5 * h.q / h.m * h.dt;
+    d.qdv = h.q / dV;
+    for (int a = 0; a < 3; ++a) {
+        d.jf[a] = h.dx[a] / h.dt;
+        d.dtdx[a] = h.dt / h.dx[a];
+        d.inv_dx[a] = 1.0 / h.dx[a];
+    }
+    d.half_dt = 0.5 * h.dt;
+    d.dt = h.dt;
+    h.cd = d;
+    StepCoef<float> f;
+    f.h = (float)d.h;
+    f.qdv = (float)d.qdv * h.jscale;
+    for (int a = 0; a < 3; ++a) {
+        f.jf[a] = (float)d.jf[a];
+        f.dtdx[a] = (float)d.dtdx[a];
+        f.inv_dx[a] = (float)d.inv_dx[a];
+    }
+    f.half_dt = (float)d.half_dt;
+    f.dt = (float)d.dt;
+    h.cf = f;
+}
+
 static pic_status upload_inst(pic_ctx *c)
 {
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_inst, &c->h, sizeof(InstDev), cudaMemcpyHostToDevice, c->stream));
@@ -328,6 +357,8 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     h.dt = dt;
     h.q = o.charge;
     h.m = o.mass;
+    h.jscale = h.jinv = 1.0f;  // until a load sets the FP32 current scale
+    fill_step_coef(h);
     // gather box (tile + guard) and J tile geometry; the box starts one cell before the
     // tile (padded x coordinate T0 + 4, 16-byte aligned) and its x extent is a multiple of
     // 16 bytes
@@ -643,6 +674,7 @@ static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg, double wm
         h.jscale = bound > 0.0 ? (float)std::ldexp(1.0, 20 - e) : 1.0f;
         h.jinv = bound > 0.0 ? (float)std::ldexp(1.0, e - 20) : 1.0f;
     }
+    fill_step_coef(h);
     // cur, err, live, jsel, lost and the particle-phase counter
     CUDA_OR_FAIL(c, cudaMemset(h.cur, 0, 16 + sizeof(unsigned long long) + sizeof(int)));
     CUDA_OR_FAIL(c, cudaMemset(h.J[0], 0, 3 * (size_t)h.cstride * c->es));

@@ -48,6 +48,20 @@ constexpr int kErrCapacity = 8;     // more particles than the buffers hold
 
 // Device view of one instance.  Pointers are device addresses; field arrays are padded
 // with kGhost layers per side on active axes, x rows padded to a 16-byte multiple.
+// Per-instance step constants in the working precision, formed once on the host in FP64
+// (and rounded to FP32 for FP32 instances) so that no kernel spends FP64 divisions on
+// them: GB300's FP64 pipe is a small fraction of its FP32 rate.
+template <typename R>
+struct StepCoef {
+    R h;          // q dt / (2 m)
+    R qdv;        // q / dV, times the fixed-point current scale in FP32 mode
+    R jf[3];      // dx_a / dt
+    R dtdx[3];    // dt / dx_a
+    R half_dt;    // dt / 2
+    R dt;
+    R inv_dx[3];  // 1 / dx_a
+};
+
 struct InstDev {
     int ndim;
     int n[3];       // interior cells
@@ -67,6 +81,8 @@ struct InstDev {
     int absorb_cells;
     double absorb_strength;
     double dt, dx[3], q, m;
+    StepCoef<float> cf;   // FP32 instances
+    StepCoef<double> cd;  // FP64 instances
     // fields (element type set by the precision of the launch)
     void *E[3], *B[3], *J[3], *Jt[3];  // Jt: scratch for filter sweeps
     // particles, two buffers
@@ -103,6 +119,13 @@ struct InstDev {
     int jlo;            // J tile origin relative to the tile origin (-1 or -2)
     int jdim[3];        // J tile extents
 };
+
+template <typename R>
+__host__ __device__ __forceinline__ const StepCoef<R> &coef(const InstDev &I);
+template <>
+__host__ __device__ __forceinline__ const StepCoef<float> &coef<float>(const InstDev &I) { return I.cf; }
+template <>
+__host__ __device__ __forceinline__ const StepCoef<double> &coef<double>(const InstDev &I) { return I.cd; }
 
 // launch-wide view of a set of instances stepped together
 struct Launch {

@@ -241,9 +241,20 @@ def test_config1_2d3v_fp32_100_steps():
     stage, the beam, the batched scan) meet 1e-5 after 100 steps in their own tests."""
     n = (128, 1, 128)
     g, o = pair(2, n, (0, 0, 0), (1.0, 1.0, 1.0), 0.5, 1, FP32, tile=(16, 1, 16))
-    load_both(g, o, synth.uniform_plasma(n, 2, 4, 0.01, seed=1))
+    p = synth.uniform_plasma(n, 2, 4, 0.01, seed=1)
+    load_both(g, o, p)
     g.step(100)
     o.step(100)
+    # the floor FP32 storage alone sets: the oracle with its state rounded every step
+    e = oracle.Sim(2, n, (0, 0, 0), (1.0, 1.0, 1.0), 0.5, order=1, tile=(16, 1, 16))
+    e.set_particles(*[p[k] for k in ("cell", "off", "u", "w", "id")])
+    e.round_state_fp32()
+    for _ in range(100):
+        e.step(1)
+        e.round_state_fp32()
+    floor = max(rel2(e.get_field(c), o.get_field(c)) for c in COMPS)
+    print(f"FP32 storage floor after 100 steps (worst field): {floor:.2e}")
+    assert floor < 1e-5
     worst = compare_fields(g, o, COMPS + [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ], 5e-5, tol_inf=1e-4)
     print("FP32 config-1 relative errors after 100 steps (2-norm, max-norm) per field:", worst)
     compare_particles(g, o, 5e-5, exact_order=False, tol_inf=1e-4)

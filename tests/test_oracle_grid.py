@@ -289,3 +289,25 @@ def test_diagnostics_closed_forms():
     assert abs(d["field_energy"] - 0.5 * (0.09 + 0.04) * V) < 1e-12
     assert abs(d["kinetic_energy"] - 2.5 * (math.sqrt(10) - 1)) < 1e-12  # both have gamma = sqrt(10)
     assert d["total_charge"] == -2.5 and d["n_particles"] == 2
+
+
+def test_round_state_fp32_matches_float32_storage():
+    """The FP32-storage helper rounds each stored value as a float32 cast does and keeps
+    offsets below 1."""
+    s = make(3, (4, 4, 4), dx=(1.0, 1.0, 1.0))
+    rng = np.random.default_rng(41)
+    cell = np.arange(3, dtype=np.int32)
+    off = np.array([[0.1, 0.2, 0.3], [1 - 2 ** -30, 0.5, 0.25], [0.123456789123, 0.999999999, 0.0]])
+    u = rng.normal(size=(3, 3)) * 1e3
+    w = rng.random(3)
+    s.set_particles(cell, off, u, w)
+    f = rng.normal(size=(4, 4, 4))
+    s.set_field(oracle.EX, f)
+    s.round_state_fp32()
+    p = s.get_particles()
+    below = np.float64(np.nextafter(np.float32(1), np.float32(0)))
+    ref_off = np.minimum(off.astype(np.float32).astype(np.float64), below)
+    assert np.array_equal(p["off"], ref_off) and p["off"][1, 0] == below
+    assert np.array_equal(p["u"], u.astype(np.float32).astype(np.float64))
+    assert np.array_equal(p["w"], w.astype(np.float32).astype(np.float64))
+    assert np.array_equal(s.get_field(oracle.EX), f.astype(np.float32).astype(np.float64))
