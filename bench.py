@@ -15,6 +15,7 @@ has no exchange in this build); rank 0 prints the aggregate over ranks.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -42,6 +43,34 @@ PPC = 2
 
 def workload(nz=N_GRID[2]):
     return synth.lwfa_stage((N_GRID[0], N_GRID[1], nz), GAMMA_B, PPC, seed=3, lambda0=LAMBDA0)
+
+
+# DRAM traffic of the particle kernel, from one ncu capture of a 128x128x128 slab of the
+# same workload (profiles/k_particles_lwfa_128x128x128.md), valid while the kernel's
+# sources are the ones that were captured
+PROFILE = os.path.join(ROOT, "profiles", "k_particles_lwfa_128x128x128.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_0909_5603_gb300", "csrc", f)
+                  for f in ("k_particles.cuh", "pic_device.cuh", "k_push_f32.cu", "pic_internal.h")]
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(particles):
+    """DRAM bytes per launch scaled from the capture, or None when the kernel changed."""
+    try:
+        with open(PROFILE) as f:
+            kv = dict(line.split(":", 1) for line in f if line.startswith(("dram_bytes_per_particle", "kernel_source_sha256")))
+    except (OSError, ValueError):
+        return None
+    if kv.get("kernel_source_sha256", "").strip() != kernel_source_hash():
+        return None
+    return float(kv["dram_bytes_per_particle"]) * particles
 
 
 def measured_peaks():
@@ -231,7 +260,7 @@ def run_ours(args, rank, world):
     algo_bytes = 0.5 * (nb + na) * bytes_particle + ncell * bytes_cell
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_kind": peak_kind,
+            "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(0.5 * (nb + na)), "peak_kind": peak_kind,
             "kernel": "k_particles<3,2,float,Vay>", "kernel_ms": kern_ms,
             "bytes_per_launch": algo_bytes}
 

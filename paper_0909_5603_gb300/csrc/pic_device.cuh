@@ -137,8 +137,9 @@ struct FixedAcc {
         const float r = __fsub_rn(x, __fsub_rn(y, M));   // exact, |r| <= 1/2
         const float z = __fmaf_rn(r, 65536.0f, M);
         const int lo = __float_as_int(z) - 0x4B400000;
-        if (hi != 0) atomicAdd(H + idx, hi);
-        if (lo != 0) atomicAdd(L + idx, lo);
+        // unconditional: a zero add costs less than the branches around it
+        atomicAdd(H + idx, hi);
+        atomicAdd(L + idx, lo);
     }
 };
 

@@ -147,6 +147,23 @@ def test_filter_phase(ndim, bc, passes, prec, tol):
     compare_fields(g, o, [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ], tol)
 
 
+@pytest.mark.parametrize("ndim,n,bc", [(3, (40, 20, 150), (0, 1, 0)), (3, (36, 12, 70), (1, 0, 1)),
+                                       (3, (8, 8, 8), (0, 0, 0)), (2, (300, 1, 70), (1, 0, 0)), (2, (12, 1, 8), (0, 0, 0))])
+@pytest.mark.parametrize("passes", [2, 8])
+def test_filter_phase_many_tiles(ndim, n, bc, passes):
+    """The fused filter over several column blocks and plane segments with ragged ends,
+    up to the maximum number of passes, and on axes shorter than the pass halo (periodic
+    wrap several times around)."""
+    g, o = pair(ndim, n, bc, (1.0, 1.0, 1.0), 0.3, 1, FP64, passes=passes)
+    g.load_particles(np.zeros(0, np.int32), np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0))
+    rng = np.random.default_rng(10)
+    J = [rng.normal(size=(n[2], n[1], n[0])) for _ in range(3)]
+    set_fields_both(g, o, J, [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ])
+    g.run_phases(pic.PIC_PHASE_FILTER)
+    o.filter()
+    compare_fields(g, o, [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ], 1e-14)
+
+
 PARTICLE_CASES = [(nd, order, pusher, bcs) for nd in (3, 2) for order in (1, 2) for pusher in (VAY, BORIS)
                   for bcs in ("per", "abs")]
 
