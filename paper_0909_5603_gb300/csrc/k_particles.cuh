@@ -339,8 +339,8 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ SrcTable S;
     __shared__ uint64_t bar;
-    __shared__ int s_base[kBuckets], s_run[kBuckets];
-    __shared__ int s_cnt[2][kNW][kBuckets];  // double-buffered per chunk
+    __shared__ int s_run[kBuckets];          // running bucket totals of the tile (warp 0)
+    __shared__ int s_cnt[2][kNW][kBuckets];  // per-warp bucket counts, double-buffered per chunk
 
     const int g = blockIdx.x;
     const int ii = find_instance(L.tile_start, L.ninst, g);
@@ -567,46 +567,50 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             cell_new = cn[0] + I.n[0] * (cn[1] + I.n[1] * cn[2]);
         }
 
-        // ---- stable ranking of the chunk by bucket: order (warp, lane).  s_cnt[cb] was
-        // cleared during the previous chunk (or at the start); two barriers per chunk.
+        // ---- stable ranking of the chunk by bucket: order (warp, lane), one barrier per
+        // chunk.  Each warp writes its bucket counts into its own row of s_cnt[cbuf]
+        // (cleared by that warp first: the row was last read in chunk r - 2, before the
+        // barrier of chunk r - 1), and after the barrier every warp forms the offsets it
+        // needs itself: lane d sums bucket d over the warps (its own prefix and the total),
+        // and a scan over the lanes gives the bucket bases.  Warp 0 keeps the running
+        // bucket totals of the tile and writes the chunk's records.
         const int cbuf = r & 1;
+        if (lane < kBuckets) s_cnt[cbuf][warp][lane] = 0;
+        __syncwarp();
         const unsigned peers = __match_any_sync(0xffffffffu, bucket);
         const int rank = __popc(peers & ((1u << lane) - 1u));
         if (bucket < kBuckets && lane == __ffs(peers) - 1) s_cnt[cbuf][warp][bucket] = __popc(peers);
         __syncthreads();
-        // every warp is past the previous chunk's reads: clear the other buffer
-        for (int e = tid; e < kNW * kBuckets; e += kNT) (&s_cnt[cbuf ^ 1][0][0])[e] = 0;
-        if (warp == 0) {
-            // lane d: exclusive offsets of bucket d over the warps, then over the buckets
-            int totd = 0;
-            if (lane < kBuckets) {
-                for (int ww = 0; ww < kNW; ++ww) {
-                    const int v = s_cnt[cbuf][ww][lane];
-                    s_cnt[cbuf][ww][lane] = totd;
-                    totd += v;
-                }
-            }
-            int incl = totd;
+        int totd = 0, below = 0;  // lane d: bucket d over all warps, and over the warps before this one
+        if (lane < kBuckets) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+            for (int ww = 0; ww < kNW; ++ww) {
+                const int v = s_cnt[cbuf][ww][lane];
+                below += ww < warp ? v : 0;
+                totd += v;
             }
+        }
+        int incl = totd;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int basev = incl - totd;  // lane d: first position of bucket d in the chunk
+        const int myoff = __shfl_sync(0xffffffffu, basev + below, bucket < kBuckets ? bucket : 0);
+        if (warp == 0) {
             const int c = chunk_out + r;
             if (lane < kBuckets) {
-                const int basev = incl - totd;
-                s_base[lane] = basev;
                 I.chunk_pre[out][(long long)c * kPre + lane] = basev;
                 I.chunk_cb[out][(long long)c * kBuckets + lane] = s_run[lane];
                 s_run[lane] += totd;
                 if (lane == kBuckets - 1) I.chunk_pre[out][(long long)c * kPre + kBuckets] = incl;
             }
         }
-        __syncthreads();
 
         // ---- write the particle out, partitioned by bucket
         if (bucket < kDead) {
-            const int p = seg_out + base + s_base[bucket] + s_cnt[cbuf][warp][bucket] + rank;
+            const int p = seg_out + base + myoff + rank;
             cell_out[p] = cell_new;
             off_out[0][p] = o1[0];
             if (ND == 3) off_out[1][p] = o1[1];
