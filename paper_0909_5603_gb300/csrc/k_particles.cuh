@@ -340,6 +340,10 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     __shared__ SrcTable S;
     __shared__ uint64_t bar;
     __shared__ int s_run[kBuckets];          // running bucket totals of the tile (warp 0)
+    // each thread's particle of the next chunk, copied in (cp.async) while the current
+    // chunk is processed; two buffers, chunk r in buffer r & 1
+    __shared__ int s_pcell[2][kNT];
+    __shared__ R s_poff[2][3][kNT], s_pu[2][3][kNT], s_pw[2][kNT];
     __shared__ int s_cnt[2][kNW][kBuckets];  // per-warp bucket counts, double-buffered per chunk
 
     const int g = blockIdx.x;
@@ -431,17 +435,39 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     R *w_out = (R *)I.w[out];
     int *id_out = I.id[out];
 
+    // stages this thread's particle of slot `sl` into buffer b of the s_p* arrays
+    // (asynchronously); returns its position in the input buffer, or -1
+    auto stage = [&](int sl, int b) -> int {
+        const int p = sl < count ? slot_position(I, in, S, sl) : -1;
+        if (p >= 0 && p < I.cap) {
+            cp_async<4>(&s_pcell[b][tid], cell_in + p);
+            cp_async<sizeof(R)>(&s_poff[b][0][tid], off_in[0] + p);
+            if (ND == 3) cp_async<sizeof(R)>(&s_poff[b][1][tid], off_in[1] + p);
+            cp_async<sizeof(R)>(&s_poff[b][2][tid], off_in[2] + p);
+            cp_async<sizeof(R)>(&s_pu[b][0][tid], u_in[0] + p);
+            cp_async<sizeof(R)>(&s_pu[b][1][tid], u_in[1] + p);
+            cp_async<sizeof(R)>(&s_pu[b][2][tid], u_in[2] + p);
+            cp_async<sizeof(R)>(&s_pw[b][tid], w_in + p);
+        }
+        cp_async_commit();
+        return p;
+    };
+    int pos_next = stage(tid, 0);
+
     for (int base = 0, r = 0; base < count; base += kChunk, ++r) {
         int bucket = 28;  // 0..26 direction, 27 dead, 28 no particle
         int cell_new = 0, pid = 0;
         R o1[3] = {R(0), R(0), R(0)}, u[3] = {R(0), R(0), R(0)}, w = R(0);
         const int slot = base + tid;
-        const int pos = slot < count ? slot_position(I, in, S, slot) : -1;
+        const int pos = pos_next;
+        const int pb = r & 1;
+        cp_async_wait_all();  // this thread's particle of this chunk has landed
+        if (base + kChunk < count) pos_next = stage(base + kChunk + tid, pb ^ 1);
         if (slot < count && (pos < 0 || pos >= I.cap)) atomicOr(I.err, kErrInternal);
         int l[3] = {0, 0, 0}, cc[3] = {0, 0, 0};
         bool have = false;
         if (pos >= 0 && pos < I.cap) {
-            const int c = __ldg(cell_in + pos);
+            const int c = s_pcell[pb][tid];
             const int cyz = fast_div(c, I.div_n0);
             cc[0] = c - cyz * I.n[0];
             cc[2] = fast_div(cyz, I.div_n1);
@@ -454,13 +480,13 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
         }
         if (have) {
             R o[3];
-            o[0] = __ldg(off_in[0] + pos);
-            o[1] = ND == 3 ? __ldg(off_in[1] + pos) : R(0);
-            o[2] = __ldg(off_in[2] + pos);
-            u[0] = __ldg(u_in[0] + pos);
-            u[1] = __ldg(u_in[1] + pos);
-            u[2] = __ldg(u_in[2] + pos);
-            w = __ldg(w_in + pos);
+            o[0] = s_poff[pb][0][tid];
+            o[1] = ND == 3 ? s_poff[pb][1][tid] : R(0);
+            o[2] = s_poff[pb][2][tid];
+            u[0] = s_pu[pb][0][tid];
+            u[1] = s_pu[pb][1][tid];
+            u[2] = s_pu[pb][2][tid];
+            w = s_pw[pb][tid];
             pid = id_in ? __ldg(id_in + pos) : 0;
 
             // ---- gather (Yee positions: E_a staggered along a, B_a along the other two)

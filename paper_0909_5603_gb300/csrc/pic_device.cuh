@@ -430,6 +430,18 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap *map)
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
 }
 
+// Ampere-style asynchronous global -> shared copies of 4 or 8 bytes (cp.async), grouped
+// per thread: commit closes a group, wait_all waits for this thread's groups.
+template <int N>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src)
+{
+    static_assert(N == 4 || N == 8, "cp.async size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(smem_dst)), "l"(gmem_src), "n"(N)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
 {
     asm volatile(
