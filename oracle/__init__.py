@@ -103,6 +103,8 @@ def lib():
         L.orc_load_lab_frame.argtypes = [vp, ctypes.c_double, vp, vp, vp]
         L.orc_beam_self_field.restype = ctypes.c_int
         L.orc_beam_self_field.argtypes = [vp, _f64p, ctypes.c_double, ctypes.c_double]
+        L.orc_station_record.restype = ctypes.c_int
+        L.orc_station_record.argtypes = [vp, ctypes.c_double, ctypes.c_double, _f64p, _f64p]
         L.orc_round_state_fp32.restype = None
         L.orc_round_state_fp32.argtypes = [vp]
         L.orc_ion_integral.restype = ctypes.c_double
@@ -238,6 +240,14 @@ class Sim:
         """Adds the self-field of node charge density rho (n2, n1, n0) moving at beta z."""
         r = np.ascontiguousarray(np.asarray(rho, np.float64).ravel())
         lib().orc_beam_self_field(self._h, r, float(gamma), float(beta))
+
+    def station_record(self, gamma_b, z_lab):
+        """Lab-frame station at z_lab now: (t_lab, fields (6, n2=1.., n1, n0)) or None."""
+        out = np.zeros(6 * self.n[0] * self.n[1])
+        t = np.zeros(1)
+        if not lib().orc_station_record(self._h, float(gamma_b), float(z_lab), out, t):
+            return None
+        return float(t[0]), out.reshape(6, self.n[1], self.n[0])
 
     def round_state_fp32(self):
         """Rounds the stored state to FP32 (the storage of an FP32 implementation)."""

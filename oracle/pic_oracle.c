@@ -863,6 +863,46 @@ void orc_div_e(const orc_sim *s, double *out)
                                               dbwd(s, ORC_EZ, 2, i, j, k);
 }
 
+/* ------------------------------------------------------------------------------------
+ * Lab-frame station (Sec. 2, reading): a plane z = z_lab immobile in the laboratory
+ * frame.  Lab and boosted frames share their origin (z = z' = 0 at t = t' = 0) and the
+ * boost is along +z, so at boosted time t' the plane sits at z' = z_lab / g - b t' and the
+ * lab time there is t = t' / g + b z_lab.  The station samples every field component at
+ * its own transverse Yee position, interpolating linearly in z' between the two grid
+ * planes of that component's z stagger around z' (zero beyond an absorbing face, wrapped
+ * on a periodic axis), and transforms the sample back to the lab frame (a boost by -b):
+ *   E_x = g (E'_x + b B'_y),  E_y = g (E'_y - b B'_x),  E_z = E'_z,
+ *   B_x = g (B'_x - b E'_y),  B_y = g (B'_y + b E'_x),  B_z = B'_z.
+ * t' is s->step dt: E and B after `step` full steps.  Returns 1 and fills out[6][n1][n0]
+ * and *t_lab when z' lies in [0, n2 dz), else 0.
+ * ---------------------------------------------------------------------------------- */
+int orc_station_record(const orc_sim *s, double gb, double z_lab, double *out, double *t_lab)
+{
+    double b = boost_beta(gb);
+    double tp = (double)s->step * s->dt;
+    double zp = z_lab / gb - b * tp;
+    double Lz = s->n[2] * s->dx[2];
+    if (!(zp >= 0.0 && zp < Lz)) return 0;
+    int64_t plane = (int64_t)s->n[0] * s->n[1];
+    for (int j = 0; j < s->n[1]; ++j)
+        for (int i = 0; i < s->n[0]; ++i) {
+            double f[6];
+            for (int c = ORC_EX; c <= ORC_BZ; ++c) {
+                /* z' in units of the component's own grid planes */
+                double q = zp / s->dx[2] - STAG[c][2];
+                double k = floor(q);
+                double fr = q - k;
+                f[c] = (1.0 - fr) * fget(s, c, i, j, (int)k) + fr * fget(s, c, i, j, (int)k + 1);
+            }
+            double g = gb;
+            double lab[6] = {g * (f[ORC_EX] + b * f[ORC_BY]), g * (f[ORC_EY] - b * f[ORC_BX]), f[ORC_EZ],
+                             g * (f[ORC_BX] - b * f[ORC_EY]), g * (f[ORC_BY] + b * f[ORC_EX]), f[ORC_BZ]};
+            for (int c = 0; c < 6; ++c) out[(int64_t)c * plane + (int64_t)j * s->n[0] + i] = lab[c];
+        }
+    *t_lab = tp / gb + b * z_lab;
+    return 1;
+}
+
 /* Test helper: rounds the stored state (offsets, momenta, weights, E, B) to FP32, as an
  * FP32 implementation stores it between steps; offsets that round to 1 keep the largest
  * float below 1 (same cell).  Calling it after every step gives the error floor that FP32

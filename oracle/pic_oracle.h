@@ -71,6 +71,10 @@ double orc_ion_integral(const orc_sim *s, double a, double b);
  * (Lorentz factor gamma) along z: relativistic Poisson solve, E = -grad phi with the z
  * part over gamma^2, B = beta z x E.  Returns 0. */
 int orc_beam_self_field(orc_sim *s, const double *rho, double gamma, double beta);
+/* Lab-frame station z = z_lab at the current step: fills out[6][n1][n0] (lab-frame Ex Ey
+ * Ez Bx By Bz at the plane, each at its transverse Yee position) and *t_lab; returns 1,
+ * or 0 when the plane lies outside the box now. */
+int orc_station_record(const orc_sim *s, double gamma_b, double z_lab, double *out, double *t_lab);
 /* Test helper: rounds offsets (kept below 1), momenta, weights, E and B to FP32. */
 void orc_round_state_fp32(orc_sim *s);
 
