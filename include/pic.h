@@ -252,6 +252,28 @@ pic_status pic_synchronize(pic_ctx *ctx);
  * pic_set_profiling, pic_get_timings and pic_destroy accept a batch. */
 pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx **batch);
 
+/* Lab-frame stations (Sec. 2: the results are recorded at planes immobile in the
+ * laboratory frame and transformed back to it).  Replaces the stations with `count`
+ * planes z = z_lab[i] (lab coordinates; lab and boosted frames share their origin at
+ * t = t' = 0, boost along +z), each holding up to max_records records (count = 0 removes
+ * them).  At boosted time t' a plane sits at z' = z_lab / gamma_b - beta_b t'; after the
+ * load or pic_set_stations, and after every full step (pic_step, or pic_run_phases with
+ * PIC_PHASE_ALL), every station whose plane lies in the box records: each field
+ * component at its own transverse Yee position, interpolated linearly in z' between the
+ * two planes of its z stagger (zero beyond an absorbing face, wrapped on a periodic
+ * axis), transformed back to the lab frame (E_x = g (E'_x + b B'_y), E_y = g (E'_y -
+ * b B'_x), B_x = g (B'_x - b E'_y), B_y = g (B'_y + b E'_x), z components unchanged), with
+ * its lab time t'/gamma_b + beta_b z_lab.  FP64 arithmetic, stored in the working
+ * precision.  A new load restarts every station's history.  Device memory: 6 n0 n1
+ * values per record.  Not valid on a batch (PIC_ERR_ARG). */
+pic_status pic_set_stations(pic_ctx *ctx, int count, const double *z_lab, int max_records);
+
+/* Copies station `station`'s history: *n_records; t_lab[n_records] (may be NULL, else
+ * t_count >= n_records); fields[n_records][6][n1][n0] as Ex Ey Ez Bx By Bz (may be NULL,
+ * else f_count >= n_records 6 n0 n1).  Synchronises. */
+pic_status pic_get_station(pic_ctx *ctx, int station, int *n_records, double *t_lab, size_t t_count, double *fields,
+                           size_t f_count);
+
 /* Autotuner: picks the particle tile shape for a workload by measurement (the paper has
  * no counterpart; it tunes this implementation).  For every candidate tile (3D: 8^3,
  * 16x8x8, 8x8x16, 8x16x8, 16x16x4, 16x8x4, 8x8x4, 4x8x8, 16x16x8, 32x8x4; 2D: 16x16,

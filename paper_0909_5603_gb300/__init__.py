@@ -32,7 +32,8 @@ PIC_PHASE_PARTICLES, PIC_PHASE_FILTER, PIC_PHASE_MAXWELL, PIC_PHASE_ALL = 1, 2, 
 EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error", "pic_load_lab_frame",
             "pic_load_particles", "pic_set_field", "pic_step", "pic_run_phases", "pic_get_field",
             "pic_num_particles", "pic_get_particles", "pic_get_diagnostics", "pic_set_profiling",
-            "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc", "pic_autotune"]
+            "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc", "pic_autotune",
+            "pic_set_stations", "pic_get_station"]
 PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
@@ -141,6 +142,10 @@ def lib():
         L.pic_batch_create.argtypes = [ctypes.c_int, P(vp), P(vp)]
         L.pic_get_rho_noalloc.restype = st
         L.pic_get_rho_noalloc.argtypes = [vp, vp, ctypes.c_size_t]
+        L.pic_set_stations.restype = st
+        L.pic_set_stations.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+        L.pic_get_station.restype = st
+        L.pic_get_station.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), vp, ctypes.c_size_t, vp, ctypes.c_size_t]
         L.pic_autotune.restype = st
         L.pic_autotune.argtypes = [P(pic_grid), P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    P(pic_options), P(pic_laser_lab), P(pic_plasma_lab), P(pic_beam_lab), ctypes.c_int,
@@ -320,6 +325,21 @@ class Simulation:
         la, pl, be = _lab_structs(laser, plasma, beam)
         _check(lib().pic_load_lab_frame(self.h, ctypes.byref(la) if la else None, ctypes.byref(pl) if pl else None,
                                         ctypes.byref(be) if be else None), self.h)
+
+    def set_stations(self, z_lab, max_records):
+        """pic_set_stations: lab-frame stations at the planes z_lab."""
+        z = np.ascontiguousarray(z_lab, dtype=np.float64)
+        self._stations = z.size
+        _check(lib().pic_set_stations(self.h, z.size, _ptr(z), int(max_records)), self.h)
+
+    def station(self, i):
+        """History of station i: (t_lab (n,), fields (n, 6, n1, n0)) in the lab frame."""
+        n = ctypes.c_int(0)
+        _check(lib().pic_get_station(self.h, i, ctypes.byref(n), None, 0, None, 0), self.h)
+        t = np.zeros(n.value)
+        f = np.zeros((n.value, 6, self.n[1], self.n[0]))
+        _check(lib().pic_get_station(self.h, i, ctypes.byref(n), _ptr(t), t.size, _ptr(f), f.size), self.h)
+        return t, f
 
     def set_field(self, comp, arr):
         a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(-1))

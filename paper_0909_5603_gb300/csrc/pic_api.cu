@@ -60,6 +60,11 @@ struct pic_ctx {
     bool loaded = false;
     int64_t step = 0;
     int last_filtered = 0;
+    // lab-frame stations
+    int nst = 0, st_max = 0;
+    double *d_st_z = nullptr, *d_st_t = nullptr;
+    int *d_st_count = nullptr;
+    void *d_st_fields = nullptr;
     // scratch
     double *d_dense = nullptr;   // ncell doubles (field exchange)
     double *d_sums = nullptr;    // diagnostics sums
@@ -355,6 +360,8 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     h.absorb_cells = o.absorb_cells;
     h.absorb_strength = o.absorb_strength;
     h.dt = dt;
+    h.gb = gamma_boost;
+    h.beta_b = std::sqrt(1.0 - 1.0 / (gamma_boost * gamma_boost));
     h.q = o.charge;
     h.m = o.mass;
     h.jscale = h.jinv = 1.0f;  // until a load sets the FP32 current scale
@@ -683,7 +690,14 @@ static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg, double wm
     c->step = 0;
     c->last_filtered = 0;
     destroy_graph(c);
-    return upload_inst(c);
+    pic_status st = upload_inst(c);
+    if (st != PIC_OK || c->nst == 0) return st;
+    // stations start a new history with the loaded state as its first record
+    CUDA_OR_FAIL(c, cudaMemset(c->d_st_count, 0, sizeof(int) * c->nst));
+    StationDev S{c->d_st_z, c->d_st_count, c->d_st_t, c->d_st_fields, c->st_max};
+    CUDA_OR_FAIL(c, launch_stations(c->fp64, c->d_inst, S, c->nst, c->n[0] * c->n[1], c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
 }
 
 // Host particles (FP64, any order): validated, laid out in the canonical order with a
@@ -961,6 +975,13 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
                 launches++;
             }
         tm.end(3);
+    }
+    if (mask == PIC_PHASE_ALL && c->nst > 0 && !c->is_batch) {
+        tm.begin(4);
+        StationDev S{c->d_st_z, c->d_st_count, c->d_st_t, c->d_st_fields, c->st_max};
+        CUDA_OR_FAIL(c, launch_stations(fp64, c->d_inst, S, c->nst, c->n[0] * c->n[1], c->stream));
+        tm.end(4);
+        launches += 2;
     }
     if (mask & (PIC_PHASE_FILTER | PIC_PHASE_MAXWELL)) {
         c->last_filtered = filtered;
@@ -1244,6 +1265,83 @@ extern "C" pic_status pic_get_timings(pic_ctx *ctx, pic_timings *out)
 // ------------------------------------------------------------------------------------
 // batching
 // ------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------
+// lab-frame stations
+// ------------------------------------------------------------------------------------
+extern "C" pic_status pic_set_stations(pic_ctx *ctx, int count, const double *z_lab, int max_records)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_set_stations takes a member, not a batch");
+    if (count < 0 || (count > 0 && (!z_lab || max_records < 1)))
+        return fail(ctx, PIC_ERR_ARG, "need count >= 0, z_lab and max_records >= 1");
+    for (int i = 0; i < count; ++i)
+        if (!std::isfinite(z_lab[i])) return fail(ctx, PIC_ERR_NAN, "station %d position not finite", i);
+    cudaSetDevice(ctx->device);
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, ctx->d_st_z);
+    dfree(ctx, ctx->d_st_t);
+    dfree(ctx, ctx->d_st_count);
+    dfree(ctx, ctx->d_st_fields);
+    ctx->d_st_z = ctx->d_st_t = nullptr;
+    ctx->d_st_count = nullptr;
+    ctx->d_st_fields = nullptr;
+    ctx->nst = 0;
+    ctx->st_max = 0;
+    destroy_graph(ctx);
+    if (count == 0) return PIC_OK;
+    const size_t plane = (size_t)ctx->n[0] * ctx->n[1];
+    ctx->d_st_z = (double *)dalloc(ctx, sizeof(double) * count);
+    ctx->d_st_t = (double *)dalloc(ctx, sizeof(double) * count * (size_t)max_records);
+    ctx->d_st_count = (int *)dalloc(ctx, sizeof(int) * count);
+    ctx->d_st_fields = dalloc(ctx, ctx->es * 6 * plane * count * (size_t)max_records);
+    if (!ctx->d_st_z || !ctx->d_st_t || !ctx->d_st_count || !ctx->d_st_fields)
+        return fail(ctx, PIC_ERR_OOM, "no device memory for %d stations x %d records", count, max_records);
+    CUDA_OR_FAIL(ctx, cudaMemcpy(ctx->d_st_z, z_lab, sizeof(double) * count, cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(ctx, cudaMemset(ctx->d_st_count, 0, sizeof(int) * count));
+    ctx->nst = count;
+    ctx->st_max = max_records;
+    if (ctx->loaded) {  // the current state is the first record
+        StationDev S{ctx->d_st_z, ctx->d_st_count, ctx->d_st_t, ctx->d_st_fields, ctx->st_max};
+        CUDA_OR_FAIL(ctx, launch_stations(ctx->fp64, ctx->d_inst, S, ctx->nst, (int)plane, ctx->stream));
+        CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_station(pic_ctx *ctx, int station, int *n_records, double *t_lab, size_t t_count,
+                                      double *fields, size_t f_count)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_get_station takes a member, not a batch");
+    if (station < 0 || station >= ctx->nst) return fail(ctx, PIC_ERR_ARG, "no station %d", station);
+    if (!n_records) return fail(ctx, PIC_ERR_ARG, "n_records is NULL");
+    cudaSetDevice(ctx->device);
+    pic_status st = pic_synchronize(ctx);
+    if (st != PIC_OK) return st;
+    int n = 0;
+    CUDA_OR_FAIL(ctx, cudaMemcpy(&n, ctx->d_st_count + station, sizeof(int), cudaMemcpyDeviceToHost));
+    *n_records = n;
+    const size_t plane = (size_t)ctx->n[0] * ctx->n[1];
+    if (t_lab) {
+        if (t_count < (size_t)n) return fail(ctx, PIC_ERR_ARG, "t_lab needs room for %d values", n);
+        CUDA_OR_FAIL(ctx, cudaMemcpy(t_lab, ctx->d_st_t + (size_t)station * ctx->st_max, sizeof(double) * n,
+                                     cudaMemcpyDeviceToHost));
+    }
+    if (fields) {
+        const size_t need = (size_t)n * 6 * plane;
+        if (f_count < need) return fail(ctx, PIC_ERR_ARG, "fields needs room for %zu values", need);
+        const unsigned char *src = (const unsigned char *)ctx->d_st_fields + (size_t)station * ctx->st_max * 6 * plane * ctx->es;
+        if (ctx->fp64) {
+            CUDA_OR_FAIL(ctx, cudaMemcpy(fields, src, sizeof(double) * need, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> tmp(need);
+            CUDA_OR_FAIL(ctx, cudaMemcpy(tmp.data(), src, sizeof(float) * need, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < need; ++i) fields[i] = tmp[i];
+        }
+    }
+    return PIC_OK;
+}
+
 static pic_status refresh_batch(pic_ctx *c)
 {
     bool stale = c->member_versions.size() != c->members.size();

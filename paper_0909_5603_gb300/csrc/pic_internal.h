@@ -114,6 +114,7 @@ struct InstDev {
     double ion_n0, ion_zs, ion_ramp, ion_gb, ion_beta;
     void *ion_face;     // [n[2]] this step's ion current on the Jz faces (working precision)
     int *phase;         // particle phases run since the last load (device counter)
+    double gb, beta_b;  // the frame's boost: Lorentz factor and velocity
     int box[3];         // TMA box extents (elements)
     int box_lo[3];      // box origin relative to the tile origin (cells, <= 0)
     int jlo;            // J tile origin relative to the tile origin (-1 or -2)
@@ -180,7 +181,17 @@ struct PlasmaGen {
     uint64_t seed;
 };
 
+// Lab-frame stations of one instance (k_stations.cu): device arrays
+struct StationDev {
+    const double *z_lab;  // [nst]
+    int *count;           // [nst] records taken
+    double *t_lab;        // [nst][max_records]
+    void *fields;         // [nst][max_records][6][n1][n0], working precision
+    int max_records;
+};
+
 // host-side launchers
+cudaError_t launch_stations(int fp64, const InstDev *d_inst, const StationDev &S, int nst, int plane, cudaStream_t s);
 cudaError_t launch_place(int fp64, const InstDev &I, const PlaceSrc &s, cudaStream_t st);
 cudaError_t launch_plasma_count(const PlasmaGen &G, int *count, cudaStream_t st);
 cudaError_t launch_plasma_write(int fp64, const InstDev &I, const PlasmaGen &G, const int *slot0, const int *id0,
