@@ -25,6 +25,7 @@ _HDR = [os.path.join(_HERE, "pic_oracle.h")]
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ = range(9)
 PERIODIC, ABSORBING = 0, 1
 VAY, BORIS = 0, 1
+SOLVER_YEE, SOLVER_CK = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -103,6 +104,8 @@ def lib():
         L.orc_load_lab_frame.argtypes = [vp, ctypes.c_double, vp, vp, vp]
         L.orc_beam_self_field.restype = ctypes.c_int
         L.orc_beam_self_field.argtypes = [vp, _f64p, ctypes.c_double, ctypes.c_double]
+        L.orc_set_solver.restype = None
+        L.orc_set_solver.argtypes = [vp, ctypes.c_int]
         L.orc_station_record.restype = ctypes.c_int
         L.orc_station_record.argtypes = [vp, ctypes.c_double, ctypes.c_double, _f64p, _f64p]
         L.orc_round_state_fp32.restype = None
@@ -161,7 +164,7 @@ class Sim:
     """One FP64 CPU simulation instance (same conventions as the CUDA library)."""
 
     def __init__(self, ndim, n, bc, dx, dt, order=1, pusher=VAY, filter_passes=0,
-                 tile=(8, 8, 8), q=-1.0, m=1.0, absorb_cells=16, absorb_strength=0.1):
+                 tile=(8, 8, 8), q=-1.0, m=1.0, absorb_cells=16, absorb_strength=0.1, solver=0):
         n = list(n)
         if ndim == 2:
             n[1] = 1
@@ -170,6 +173,8 @@ class Sim:
         self.ncell = self.n[0] * self.n[1] * self.n[2]
         self._h = lib().orc_create(ndim, _I3(*self.n), _I3(*bc), _D3(*dx), dt, order, pusher,
                                    filter_passes, _I3(*tile), q, m, absorb_cells, absorb_strength)
+        if solver:
+            lib().orc_set_solver(self._h, int(solver))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

@@ -45,6 +45,7 @@ struct orc_sim {
     int ion;
     double ion_n0, ion_zs, ion_ramp, ion_gb, ion_beta;
     int64_t n_pp; /* particle phases run since the last load */
+    int solver;   /* ORC_SOLVER_YEE or ORC_SOLVER_CK */
 };
 
 /* Yee staggering (in cells) of each component along each axis. */
@@ -742,6 +743,41 @@ static double dbwd(const orc_sim *s, int comp, int a, int i, int j, int k)
     return (fget(s, comp, i, j, k) - fget(s, comp, p[0], p[1], p[2])) / s->dx[a];
 }
 
+/* ------------------------------------------------------------------------------------
+ * Low-dispersion solver (Sec. 2 names low-dispersion electromagnetic solvers as one cure
+ * of the boosted-frame instability, citing Karkkainen et al., ICAP 2006; reading): in the
+ * Faraday update every forward difference along axis a is averaged over the two other
+ * axes, weight 7/12 on the difference itself, 1/12 on each of its four edge neighbours
+ * and 1/48 on each of its four corner neighbours (an invariant axis folds its neighbours
+ * onto the centre: 3/4 and 1/8 in 2D3V).  In Fourier space the difference along a is
+ * multiplied by
+ *   S_a = 7/12 + (1/6) (cos th_b + cos th_c) + (1/12) cos th_b cos th_c,  th = k dx,
+ * which lies in [1/3, 1] (no mode loses its Faraday coupling), so for fields with
+ * discrete div E = 0 the dispersion relation is
+ *   sin^2(w dt / 2) / dt^2 = sum_a S_a sin^2(k_a dx_a / 2) / dx_a^2:
+ * a wave along the axis of the smallest cell travels without dispersion at dt equal to
+ * that cell, and the scheme is stable up to dt = min_a dx_a (the Yee limit is
+ * 1 / sqrt(sum_a 1 / dx_a^2)).  Ampere's law keeps the Yee differences.
+ * ---------------------------------------------------------------------------------- */
+static double dfwd_ck(const orc_sim *s, int comp, int a, int i, int j, int k)
+{
+    if (!s->active[a]) return 0.0;
+    int b = (a + 1) % 3, c = (a + 2) % 3;
+    double sum = 0.0;
+    for (int db = -1; db <= 1; ++db)
+        for (int dc = -1; dc <= 1; ++dc) {
+            int p[3] = {i, j, k};
+            p[b] += db; /* on an invariant axis this is the same cell */
+            p[c] += dc;
+            int edges = (db != 0) + (dc != 0);
+            double w = edges == 0 ? 7.0 / 12.0 : (edges == 1 ? 1.0 / 12.0 : 1.0 / 48.0);
+            sum += w * dfwd(s, comp, a, p[0], p[1], p[2]);
+        }
+    return sum;
+}
+
+void orc_set_solver(orc_sim *s, int solver) { s->solver = solver; }
+
 /* B <- B - h curl E (h = dt / 2), optionally damped afterwards. */
 static void half_b(orc_sim *s, int damp)
 {
@@ -753,9 +789,10 @@ static void half_b(orc_sim *s, int damp)
         for (int j = 0; j < s->n[1]; ++j)
             for (int i = 0; i < s->n[0]; ++i) {
                 int64_t id = node_index(s, i, j, k);
-                double cx = dfwd(s, ORC_EZ, 1, i, j, k) - dfwd(s, ORC_EY, 2, i, j, k);
-                double cy = dfwd(s, ORC_EX, 2, i, j, k) - dfwd(s, ORC_EZ, 0, i, j, k);
-                double cz = dfwd(s, ORC_EY, 0, i, j, k) - dfwd(s, ORC_EX, 1, i, j, k);
+                double (*d)(const orc_sim *, int, int, int, int, int) = s->solver == ORC_SOLVER_CK ? dfwd_ck : dfwd;
+                double cx = d(s, ORC_EZ, 1, i, j, k) - d(s, ORC_EY, 2, i, j, k);
+                double cy = d(s, ORC_EX, 2, i, j, k) - d(s, ORC_EZ, 0, i, j, k);
+                double cz = d(s, ORC_EY, 0, i, j, k) - d(s, ORC_EX, 1, i, j, k);
                 int c[3] = {i, j, k};
                 double f = damp ? damp_factor(s, c) : 1.0;
                 nb[0][id] = f * (s->f[ORC_BX][id] - h * cx);

@@ -28,6 +28,7 @@ extern "C" {
 enum { ORC_EX, ORC_EY, ORC_EZ, ORC_BX, ORC_BY, ORC_BZ, ORC_JX, ORC_JY, ORC_JZ, ORC_NCOMP };
 enum { ORC_PERIODIC = 0, ORC_ABSORBING = 1 };
 enum { ORC_VAY = 0, ORC_BORIS = 1 };
+enum { ORC_SOLVER_YEE = 0, ORC_SOLVER_CK = 1 };
 
 typedef struct orc_sim orc_sim;
 
@@ -75,6 +76,9 @@ int orc_beam_self_field(orc_sim *s, const double *rho, double gamma, double beta
  * Ez Bx By Bz at the plane, each at its transverse Yee position) and *t_lab; returns 1,
  * or 0 when the plane lies outside the box now. */
 int orc_station_record(const orc_sim *s, double gamma_b, double z_lab, double *out, double *t_lab);
+/* Field solver: ORC_SOLVER_YEE (default) or ORC_SOLVER_CK, the low-dispersion solver
+ * (Faraday differences averaged over their transverse neighbours, 7/12, 1/12, 1/48). */
+void orc_set_solver(orc_sim *s, int solver);
 /* Test helper: rounds offsets (kept below 1), momenta, weights, E and B to FP32. */
 void orc_round_state_fp32(orc_sim *s);
 
