@@ -456,6 +456,42 @@ def precision_sweep(pic, torch, args):
     return out
 
 
+def instability_study(pic, torch, args):
+    """Boosted-frame numerical instability (Sec. 2: a short-wavelength instability whose
+    growth rises with the boost and the inverse resolution, controlled with low-dispersion
+    solvers and low-pass filtering): the LWFA stage downscaled to 32 x 32 x 256 cells with
+    a 2-period laser, cold plasma with its ions, FP32, for each boost, solver and number of
+    filter passes; reports max |E| after `--study-steps` steps over its value after 10
+    steps (the laser's), and the field energy ratio.  Yee runs at dt = dz/2 capped at 0.9
+    of its Courant limit; the low-dispersion solver at dt = 0.9 min(dx, dz)."""
+    rows = []
+    for gb in [float(g) for g in args.sweep_gammas.split(",")]:
+        w = synth.lwfa_stage((32, 32, 256), gb, 2)
+        lz = w["n"][2] * w["dx"][2]
+        doppler = gb * (1 + math.sqrt(1 - 1 / gb ** 2))
+        laser = (2.0, 1.0, 20.0, 2.0, 0.5 * lz / doppler)
+        for solver, name in ((pic.PIC_SOLVER_YEE, "yee"), (pic.PIC_SOLVER_CK, "ck")):
+            dt = w["dt"] if solver == pic.PIC_SOLVER_YEE else 0.9 * min(w["dx"][0], w["dx"][2])
+            for passes in (0, 3):
+                sim = pic.Simulation(3, w["n"], (1, 1, 1), w["dx"], dt, gamma_boost=gb, order=2,
+                                     precision=pic.PIC_PREC_FP32, filter_passes=passes, tile=(8, 8, 8),
+                                     track_ids=False, solver=solver, absorb_cells=8)
+                sim.load_lab_frame(laser=laser, plasma=w["plasma"])
+                sim.step(10)
+                e0 = max(np.abs(sim.get_field(c)).max() for c in (pic.PIC_EX, pic.PIC_EY, pic.PIC_EZ))
+                f0 = sim.diagnostics()["field_energy"]
+                sim.step(args.study_steps - 10)
+                e1 = max(np.abs(sim.get_field(c)).max() for c in (pic.PIC_EX, pic.PIC_EY, pic.PIC_EZ))
+                f1 = sim.diagnostics()["field_energy"]
+                row = {"gamma_boost": gb, "solver": name, "filter_passes": passes, "dt": dt,
+                       "steps": args.study_steps, "max_E_growth": e1 / e0, "field_energy_ratio": f1 / f0}
+                rows.append(row)
+                print(json.dumps(row), flush=True)
+                del sim
+                torch.cuda.empty_cache()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,13 +506,22 @@ def main():
                     help="instead of the benchmark: FP32 vs FP64 on the LWFA stage at 256x256x2048, 4 ppc, per boost")
     ap.add_argument("--sweep-gammas", default="2,5,13,30,100")
     ap.add_argument("--sweep-steps", type=int, default=100)
+    ap.add_argument("--instability-study", action="store_true",
+                    help="instead of the benchmark: field growth per boost, solver and filter passes")
+    ap.add_argument("--study-steps", type=int, default=400)
     ap.add_argument("--nz", type=int, default=N_GRID[2],
                     help="cells along z (a shorter slab of the same workload, for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     rank, world = dist_init()
-    if args.precision_sweep:
+    if args.instability_study:
+        import torch
+
+        import paper_0909_5603_gb300 as pic
+        pic.build()
+        print(json.dumps({"instability_study": instability_study(pic, torch, args)}))
+    elif args.precision_sweep:
         import torch
 
         import paper_0909_5603_gb300 as pic

@@ -66,6 +66,7 @@ typedef enum {
 enum { PIC_PERIODIC = 0, PIC_ABSORBING = 1 };
 enum { PIC_PREC_FP32 = 0, PIC_PREC_FP64 = 1 };
 enum { PIC_PUSHER_VAY = 0, PIC_PUSHER_BORIS = 1 };
+enum { PIC_SOLVER_YEE = 0, PIC_SOLVER_CK = 1 };
 enum {
     PIC_EX = 0, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ,
     PIC_RHO = 9, /* charge density on the nodes: particles + ion background (getter only) */
@@ -104,6 +105,15 @@ typedef struct {
     void *alloc_user;
     void *stream;           /* cudaStream_t used for all work; NULL = legacy stream */
     int device;             /* CUDA device ordinal (default: the current device) */
+    int solver;             /* PIC_SOLVER_YEE (default): the Yee scheme, Courant limit
+                               1 / sqrt(sum_a 1/dx_a^2).  PIC_SOLVER_CK: the low-dispersion
+                               solver Sec. 2 uses against the boosted-frame instability
+                               (after Karkkainen et al.): every difference of the Faraday
+                               update averaged over its transverse neighbours, 7/12 on
+                               itself, 1/12 on the four edge and 1/48 on the four corner
+                               neighbours (3/4, 1/8 in 2D3V); dispersion-free along the axis
+                               of the smallest cell at dt equal to it, Courant limit
+                               min_a dx_a.  Ampere's law keeps the Yee differences. */
 } pic_options;
 
 typedef struct {

@@ -26,6 +26,7 @@ PIC_ERR_PARTICLE_SPEED, PIC_ERR_TIMEOUT, PIC_ERR_NAN, PIC_ERR_UNSUPPORTED, PIC_E
 PIC_PERIODIC, PIC_ABSORBING = 0, 1
 PIC_PREC_FP32, PIC_PREC_FP64 = 0, 1
 PIC_PUSHER_VAY, PIC_PUSHER_BORIS = 0, 1
+PIC_SOLVER_YEE, PIC_SOLVER_CK = 0, 1
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO, PIC_DIVE = range(11)
 PIC_PHASE_PARTICLES, PIC_PHASE_FILTER, PIC_PHASE_MAXWELL, PIC_PHASE_ALL = 1, 2, 4, 7
 
@@ -56,7 +57,7 @@ class pic_options(ctypes.Structure):
                 ("tile", ctypes.c_int * 3), ("threads", ctypes.c_int), ("absorb_cells", ctypes.c_int),
                 ("absorb_strength", ctypes.c_double), ("charge", ctypes.c_double), ("mass", ctypes.c_double),
                 ("track_ids", ctypes.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
-                ("stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("solver", ctypes.c_int)]
 
 
 class pic_diag(ctypes.Structure):
@@ -253,7 +254,7 @@ class Simulation:
     def __init__(self, ndim, n, bc, dx, dt, gamma_boost=1.0, order=1, precision=PIC_PREC_FP32,
                  pusher=PIC_PUSHER_VAY, filter_passes=0, tile=(0, 0, 0), absorb_cells=16,
                  absorb_strength=0.1, charge=-1.0, mass=1.0, track_ids=True, stream=None, device=None,
-                 use_torch_allocator=True):
+                 use_torch_allocator=True, solver=PIC_SOLVER_YEE):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required: the PIC step runs only in the sm_103a kernels")
@@ -278,6 +279,7 @@ class Simulation:
         opt.charge = charge
         opt.mass = mass
         opt.track_ids = 1 if track_ids else 0
+        opt.solver = solver
         opt.stream = self.stream.cuda_stream
         opt.device = self.device
         self._live = {}

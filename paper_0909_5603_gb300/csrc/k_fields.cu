@@ -60,6 +60,28 @@ __device__ __forceinline__ R damp_factor(const InstDev &I, const CellPos &c)
     return f;
 }
 
+// Forward difference of F along axis a at padded index p, averaged over the two
+// transverse axes with weights 7/12 (itself), 1/12 (edge neighbours), 1/48 (corners);
+// up / dn are the +1 / -1 neighbour offsets of the cell (wrapping on periodic axes, 0 on
+// an invariant one).
+template <typename R>
+__device__ __forceinline__ R ck_diff(const R *F, long long p, const long long up[3], const long long dn[3], int a)
+{
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    const long long ob[3] = {dn[b], 0, up[b]}, oc[3] = {dn[c], 0, up[c]};
+    R sum = R(0);
+#pragma unroll
+    for (int ib = 0; ib < 3; ++ib)
+#pragma unroll
+        for (int ic = 0; ic < 3; ++ic) {
+            const int edges = (ib != 1) + (ic != 1);
+            const R w = edges == 0 ? R(7.0 / 12.0) : (edges == 1 ? R(1.0 / 12.0) : R(1.0 / 48.0));
+            const long long q = p + ob[ib] + oc[ic];
+            sum += w * (F[q + up[a]] - F[q]);
+        }
+    return sum;
+}
+
 // B <- B - (dt/2) curl E  [then x damping on the second half of the step]
 template <typename R>
 __global__ void __launch_bounds__(256) k_bhalf(Launch L, int damp)
@@ -77,12 +99,29 @@ __global__ void __launch_bounds__(256) k_bhalf(Launch L, int damp)
     const R h = K.half_dt;
     const R ix = K.inv_dx[0], iy = K.inv_dx[1], iz = K.inv_dx[2];
     const long long p = c.p;
-    const R ex = Ex[p], ey = Ey[p], ez = Ez[p];
-    R dEz_dy = R(0), dEy_dz = (Ey[p + up[2]] - ey) * iz, dEx_dz = (Ex[p + up[2]] - ex) * iz;
-    R dEz_dx = (Ez[p + up[0]] - ez) * ix, dEy_dx = (Ey[p + up[0]] - ey) * ix, dEx_dy = R(0);
-    if (I.ndim == 3) {
-        dEz_dy = (Ez[p + up[1]] - ez) * iy;
-        dEx_dy = (Ex[p + up[1]] - ex) * iy;
+    R dEz_dy = R(0), dEy_dz, dEx_dz, dEz_dx, dEy_dx, dEx_dy = R(0);
+    if (I.solver == PIC_SOLVER_CK) {
+        // low-dispersion solver: each forward difference averaged over its transverse
+        // neighbours, 7/12 on itself, 1/12 on the edge and 1/48 on the corner ones (on
+        // an invariant axis the neighbours are the cell itself)
+        dEy_dz = ck_diff(Ey, p, up, dn, 2) * iz;
+        dEx_dz = ck_diff(Ex, p, up, dn, 2) * iz;
+        dEz_dx = ck_diff(Ez, p, up, dn, 0) * ix;
+        dEy_dx = ck_diff(Ey, p, up, dn, 0) * ix;
+        if (I.ndim == 3) {
+            dEz_dy = ck_diff(Ez, p, up, dn, 1) * iy;
+            dEx_dy = ck_diff(Ex, p, up, dn, 1) * iy;
+        }
+    } else {
+        const R ex = Ex[p], ey = Ey[p], ez = Ez[p];
+        dEy_dz = (Ey[p + up[2]] - ey) * iz;
+        dEx_dz = (Ex[p + up[2]] - ex) * iz;
+        dEz_dx = (Ez[p + up[0]] - ez) * ix;
+        dEy_dx = (Ey[p + up[0]] - ey) * ix;
+        if (I.ndim == 3) {
+            dEz_dy = (Ez[p + up[1]] - ez) * iy;
+            dEx_dy = (Ex[p + up[1]] - ex) * iy;
+        }
     }
     R bx = Bx[p] - h * (dEz_dy - dEy_dz);
     R by = By[p] - h * (dEx_dz - dEz_dx);

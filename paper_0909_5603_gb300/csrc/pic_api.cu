@@ -280,15 +280,20 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     if (shape_order != 1 && shape_order != 2) return fail(nullptr, PIC_ERR_ARG, "shape_order must be 1 or 2");
     if (!(gamma_boost >= 1.0) || !std::isfinite(gamma_boost)) return fail(nullptr, PIC_ERR_ARG, "gamma_boost must be >= 1");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, PIC_ERR_ARG, "dt must be finite and > 0");
-    double inv2 = 0.0;
-    for (int a = 0; a < 3; ++a)
-        if (activeaxis(grid->ndim, a)) inv2 += 1.0 / (dx[a] * dx[a]);
-    if (dt > 1.0 / std::sqrt(inv2) * (1.0 + 1e-12))
-        return fail(nullptr, PIC_ERR_CFL, "dt = %g exceeds the Courant limit %g", dt, 1.0 / std::sqrt(inv2));
-
     pic_options o;
     pic_default_options(&o);
     if (opt) o = *opt;
+    if (o.solver != PIC_SOLVER_YEE && o.solver != PIC_SOLVER_CK) return fail(nullptr, PIC_ERR_ARG, "solver invalid");
+    // Courant limit: Yee 1 / sqrt(sum_a 1/dx_a^2); the low-dispersion solver min_a dx_a
+    double inv2 = 0.0, dmin = 1e300;
+    for (int a = 0; a < 3; ++a)
+        if (activeaxis(grid->ndim, a)) {
+            inv2 += 1.0 / (dx[a] * dx[a]);
+            dmin = std::min(dmin, dx[a]);
+        }
+    const double courant = o.solver == PIC_SOLVER_CK ? dmin : 1.0 / std::sqrt(inv2);
+    if (dt > courant * (1.0 + 1e-12))
+        return fail(nullptr, PIC_ERR_CFL, "dt = %g exceeds the Courant limit %g", dt, courant);
     if (o.precision != PIC_PREC_FP32 && o.precision != PIC_PREC_FP64) return fail(nullptr, PIC_ERR_ARG, "precision invalid");
     if (o.pusher != PIC_PUSHER_VAY && o.pusher != PIC_PUSHER_BORIS) return fail(nullptr, PIC_ERR_ARG, "pusher invalid");
     if (o.filter_passes < 0 || o.filter_passes > 8) return fail(nullptr, PIC_ERR_ARG, "filter_passes must be 0..8");
@@ -357,6 +362,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     h.tile_base = 0;
     h.R = particle_chunk();
     h.filter_passes = o.filter_passes;
+    h.solver = o.solver;
     h.absorb_cells = o.absorb_cells;
     h.absorb_strength = o.absorb_strength;
     h.dt = dt;

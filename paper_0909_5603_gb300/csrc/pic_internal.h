@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/pic.h"
+
 namespace pic {
 
 constexpr int kGhost = 4;       // ghost layers per side of every active axis (fields)
@@ -78,6 +80,7 @@ struct InstDev {
     int cap;        // particle capacity per buffer
     int chunk_cap;  // chunk records per layout
     int filter_passes;
+    int solver;         // PIC_SOLVER_YEE or PIC_SOLVER_CK
     int absorb_cells;
     double absorb_strength;
     double dt, dx[3], q, m;
