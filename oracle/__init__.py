@@ -110,6 +110,10 @@ def lib():
         L.orc_station_record.argtypes = [vp, ctypes.c_double, ctypes.c_double, _f64p, _f64p]
         L.orc_round_state_fp32.restype = None
         L.orc_round_state_fp32.argtypes = [vp]
+        L.orc_set_injection.restype = None
+        L.orc_set_injection.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int32]
+        L.orc_num_frozen.restype = ctypes.c_int64
+        L.orc_num_frozen.argtypes = [vp]
         L.orc_ion_integral.restype = ctypes.c_double
         L.orc_ion_integral.argtypes = [vp, ctypes.c_double, ctypes.c_double]
         _lib = L
@@ -253,6 +257,14 @@ class Sim:
         if not lib().orc_station_record(self._h, float(gamma_b), float(z_lab), out, t):
             return None
         return float(t[0]), out.reshape(6, self.n[1], self.n[0])
+
+    def set_injection(self, gamma_b, z_lab, first_id=-1, enable=True):
+        """Beam injection through the lab plane z_lab: beam particles (id >= first_id, or
+        the last lab-frame load's beam) upstream of it are frozen."""
+        lib().orc_set_injection(self._h, int(bool(enable)), float(gamma_b), float(z_lab), int(first_id))
+
+    def num_frozen(self):
+        return int(lib().orc_num_frozen(self._h))
 
     def round_state_fp32(self):
         """Rounds the stored state to FP32 (the storage of an FP32 implementation)."""

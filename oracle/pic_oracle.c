@@ -46,6 +46,11 @@ struct orc_sim {
     double ion_n0, ion_zs, ion_ramp, ion_gb, ion_beta;
     int64_t n_pp; /* particle phases run since the last load */
     int solver;   /* ORC_SOLVER_YEE or ORC_SOLVER_CK */
+    /* beam injection through a lab-fixed plane (see orc_set_injection) */
+    int inj;
+    double inj_zb, inj_beta; /* the plane in this frame: z' = inj_zb - inj_beta t' */
+    int32_t inj_first;       /* first beam id, or -1: the beam of the last lab-frame load */
+    int32_t beam_id0;        /* first id of that beam (INT32_MAX: none) */
 };
 
 /* Yee staggering (in cells) of each component along each axis. */
@@ -227,6 +232,7 @@ orc_sim *orc_create(int ndim, const int n[3], const int bc[3], const double dx[3
     s->absorb_cells = absorb_cells;
     s->absorb_strength = absorb_strength;
     s->ncell = (int64_t)s->n[0] * s->n[1] * s->n[2];
+    s->beam_id0 = INT32_MAX;
     for (int c = 0; c < ORC_NCOMP; ++c) s->f[c] = (double *)calloc((size_t)s->ncell, sizeof(double));
     return s;
 }
@@ -284,6 +290,7 @@ int orc_set_particles(orc_sim *s, int64_t np, const int32_t *cell, const double 
             if (!(o >= 0.0 && o < 1.0)) return -2;
         }
     }
+    s->beam_id0 = INT32_MAX; /* no lab-frame beam */
     memcpy(s->cell, cell, (size_t)np * sizeof(int32_t));
     memcpy(s->off, off, (size_t)np * 3 * sizeof(double));
     memcpy(s->u, u, (size_t)np * 3 * sizeof(double));
@@ -608,6 +615,46 @@ static void add_ion_current(orc_sim *s)
     }
 }
 
+/* ------------------------------------------------------------------------------------
+ * Beam injection through a plane fixed in the laboratory (Sec. 2: the beam enters the
+ * boosted frame through a transverse lab-fixed plane that drifts in this frame, and the
+ * beam still upstream of it is represented by frozen macro-particles that drift).
+ * Reading: the lab plane z = z_lab sits in this frame at z' = z_lab / gamma_b - beta_b t';
+ * a beam particle (id >= first_id; first_id < 0: the beam of the last lab-frame load,
+ * whose ids follow the plasma's) whose position z'^n at t^n = n dt lies strictly upstream
+ * of the plane, z'^n / dz < (z_lab / gamma_b - beta_b t^n) / dz (compared in FP64 in cell
+ * units), is frozen for that step: no field acts on it (its momentum is kept), it moves
+ * at its own velocity and deposits its current like any particle, so the beam's charge
+ * near the plane is present for the space-charge field.  Downstream of the plane it is
+ * pushed as usual.  With a lab beam that drifts freely upstream of z_lab this reproduces
+ * the lab-frame history: a frozen particle's straight worldline is the lab one.
+ * ---------------------------------------------------------------------------------- */
+void orc_set_injection(orc_sim *s, int enable, double gamma_b, double z_lab, int32_t first_id)
+{
+    s->inj = enable != 0;
+    s->inj_zb = z_lab / gamma_b;
+    s->inj_beta = boost_beta(gamma_b);
+    s->inj_first = first_id;
+}
+
+static int frozen_at_plane(const orc_sim *s, int64_t p)
+{
+    if (!s->inj) return 0;
+    int32_t id0 = s->inj_first >= 0 ? s->inj_first : s->beam_id0;
+    if (s->id[p] < id0) return 0;
+    double zp = (s->inj_zb - s->inj_beta * ((double)s->n_pp * s->dt)) / s->dx[2];
+    int c[3];
+    cell_coords(s, s->cell[p], c);
+    return (double)c[2] + s->off[3 * p + 2] < zp;
+}
+
+int64_t orc_num_frozen(const orc_sim *s)
+{
+    int64_t n = 0;
+    for (int64_t p = 0; p < s->np; ++p) n += frozen_at_plane(s, p);
+    return n;
+}
+
 void orc_particle_phase(orc_sim *s)
 {
     for (int c = ORC_JX; c <= ORC_JZ; ++c) memset(s->f[c], 0, (size_t)s->ncell * sizeof(double));
@@ -617,11 +664,13 @@ void orc_particle_phase(orc_sim *s)
         double E[3], B[3];
         double *o = &s->off[3 * p];
         double *u = &s->u[3 * p];
-        orc_gather(s, s->cell[p], o, E, B);
-        if (s->pusher == ORC_VAY)
-            orc_push_vay(u, E, B, s->q / s->m, s->dt);
-        else
-            orc_push_boris(u, E, B, s->q / s->m, s->dt);
+        if (!frozen_at_plane(s, p)) {
+            orc_gather(s, s->cell[p], o, E, B);
+            if (s->pusher == ORC_VAY)
+                orc_push_vay(u, E, B, s->q / s->m, s->dt);
+            else
+                orc_push_boris(u, E, B, s->q / s->m, s->dt);
+        }
         double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         int c0[3], c1[3];
         double o0[3] = {o[0], o[1], o[2]}, o1[3];
@@ -1229,6 +1278,7 @@ int orc_load_lab_frame(orc_sim *s, double gb, const double *laser, const double 
             }
         }
     }
+    s->beam_id0 = beam ? next_id : INT32_MAX; /* beam ids follow the plasma's */
     if (beam) {
         int64_t first = s->np;
         int64_t nb = (int64_t)beam[0];

@@ -79,6 +79,13 @@ int orc_station_record(const orc_sim *s, double gamma_b, double z_lab, double *o
 /* Field solver: ORC_SOLVER_YEE (default) or ORC_SOLVER_CK, the low-dispersion solver
  * (Faraday differences averaged over their transverse neighbours, 7/12, 1/12, 1/48). */
 void orc_set_solver(orc_sim *s, int solver);
+/* Beam injection through the lab plane z = z_lab (in this frame z' = z_lab / gamma_b -
+ * beta_b t'): beam particles (id >= first_id; first_id < 0: the beam of the last
+ * lab-frame load) upstream of the plane are frozen (no field acts on them; they drift and
+ * deposit).  enable = 0 turns it off.  Kept across loads. */
+void orc_set_injection(orc_sim *s, int enable, double gamma_b, double z_lab, int32_t first_id);
+/* Particles frozen at the current step (upstream of the injection plane). */
+int64_t orc_num_frozen(const orc_sim *s);
 /* Test helper: rounds offsets (kept below 1), momenta, weights, E and B to FP32. */
 void orc_round_state_fp32(orc_sim *s);
 
