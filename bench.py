@@ -50,7 +50,7 @@ def workload(nz=N_GRID[2]):
 # sources are the ones that were captured
 PROFILE = os.path.join(ROOT, "profiles", "k_particles_lwfa_128x128x128.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0909_5603_gb300", "csrc", f)
-                  for f in ("k_particles.cuh", "pic_device.cuh", "k_push_f32.cu", "pic_internal.h")]
+                  for f in ("k_particles.cuh", "pic_device.cuh", "k_push.cuh", "k_push_f32.cu", "pic_internal.h")]
 
 
 def kernel_source_hash():
@@ -305,7 +305,8 @@ def run_ours(args, rank, world):
             "config": {"workload": f"boosted LWFA stage (3D laser wakefield), gamma_boost 13, 128x128x{args.nz} cells, "
                                    f"2 ppc = {n0:,} particles, order-2 shape, 3-pass 1-2-1 filter, Vay, "
                                    "FP32 + FP64 gamma solve",
-                       "particles": n0, "cells": ncell, "l2": "inputs larger than L2 (1.07 GB of particles)",
+                       "particles": n0, "cells": ncell, "l2": (f"inputs larger than L2 ({n0 * 32 / 1e9:.2f} GB of particles per buffer, L2 0.13 GB)"
+                              if n0 * 32 > 129e6 else f"inputs of {n0 * 32 / 1e9:.3f} GB fit in L2"),
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "cell_updates_per_s": ncell * args.steps * world / (ms_max * 1e-3),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64, "batched_scan": scan,

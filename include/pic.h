@@ -255,7 +255,7 @@ pic_status pic_get_timings(pic_ctx *ctx, pic_timings *out);
 pic_status pic_synchronize(pic_ctx *ctx);
 
 /* Groups n >= 1 instances created with identical ndim, shape order, precision, pusher,
- * tile, threads and device into a batch whose pic_step advances all of them in one
+ * field solver, tile, threads and device into a batch whose pic_step advances all of them in one
  * launch per phase (one flattened tile list over all instances), captured in one graph.
  * The members keep their own memory and stay readable with the getters; destroy the
  * batch before its members.  Only pic_step, pic_run_phases, pic_synchronize,
@@ -283,6 +283,26 @@ pic_status pic_set_stations(pic_ctx *ctx, int count, const double *z_lab, int ma
  * else f_count >= n_records 6 n0 n1).  Synchronises. */
 pic_status pic_get_station(pic_ctx *ctx, int station, int *n_records, double *t_lab, size_t t_count, double *fields,
                            size_t f_count);
+
+/* Beam injection through a plane fixed in the laboratory (Sec. 2: the beam enters the
+ * boosted frame through a transverse lab-fixed plane that drifts in this frame; the beam
+ * still upstream of it is carried by frozen, drifting macro-particles).
+ *  enable: 1 sets the plane, 0 removes it (z_lab and first_id ignored).
+ *  z_lab: lab position of the plane (finite); at boosted time t' it sits at
+ *    z' = z_lab / gamma_b - beta_b t'.
+ *  first_id: particles with id >= first_id are beam particles; first_id < 0 selects the
+ *    beam of the last pic_load_lab_frame (its ids follow the plasma's; no beam there:
+ *    no particle is frozen).
+ * At each particle phase (push time t^n = n dt, n = particle phases since the load), a
+ * beam particle whose z position in cells, k + offset, is below (z_lab / gamma_b -
+ * beta_b t^n) / dz (both in FP64) is frozen for that phase: no field acts on it (its
+ * momentum stays bit for bit), it moves at its own velocity and deposits its current like
+ * any particle, so the space charge of the beam upstream of the plane is present.
+ * Downstream of the plane it is pushed as usual.  With a lab beam drifting freely
+ * upstream of z_lab this reproduces the lab history: the frozen worldline is the lab one.
+ * The setting persists across loads.  Needs particle ids (track_ids; else
+ * PIC_ERR_STATE); not valid on a batch (PIC_ERR_ARG); z_lab not finite: PIC_ERR_ARG. */
+pic_status pic_set_injection(pic_ctx *ctx, int enable, double z_lab, int32_t first_id);
 
 /* Autotuner: picks the particle tile shape for a workload by measurement (the paper has
  * no counterpart; it tunes this implementation).  For every candidate tile (3D: 8^3,

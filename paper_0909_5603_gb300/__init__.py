@@ -34,7 +34,7 @@ EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error"
             "pic_load_particles", "pic_set_field", "pic_step", "pic_run_phases", "pic_get_field",
             "pic_num_particles", "pic_get_particles", "pic_get_diagnostics", "pic_set_profiling",
             "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc", "pic_autotune",
-            "pic_set_stations", "pic_get_station"]
+            "pic_set_stations", "pic_get_station", "pic_set_injection"]
 PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
@@ -147,6 +147,8 @@ def lib():
         L.pic_set_stations.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         L.pic_get_station.restype = st
         L.pic_get_station.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), vp, ctypes.c_size_t, vp, ctypes.c_size_t]
+        L.pic_set_injection.restype = st
+        L.pic_set_injection.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int32]
         L.pic_autotune.restype = st
         L.pic_autotune.argtypes = [P(pic_grid), P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    P(pic_options), P(pic_laser_lab), P(pic_plasma_lab), P(pic_beam_lab), ctypes.c_int,
@@ -333,6 +335,11 @@ class Simulation:
         z = np.ascontiguousarray(z_lab, dtype=np.float64)
         self._stations = z.size
         _check(lib().pic_set_stations(self.h, z.size, _ptr(z), int(max_records)), self.h)
+
+    def set_injection(self, z_lab, first_id=-1, enable=True):
+        """pic_set_injection: beam particles (id >= first_id; -1: the last lab-frame load's
+        beam) upstream of the lab plane z_lab are frozen."""
+        _check(lib().pic_set_injection(self.h, int(bool(enable)), float(z_lab), int(first_id)), self.h)
 
     def station(self, i):
         """History of station i: (t_lab (n,), fields (n, 6, n1, n0)) in the lab frame."""

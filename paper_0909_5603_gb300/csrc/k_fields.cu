@@ -82,8 +82,10 @@ __device__ __forceinline__ R ck_diff(const R *F, long long p, const long long up
     return sum;
 }
 
-// B <- B - (dt/2) curl E  [then x damping on the second half of the step]
-template <typename R>
+// B <- B - (dt/2) curl E  [then x damping on the second half of the step].  CK: the
+// low-dispersion differences (a template parameter, so that the Yee kernel keeps its
+// small register footprint and full occupancy)
+template <typename R, bool CK>
 __global__ void __launch_bounds__(256) k_bhalf(Launch L, int damp)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(256) k_bhalf(Launch L, int damp)
     const R ix = K.inv_dx[0], iy = K.inv_dx[1], iz = K.inv_dx[2];
     const long long p = c.p;
     R dEz_dy = R(0), dEy_dz, dEx_dz, dEz_dx, dEy_dx, dEx_dy = R(0);
-    if (I.solver == PIC_SOLVER_CK) {
+    if (CK) {
         // low-dispersion solver: each forward difference averaged over its transverse
         // neighbours, 7/12 on itself, 1/12 on the edge and 1/48 on the corner ones (on
         // an invariant axis the neighbours are the cell itself)
@@ -421,18 +423,22 @@ cudaError_t launch_filter(int fp64, const Launch &L, const long long *const penc
     return cudaGetLastError();
 }
 
-cudaError_t launch_maxwell(int fp64, const Launch &L, int filtered, cudaStream_t s)
+template <typename R, bool CK>
+static void maxwell_kernels(const Launch &L, int filtered, unsigned nb, cudaStream_t s)
+{
+    k_bhalf<R, CK><<<nb, 256, 0, s>>>(L, 0);
+    k_efull<R><<<nb, 256, 0, s>>>(L, filtered);
+    k_bhalf<R, CK><<<nb, 256, 0, s>>>(L, 1);
+}
+
+cudaError_t launch_maxwell(int fp64, int solver, const Launch &L, int filtered, cudaStream_t s)
 {
     const unsigned nb = blocks_for(L.total_cells, 256);
-    if (fp64) {
-        k_bhalf<double><<<nb, 256, 0, s>>>(L, 0);
-        k_efull<double><<<nb, 256, 0, s>>>(L, filtered);
-        k_bhalf<double><<<nb, 256, 0, s>>>(L, 1);
-    } else {
-        k_bhalf<float><<<nb, 256, 0, s>>>(L, 0);
-        k_efull<float><<<nb, 256, 0, s>>>(L, filtered);
-        k_bhalf<float><<<nb, 256, 0, s>>>(L, 1);
-    }
+    const bool ck = solver == PIC_SOLVER_CK;
+    if (fp64)
+        ck ? maxwell_kernels<double, true>(L, filtered, nb, s) : maxwell_kernels<double, false>(L, filtered, nb, s);
+    else
+        ck ? maxwell_kernels<float, true>(L, filtered, nb, s) : maxwell_kernels<float, false>(L, filtered, nb, s);
     return cudaGetLastError();
 }
 

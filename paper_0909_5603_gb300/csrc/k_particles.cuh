@@ -332,7 +332,9 @@ __device__ __forceinline__ void flush_j_double(const InstDev &I, const int T0[3]
     }
 }
 
-template <int ND, int ORD, typename R, int PUSHER>
+// INJ: instances with a beam injection plane (a separate instantiation, so that the
+// kernel without a plane carries none of its code)
+template <int ND, int ORD, typename R, int PUSHER, bool INJ>
 __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launch L)
 {
     constexpr bool kFixed = sizeof(R) == 4;  // FP32: fixed-point integer J accumulation
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     __shared__ int s_run[kBuckets];          // running bucket totals of the tile (warp 0)
     // each thread's particle of the next chunk, copied in (cp.async) while the current
     // chunk is processed; two buffers, chunk r in buffer r & 1
-    __shared__ int s_pcell[2][kNT];
+    __shared__ int s_pcell[2][kNT], s_pid[2][kNT];
     __shared__ R s_poff[2][3][kNT], s_pu[2][3][kNT], s_pw[2][kNT];
     __shared__ int s_cnt[2][kNW][kBuckets];  // per-warp bucket counts, double-buffered per chunk
 
@@ -417,6 +419,11 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     const R qdv = K.qdv;
     const R jfx = K.jf[0], jfy = K.jf[1], jfz = K.jf[2];
     const R dtdx[3] = {K.dtdx[0], K.dtdx[1], K.dtdx[2]};
+    // beam injection plane in cells along z at this step's push time t^n = n dt (n: the
+    // phases before this one), in FP64; beam particles upstream of it are frozen
+    const bool inj = INJ && I.inj_id0 != INT_MAX;
+    double zp_inj = 0.0;
+    if (inj) zp_inj = (I.inj_zb - I.beta_b * ((double)(*I.phase - 1) * I.dt)) / I.dx[2];
     const int bx = I.box[0], bxy = I.box[0] * I.box[1];
     const int jd0 = I.jdim[0], jd01 = I.jdim[0] * I.jdim[1];
     const int jlo_y = ND == 3 ? I.jlo : 0;
@@ -448,6 +455,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             cp_async<sizeof(R)>(&s_pu[b][1][tid], u_in[1] + p);
             cp_async<sizeof(R)>(&s_pu[b][2][tid], u_in[2] + p);
             cp_async<sizeof(R)>(&s_pw[b][tid], w_in + p);
+            if (id_in) cp_async<4>(&s_pid[b][tid], id_in + p);
         }
         cp_async_commit();
         return p;
@@ -487,7 +495,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             u[1] = s_pu[pb][1][tid];
             u[2] = s_pu[pb][2][tid];
             w = s_pw[pb][tid];
-            pid = id_in ? __ldg(id_in + pos) : 0;
+            pid = id_in ? s_pid[pb][tid] : 0;
 
             // ---- gather (Yee positions: E_a staggered along a, B_a along the other two)
             R E[3], B[3];
@@ -521,6 +529,15 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
                 push_vay(u, E, B, h);
             else
                 push_boris(u, E, B, h);
+
+            // a beam particle frozen upstream of the injection plane: the fields do not act
+            // on it, it keeps its momentum (restored from the staged copy; pushing
+            // unconditionally and restoring runs faster than branching around the push)
+            if (INJ && inj && pid >= I.inj_id0 && (double)cc[2] + (double)o[2] < zp_inj) {
+                u[0] = s_pu[pb][0][tid];
+                u[1] = s_pu[pb][1][tid];
+                u[2] = s_pu[pb][2][tid];
+            }
 
             // ---- move
             bool bad = false;

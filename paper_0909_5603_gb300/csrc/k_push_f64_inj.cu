@@ -1,0 +1,11 @@
+// k_push_f64_inj.cu -- double instantiations of the fused particle kernel, with a beam injection plane.
+#include "k_push.cuh"
+
+namespace pic {
+
+cudaError_t dispatch_particles_f64_inj(int ndim, int order, int pusher, const Launch *L, size_t smem, cudaStream_t s)
+{
+    return dispatch_particles_t<double, true>(ndim, order, pusher, L, smem, s);
+}
+
+}  // namespace pic

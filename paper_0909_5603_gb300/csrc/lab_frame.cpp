@@ -155,6 +155,7 @@ void transform_lab_inputs(const Geometry &G, double gamma_b, const pic_laser_lab
             }
         }
     }
+    P.beam_first = next_id;
     if (beam) {
         const size_t first = P.cell.size();
         const Rng rng{beam->seed};

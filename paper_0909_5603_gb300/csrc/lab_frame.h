@@ -29,6 +29,7 @@ struct LabFields {
 struct LabParticles {
     std::vector<int32_t> cell, id;
     std::vector<double> off, mom, weight;
+    int32_t beam_first = 0;  // first id of the beam (its ids follow the plasma's)
     void reserve(size_t n)
     {
         cell.reserve(n);

@@ -60,6 +60,11 @@ struct pic_ctx {
     bool loaded = false;
     int64_t step = 0;
     int last_filtered = 0;
+    // beam injection plane (pic_set_injection)
+    bool inj_on = false;
+    double inj_z = 0.0;
+    int32_t inj_first = -1;          // < 0: the beam of the last lab-frame load
+    int32_t beam_first_id = INT_MAX; // first beam id of the last lab-frame load (INT_MAX: none)
     // lab-frame stations
     int nst = 0, st_max = 0;
     double *d_st_z = nullptr, *d_st_t = nullptr;
@@ -236,6 +241,15 @@ static void fill_step_coef(InstDev &h)
     h.cf = f;
 }
 
+// The injection plane in the instance parameters: on only with a plane set; the first
+// beam id is the caller's, or the last lab-frame load's beam (none: INT_MAX).
+static void apply_injection(pic_ctx *c)
+{
+    const int32_t id0 = c->inj_first >= 0 ? c->inj_first : c->beam_first_id;
+    c->h.inj_id0 = c->inj_on ? id0 : INT_MAX;
+    c->h.inj_zb = c->inj_z / c->gamma_b;
+}
+
 static pic_status upload_inst(pic_ctx *c)
 {
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_inst, &c->h, sizeof(InstDev), cudaMemcpyHostToDevice, c->stream));
@@ -368,6 +382,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     h.dt = dt;
     h.gb = gamma_boost;
     h.beta_b = std::sqrt(1.0 - 1.0 / (gamma_boost * gamma_boost));
+    h.inj_id0 = INT_MAX;
     h.q = o.charge;
     h.m = o.mass;
     h.jscale = h.jinv = 1.0f;  // until a load sets the FP32 current scale
@@ -476,7 +491,8 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
         }
         std::vector<float> f32(f.begin(), f.end());
         const void *src = c->fp64 ? (const void *)f.data() : (const void *)f32.data();
-        if (cudaMemcpy(tab, src, c->es * (size_t)c->n[a], cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (cudaMemcpyAsync(tab, src, c->es * (size_t)c->n[a], cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
             dfree_all(c);
             delete c;
             return fail(nullptr, PIC_ERR_CUDA, "absorbing-layer table upload failed");
@@ -669,12 +685,15 @@ static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg, double wm
             cbv[(size_t)cc * kBuckets + kCenterDir] = k * R;
         }
     }
-    CUDA_OR_FAIL(c, cudaMemcpy(h.seg[0], seg.data(), sizeof(int) * (h.ntiles + 1), cudaMemcpyHostToDevice));
-    CUDA_OR_FAIL(c, cudaMemcpy(h.chunk_base[0], cbase.data(), sizeof(int) * (h.ntiles + 1), cudaMemcpyHostToDevice));
-    CUDA_OR_FAIL(c, cudaMemcpy(h.tot[0], tot.data(), sizeof(int) * tot.size(), cudaMemcpyHostToDevice));
-    CUDA_OR_FAIL(c, cudaMemcpy(h.pop, pop.data(), sizeof(int) * pop.size(), cudaMemcpyHostToDevice));
-    CUDA_OR_FAIL(c, cudaMemcpy(h.chunk_pre[0], pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
-    CUDA_OR_FAIL(c, cudaMemcpy(h.chunk_cb[0], cbv.data(), sizeof(int) * cbv.size(), cudaMemcpyHostToDevice));
+    // every copy and reset goes on the context's stream (which need not synchronise with
+    // the legacy default stream) and completes before this function returns
+    cudaStream_t s = c->stream;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(h.seg[0], seg.data(), sizeof(int) * (h.ntiles + 1), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(h.chunk_base[0], cbase.data(), sizeof(int) * (h.ntiles + 1), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(h.tot[0], tot.data(), sizeof(int) * tot.size(), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(h.pop, pop.data(), sizeof(int) * pop.size(), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(h.chunk_pre[0], pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(h.chunk_cb[0], cbv.data(), sizeof(int) * cbv.size(), cudaMemcpyHostToDevice, s));
     // FP32 fixed-point current scale: the power of two that maps the bound |q| max(w) / dV
     // on any single current contribution to at most 2^20
     {
@@ -688,18 +707,23 @@ static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg, double wm
         h.jinv = bound > 0.0 ? (float)std::ldexp(1.0, e - 20) : 1.0f;
     }
     fill_step_coef(h);
+    apply_injection(c);
     // cur, err, live, jsel, lost and the particle-phase counter
-    CUDA_OR_FAIL(c, cudaMemset(h.cur, 0, 16 + sizeof(unsigned long long) + sizeof(int)));
-    CUDA_OR_FAIL(c, cudaMemset(h.J[0], 0, 3 * (size_t)h.cstride * c->es));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(h.cur, 0, 16 + sizeof(unsigned long long) + sizeof(int), s));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(h.J[0], 0, 3 * (size_t)h.cstride * c->es, s));
     c->loaded = true;
     c->version++;  // a batch holding this instance re-reads its parameters
     c->step = 0;
     c->last_filtered = 0;
     destroy_graph(c);
     pic_status st = upload_inst(c);
-    if (st != PIC_OK || c->nst == 0) return st;
+    if (st != PIC_OK) return st;
+    if (c->nst == 0) {
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
+        return PIC_OK;
+    }
     // stations start a new history with the loaded state as its first record
-    CUDA_OR_FAIL(c, cudaMemset(c->d_st_count, 0, sizeof(int) * c->nst));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_st_count, 0, sizeof(int) * c->nst, s));
     StationDev S{c->d_st_z, c->d_st_count, c->d_st_t, c->d_st_fields, c->st_max};
     CUDA_OR_FAIL(c, launch_stations(c->fp64, c->d_inst, S, c->nst, c->n[0] * c->n[1], c->stream));
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
@@ -750,7 +774,28 @@ extern "C" pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t 
     cudaSetDevice(ctx->device);
     CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->h.ion = 0;  // particles loaded directly carry no ion background
+    ctx->beam_first_id = INT_MAX;
     return load_internal(ctx, n, cell, off3, u3, w, id);
+}
+
+extern "C" pic_status pic_set_injection(pic_ctx *ctx, int enable, double z_lab, int32_t first_id)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_set_injection on a batch");
+    if (enable && !std::isfinite(z_lab)) return fail(ctx, PIC_ERR_ARG, "injection plane z_lab must be finite");
+    if (enable && !ctx->opt.track_ids) return fail(ctx, PIC_ERR_STATE, "beam injection needs particle ids (track_ids)");
+    cudaSetDevice(ctx->device);
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->inj_on = enable != 0;
+    ctx->inj_z = enable ? z_lab : 0.0;
+    ctx->inj_first = first_id < 0 ? -1 : first_id;
+    apply_injection(ctx);
+    destroy_graph(ctx);  // the particle kernel with or without the plane
+    ctx->version++;      // a batch holding this instance re-reads its parameters
+    pic_status st = upload_inst(ctx);
+    if (st != PIC_OK) return st;
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    return PIC_OK;
 }
 
 static pic_status ghost_fill_now(pic_ctx *c)
@@ -854,6 +899,7 @@ extern "C" pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *lase
         if (!F.comp[c].empty() && (st = set_field_internal(ctx, PIC_EX + c, F.comp[c].data())) != PIC_OK) return st;
     if (!on_device) {
         const int64_t np = (int64_t)P.cell.size();
+        ctx->beam_first_id = beam ? P.beam_first : INT_MAX;
         return load_internal(ctx, np, P.cell.data(), P.off.data(), P.mom.data(), P.weight.data(), P.id.data());
     }
     // canonical layout: per tile the plasma particles (cells in linear order), then the
@@ -896,6 +942,7 @@ extern "C" pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *lase
         CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
     }
     for (auto &v : P.id) v += (int32_t)plasma_ids;  // beam ids follow the plasma's
+    ctx->beam_first_id = beam ? (int32_t)plasma_ids + P.beam_first : INT_MAX;
     if ((st = place_from_host(ctx, nb, P.cell.data(), P.off.data(), P.mom.data(), P.weight.data(), P.id.data(), 0,
                               beam_slot)) != PIC_OK)
         return st;
@@ -957,7 +1004,9 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
         CUDA_OR_FAIL(c, launch_scan(L, 0, nullptr, c->stream));
         tm.end(1);
         tm.begin(0);
-        CUDA_OR_FAIL(c, launch_particles(c->ndim, c->order, fp64, c->opt.pusher, L, c->smem, c->stream));
+        bool inj = c->h.inj_id0 != INT_MAX;
+        for (auto m : c->members) inj = inj || m->h.inj_id0 != INT_MAX;
+        CUDA_OR_FAIL(c, launch_particles(c->ndim, c->order, fp64, c->opt.pusher, inj, L, c->smem, c->stream));
         tm.end(0);
         launches += 2;
     }
@@ -973,7 +1022,7 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
     }
     if (mask & PIC_PHASE_MAXWELL) {
         tm.begin(3);
-        CUDA_OR_FAIL(c, launch_maxwell(fp64, L, filtered, c->stream));
+        CUDA_OR_FAIL(c, launch_maxwell(fp64, c->opt.solver, L, filtered, c->stream));
         launches += 3;
         for (int a = 0; a < 3; ++a)
             if (c->any_periodic[a]) {
@@ -1064,10 +1113,18 @@ extern "C" pic_status pic_run_phases(pic_ctx *ctx, int mask)
     return PIC_OK;
 }
 
+// Device -> host copy ordered after the context's work (its stream need not synchronise
+// with the legacy default stream); returns when the data is on the host.
+static cudaError_t d2h(pic_ctx *c, void *dst, const void *src, size_t bytes)
+{
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(c->stream) : e;
+}
+
 static pic_status check_device_error(pic_ctx *c)
 {
     int err = 0;
-    CUDA_OR_FAIL(c, cudaMemcpy(&err, c->h.err, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_OR_FAIL(c, d2h(c, &err, c->h.err, sizeof(int)));
     if (err & kErrTimeout) return fail(c, PIC_ERR_TIMEOUT, "a bounded device wait timed out (error word 0x%x)", err);
     if (err & kErrSpeed) return fail(c, PIC_ERR_PARTICLE_SPEED, "a particle moved a cell or more in one step, or is not finite (0x%x)", err);
     if (err & (kErrInternal | kErrCapacity)) return fail(c, PIC_ERR_INTERNAL, "device consistency check failed (0x%x)", err);
@@ -1187,7 +1244,7 @@ extern "C" pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out)
     if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "getters take a member, not a batch");
     pic_status st = pic_synchronize(ctx);
     int err = 0;
-    cudaMemcpy(&err, ctx->h.err, sizeof(int), cudaMemcpyDeviceToHost);
+    d2h(ctx, &err, ctx->h.err, sizeof(int));
     std::memset(out, 0, sizeof(*out));
     out->error_flags = err;
     if (st != PIC_OK) return st;
@@ -1302,8 +1359,9 @@ extern "C" pic_status pic_set_stations(pic_ctx *ctx, int count, const double *z_
     ctx->d_st_fields = dalloc(ctx, ctx->es * 6 * plane * count * (size_t)max_records);
     if (!ctx->d_st_z || !ctx->d_st_t || !ctx->d_st_count || !ctx->d_st_fields)
         return fail(ctx, PIC_ERR_OOM, "no device memory for %d stations x %d records", count, max_records);
-    CUDA_OR_FAIL(ctx, cudaMemcpy(ctx->d_st_z, z_lab, sizeof(double) * count, cudaMemcpyHostToDevice));
-    CUDA_OR_FAIL(ctx, cudaMemset(ctx->d_st_count, 0, sizeof(int) * count));
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(ctx->d_st_z, z_lab, sizeof(double) * count, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_st_count, 0, sizeof(int) * count, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->nst = count;
     ctx->st_max = max_records;
     if (ctx->loaded) {  // the current state is the first record
@@ -1325,23 +1383,22 @@ extern "C" pic_status pic_get_station(pic_ctx *ctx, int station, int *n_records,
     pic_status st = pic_synchronize(ctx);
     if (st != PIC_OK) return st;
     int n = 0;
-    CUDA_OR_FAIL(ctx, cudaMemcpy(&n, ctx->d_st_count + station, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_OR_FAIL(ctx, d2h(ctx, &n, ctx->d_st_count + station, sizeof(int)));
     *n_records = n;
     const size_t plane = (size_t)ctx->n[0] * ctx->n[1];
     if (t_lab) {
         if (t_count < (size_t)n) return fail(ctx, PIC_ERR_ARG, "t_lab needs room for %d values", n);
-        CUDA_OR_FAIL(ctx, cudaMemcpy(t_lab, ctx->d_st_t + (size_t)station * ctx->st_max, sizeof(double) * n,
-                                     cudaMemcpyDeviceToHost));
+        CUDA_OR_FAIL(ctx, d2h(ctx, t_lab, ctx->d_st_t + (size_t)station * ctx->st_max, sizeof(double) * n));
     }
     if (fields) {
         const size_t need = (size_t)n * 6 * plane;
         if (f_count < need) return fail(ctx, PIC_ERR_ARG, "fields needs room for %zu values", need);
         const unsigned char *src = (const unsigned char *)ctx->d_st_fields + (size_t)station * ctx->st_max * 6 * plane * ctx->es;
         if (ctx->fp64) {
-            CUDA_OR_FAIL(ctx, cudaMemcpy(fields, src, sizeof(double) * need, cudaMemcpyDeviceToHost));
+            CUDA_OR_FAIL(ctx, d2h(ctx, fields, src, sizeof(double) * need));
         } else {
             std::vector<float> tmp(need);
-            CUDA_OR_FAIL(ctx, cudaMemcpy(tmp.data(), src, sizeof(float) * need, cudaMemcpyDeviceToHost));
+            CUDA_OR_FAIL(ctx, d2h(ctx, tmp.data(), src, sizeof(float) * need));
             for (size_t i = 0; i < need; ++i) fields[i] = tmp[i];
         }
     }
@@ -1393,9 +1450,10 @@ extern "C" pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx
         pic_ctx *m = instances[i];
         if (!m || m->is_batch) return fail(nullptr, PIC_ERR_ARG, "instance %d is NULL or a batch", i);
         if (m->ndim != f->ndim || m->order != f->order || m->fp64 != f->fp64 || m->opt.pusher != f->opt.pusher ||
-            m->device != f->device || m->smem != f->smem || m->h.ts[0] != f->h.ts[0] || m->h.ts[1] != f->h.ts[1] ||
-            m->h.ts[2] != f->h.ts[2])
-            return fail(nullptr, PIC_ERR_ARG, "instance %d differs in dimension, shape, precision, pusher, tile or device", i);
+            m->opt.solver != f->opt.solver || m->device != f->device || m->smem != f->smem ||
+            m->h.ts[0] != f->h.ts[0] || m->h.ts[1] != f->h.ts[1] || m->h.ts[2] != f->h.ts[2])
+            return fail(nullptr, PIC_ERR_ARG,
+                        "instance %d differs in dimension, shape, precision, pusher, field solver, tile or device", i);
         for (int j = 0; j < i; ++j)
             if (instances[j] == m) return fail(nullptr, PIC_ERR_ARG, "instance %d appears twice", i);
     }

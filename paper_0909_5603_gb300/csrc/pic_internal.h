@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+
 #include "../../include/pic.h"
 
 namespace pic {
@@ -118,6 +120,10 @@ struct InstDev {
     void *ion_face;     // [n[2]] this step's ion current on the Jz faces (working precision)
     int *phase;         // particle phases run since the last load (device counter)
     double gb, beta_b;  // the frame's boost: Lorentz factor and velocity
+    // beam injection plane: ids >= inj_id0 (INT_MAX: off) upstream of the lab plane, at
+    // z' = inj_zb - beta_b t' in this frame, are frozen (no field acts on them)
+    int inj_id0;
+    double inj_zb;
     int box[3];         // TMA box extents (elements)
     int box_lo[3];      // box origin relative to the tile origin (cells, <= 0)
     int jlo;            // J tile origin relative to the tile origin (-1 or -2)
@@ -201,7 +207,9 @@ cudaError_t launch_plasma_write(int fp64, const InstDev &I, const PlasmaGen &G, 
                                 cudaStream_t st);
 cudaError_t launch_ion_current(int fp64, const Launch &L, cudaStream_t s);
 cudaError_t launch_rho_ion(const Launch &L, long long ncell, double *rho, cudaStream_t s);
-cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, const Launch &L, size_t smem, cudaStream_t s);
+// inj: some instance of the launch has a beam injection plane
+cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, bool inj, const Launch &L, size_t smem,
+                             cudaStream_t s);
 int particle_chunk();
 int particle_threads();
 cudaError_t launch_scan(const Launch &L, int mode, int *const *dst, cudaStream_t s);
@@ -222,7 +230,7 @@ inline long long filter_pencils(const int n[3], int ndim, int axis)
     if (axis == 1) return cols * ((n[1] + kP - 1) / kP) * n[2];
     return cols * ((n[2] + kP - 1) / kP) * n[1];
 }
-cudaError_t launch_maxwell(int fp64, const Launch &L, int filtered, cudaStream_t s);
+cudaError_t launch_maxwell(int fp64, int solver, const Launch &L, int filtered, cudaStream_t s);
 cudaError_t launch_ghost(int fp64, const Launch &L, int axis, long long per_inst_max, cudaStream_t s);
 cudaError_t prepare_particles(int ndim, int order, int fp64, int pusher, size_t smem);
 cudaError_t launch_field_energy(int fp64, const Launch &L, double *sums, cudaStream_t s);
