@@ -114,6 +114,8 @@ def lib():
         L.orc_set_injection.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int32]
         L.orc_num_frozen.restype = ctypes.c_int64
         L.orc_num_frozen.argtypes = [vp]
+        L.orc_set_antenna.restype = None
+        L.orc_set_antenna.argtypes = [vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_double]
         L.orc_ion_integral.restype = ctypes.c_double
         L.orc_ion_integral.argtypes = [vp, ctypes.c_double, ctypes.c_double]
         _lib = L
@@ -262,6 +264,15 @@ class Sim:
         """Beam injection through the lab plane z_lab: beam particles (id >= first_id, or
         the last lab-frame load's beam) upstream of it are frozen."""
         lib().orc_set_injection(self._h, int(bool(enable)), float(gamma_b), float(z_lab), int(first_id))
+
+    def set_antenna(self, gamma_b, laser, z_lab, enable=True):
+        """Laser antenna on the lab plane z_lab: laser = (a0, lambda0, waist, duration,
+        z_center) of the lab pulse it emits forward (None or enable=False: off)."""
+        if laser is None or not enable:
+            lib().orc_set_antenna(self._h, 0, float(gamma_b), None, 0.0)
+            return
+        a = (ctypes.c_double * 5)(*[float(v) for v in laser])
+        lib().orc_set_antenna(self._h, 1, float(gamma_b), ctypes.cast(a, ctypes.c_void_p), float(z_lab))
 
     def num_frozen(self):
         return int(lib().orc_num_frozen(self._h))

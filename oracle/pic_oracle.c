@@ -51,6 +51,14 @@ struct orc_sim {
     double inj_zb, inj_beta; /* the plane in this frame: z' = inj_zb - inj_beta t' */
     int32_t inj_first;       /* first beam id, or -1: the beam of the last lab-frame load */
     int32_t beam_id0;        /* first id of that beam (INT32_MAX: none) */
+    /* laser antenna on a lab-fixed plane (see orc_set_antenna) */
+    int64_t n_mx;            /* Maxwell phases run since the last load */
+    int ant;
+    double ant_zb, ant_beta, ant_t0; /* plane z' = ant_zb - ant_beta t'; t' at the set */
+    int64_t ant_n;                   /* Maxwell phases since the set */
+    double ant_w0, ant_xc, ant_yc;   /* transverse profile exp(-(x^2 + y^2) / w0^2) */
+    int64_t ant_lo, ant_na;          /* 1D lattice: nodes ant_lo .. ant_lo + ant_na - 1 */
+    double *ant_e, *ant_b;           /* its E_x on the nodes, B_y half a node above */
 };
 
 /* Yee staggering (in cells) of each component along each axis. */
@@ -254,6 +262,8 @@ void orc_destroy(orc_sim *s)
     if (!s) return;
     for (int c = 0; c < ORC_NCOMP; ++c) free(s->f[c]);
     free_particles(s);
+    free(s->ant_e);
+    free(s->ant_b);
     free(s);
 }
 
@@ -291,6 +301,8 @@ int orc_set_particles(orc_sim *s, int64_t np, const int32_t *cell, const double 
         }
     }
     s->beam_id0 = INT32_MAX; /* no lab-frame beam */
+    s->n_mx = 0;
+    orc_set_antenna(s, 0, 1.0, NULL, 0.0); /* a load removes the antenna */
     memcpy(s->cell, cell, (size_t)np * sizeof(int32_t));
     memcpy(s->off, off, (size_t)np * 3 * sizeof(double));
     memcpy(s->u, u, (size_t)np * 3 * sizeof(double));
@@ -827,6 +839,159 @@ static double dfwd_ck(const orc_sim *s, int comp, int a, int i, int j, int k)
 
 void orc_set_solver(orc_sim *s, int solver) { s->solver = solver; }
 
+/* ------------------------------------------------------------------------------------
+ * Laser antenna on a plane fixed in the laboratory (Sec. 2: the laser enters through a
+ * plane fixed in the lab frame that drifts in the boosted frame; reading).  The lab pulse
+ * of the loader's parameters (a0, lambda0, waist, duration, z_center = where its
+ * envelope centre would be at lab time 0 had it always propagated freely) is emitted
+ * forward by the lab plane z = z_lab: downstream of the plane the field is the free
+ * pulse, upstream there is none.  In this frame the plane sits at
+ * z'_p(t') = z_lab / gamma_b - beta_b t', and the free pulse is
+ *   E'_x = B'_y = T(x, y) g(z' - t'),  g(u) = a0 k' exp(-((u - z'_c) / L')^2) cos(k' (u - z'_c)),
+ *   T = exp(-(x^2 + y^2) / w0^2)
+ * (k', L', z'_c Doppler-scaled by gamma_b (1 + beta_b), as for the loaded laser).
+ * Discretely the grid is split into a total-field region (z positions above
+ * z'_p(t^n) / dz, t^n the time of the fields, held fixed through the Maxwell phase that
+ * advances them) and a scattered-field region (at or below it), which holds the field
+ * minus the incident pulse.  The incident field is T times g propagated on a 1D lattice aligned
+ * with the grid's z lattice by the same leapfrog (so a plane wave crosses the boundary
+ * without any reflection), started from samples of g.  Each z difference that joins a
+ * value of one region to a value of the other takes the far value in the near one's
+ * representation: the incident value there is added (forward difference of E_x in the
+ * B update) or subtracted, which adds h T g_E / dz to B_y and dt T g_B / dz to E_x in
+ * both cases.  At the end of each Maxwell phase the values the receding plane has passed
+ * (between its positions at t^n and t^{n+1}) enter the total-field region: their incident
+ * value at t^{n+1} is added.  Setting the antenna adds the incident field to the
+ * total-field region.
+ * ---------------------------------------------------------------------------------- */
+static double ant_profile(const orc_sim *s, double x, double y)
+{
+    double dx = x - s->ant_xc, dy = s->active[1] ? y - s->ant_yc : 0.0;
+    return exp(-(dx * dx + dy * dy) / (s->ant_w0 * s->ant_w0));
+}
+
+/* the plane's position in cells along z at the start of the antenna's Maxwell phase n */
+static double ant_plane(const orc_sim *s, int64_t n)
+{
+    return (s->ant_zb - s->ant_beta * (s->ant_t0 + (double)n * s->dt)) / s->dx[2];
+}
+
+/* incident E_x at node k, B_y at half node k + 1/2 (0 outside the lattice) */
+static double ant_ge(const orc_sim *s, int64_t k)
+{
+    int64_t a = k - s->ant_lo;
+    return a >= 0 && a < s->ant_na ? s->ant_e[a] : 0.0;
+}
+
+static double ant_gb(const orc_sim *s, int64_t k)
+{
+    int64_t a = k - s->ant_lo;
+    return a >= 0 && a < s->ant_na ? s->ant_b[a] : 0.0;
+}
+
+/* the 1D leapfrog of the incident pulse (E_x on nodes, B_y on half nodes, zero beyond
+ * the lattice): B_y -= h dE_x/dz (h = dt / 2) or E_x -= dt dB_y/dz */
+static void ant_aux_b(orc_sim *s, double h)
+{
+    for (int64_t a = 0; a < s->ant_na; ++a) {
+        double e1 = a + 1 < s->ant_na ? s->ant_e[a + 1] : 0.0;
+        s->ant_b[a] -= h * (e1 - s->ant_e[a]) / s->dx[2];
+    }
+}
+
+static void ant_aux_e(orc_sim *s)
+{
+    for (int64_t a = s->ant_na - 1; a >= 0; --a) {
+        double b0 = a > 0 ? s->ant_b[a - 1] : 0.0;
+        s->ant_e[a] -= s->dt * (s->ant_b[a] - b0) / s->dx[2];
+    }
+}
+
+/* adds the incident field at E_x nodes k and B_y half nodes k + 1/2 whose z position lies
+ * in (lo, hi] (in cells) */
+static void ant_add_incident(orc_sim *s, double lo, double hi)
+{
+    for (int k = 0; k < s->n[2]; ++k)
+        for (int j = 0; j < s->n[1]; ++j)
+            for (int i = 0; i < s->n[0]; ++i) {
+                int64_t id = node_index(s, i, j, k);
+                double T = ant_profile(s, (i + 0.5) * s->dx[0], j * s->dx[1]); /* E_x and B_y share x, y */
+                if (k > lo && k <= hi) s->f[ORC_EX][id] += T * ant_ge(s, k);
+                if (k + 0.5 > lo && k + 0.5 <= hi) s->f[ORC_BY][id] += T * ant_gb(s, k);
+            }
+}
+
+void orc_set_antenna(orc_sim *s, int enable, double gb, const double *laser, double z_lab)
+{
+    free(s->ant_e);
+    free(s->ant_b);
+    s->ant_e = s->ant_b = NULL;
+    s->ant = 0;
+    if (!enable || !laser) return;
+    double b = boost_beta(gb), doppler = gb * (1.0 + b);
+    double kp = 6.283185307179586 / (laser[1] * doppler), Lp = laser[3] * doppler, zc = laser[4] * doppler;
+    double amp = laser[0] * kp, dz = s->dx[2];
+    s->ant = 1;
+    s->ant_zb = z_lab / gb;
+    s->ant_beta = b;
+    s->ant_t0 = (double)s->n_mx * s->dt;
+    s->ant_n = 0;
+    s->ant_w0 = laser[2];
+    s->ant_xc = 0.5 * s->n[0] * s->dx[0];
+    s->ant_yc = 0.5 * s->n[1] * s->dx[1];
+    /* lattice: from below the pulse's tail (5 L') and the grid, to beyond the grid by the
+     * distance light covers while the plane is still in the box (no echo of the lattice's
+     * end reaches the box meanwhile) */
+    double zp0 = ant_plane(s, 0), t0 = s->ant_t0;
+    double lo = floor((zc + t0 - 5.0 * Lp) / dz) - 2.0;
+    if (lo > 0.0) lo = 0.0;
+    double top = (double)s->n[2] > ceil(zp0) + 2.0 ? (double)s->n[2] : ceil(zp0) + 2.0;
+    double stay = zp0 > -1.0 && b > 0.0 ? (zp0 + 1.0) / b : 0.0; /* in cells of time */
+    double hi = top + ceil(stay) + 8.0;
+    s->ant_lo = (int64_t)lo;
+    s->ant_na = (int64_t)(hi - lo) + 1;
+    s->ant_e = (double *)calloc((size_t)s->ant_na, sizeof(double));
+    s->ant_b = (double *)calloc((size_t)s->ant_na, sizeof(double));
+    for (int64_t a = 0; a < s->ant_na; ++a) {
+        double ue = (s->ant_lo + a) * dz - t0 - zc, ub = (s->ant_lo + a + 0.5) * dz - t0 - zc;
+        s->ant_e[a] = amp * exp(-(ue / Lp) * (ue / Lp)) * cos(kp * ue);
+        s->ant_b[a] = amp * exp(-(ub / Lp) * (ub / Lp)) * cos(kp * ub);
+    }
+    ant_add_incident(s, zp0, INFINITY);
+}
+
+/* The incident term to add to B_y at (i, j, k + 1/2) in a B half update (times h), and
+ * to E_x at (i, j, k) in the E update (times dt), for the plane at zp (cells). */
+static double ant_b_term(const orc_sim *s, int i, int j, int k, double zp)
+{
+    if (!s->ant) return 0.0;
+    double g;
+    if (k <= zp && zp < k + 0.5) { /* B_y total field, E_x at k scattered */
+        g = ant_ge(s, k);
+    } else if (k + 0.5 <= zp && zp < k + 1) { /* B_y scattered, E_x at k + 1 total */
+        if (k + 1 >= s->n[2]) return 0.0;
+        g = ant_ge(s, k + 1);
+    } else {
+        return 0.0;
+    }
+    return ant_profile(s, (i + 0.5) * s->dx[0], j * s->dx[1]) * g / s->dx[2];
+}
+
+static double ant_e_term(const orc_sim *s, int i, int j, int k, double zp)
+{
+    if (!s->ant) return 0.0;
+    double g;
+    if (k - 0.5 <= zp && zp < k) { /* E_x total field, B_y at k - 1/2 scattered */
+        if (k - 1 < 0) return 0.0;
+        g = ant_gb(s, k - 1);
+    } else if (k <= zp && zp < k + 0.5) { /* E_x scattered, B_y at k + 1/2 total */
+        g = ant_gb(s, k);
+    } else {
+        return 0.0;
+    }
+    return ant_profile(s, (i + 0.5) * s->dx[0], j * s->dx[1]) * g / s->dx[2];
+}
+
 /* B <- B - h curl E (h = dt / 2), optionally damped afterwards. */
 static void half_b(orc_sim *s, int damp)
 {
@@ -842,6 +1007,7 @@ static void half_b(orc_sim *s, int damp)
                 double cx = d(s, ORC_EZ, 1, i, j, k) - d(s, ORC_EY, 2, i, j, k);
                 double cy = d(s, ORC_EX, 2, i, j, k) - d(s, ORC_EZ, 0, i, j, k);
                 double cz = d(s, ORC_EY, 0, i, j, k) - d(s, ORC_EX, 1, i, j, k);
+                if (s->ant) cy -= ant_b_term(s, i, j, k, ant_plane(s, s->ant_n));
                 int c[3] = {i, j, k};
                 double f = damp ? damp_factor(s, c) : 1.0;
                 nb[0][id] = f * (s->f[ORC_BX][id] - h * cx);
@@ -868,6 +1034,7 @@ static void full_e(orc_sim *s)
                 double cx = dbwd(s, ORC_BZ, 1, i, j, k) - dbwd(s, ORC_BY, 2, i, j, k);
                 double cy = dbwd(s, ORC_BX, 2, i, j, k) - dbwd(s, ORC_BZ, 0, i, j, k);
                 double cz = dbwd(s, ORC_BY, 0, i, j, k) - dbwd(s, ORC_BX, 1, i, j, k);
+                if (s->ant) cx += ant_e_term(s, i, j, k, ant_plane(s, s->ant_n));
                 int c[3] = {i, j, k};
                 double f = damp_factor(s, c);
                 ne[0][id] = f * (s->f[ORC_EX][id] + dt * (cx - s->f[ORC_JX][id]));
@@ -887,8 +1054,16 @@ static void full_e(orc_sim *s)
 void orc_maxwell(orc_sim *s)
 {
     half_b(s, 0);
+    if (s->ant) ant_aux_b(s, 0.5 * s->dt);
     full_e(s);
+    if (s->ant) ant_aux_e(s);
     half_b(s, 1);
+    if (s->ant) {
+        ant_aux_b(s, 0.5 * s->dt);
+        s->ant_n++; /* the values the receding plane passed during the phase join the total field */
+        ant_add_incident(s, ant_plane(s, s->ant_n), ant_plane(s, s->ant_n - 1));
+    }
+    s->n_mx++;
 }
 
 void orc_step(orc_sim *s, int nsteps)
@@ -1225,7 +1400,9 @@ int orc_load_lab_frame(orc_sim *s, double gb, const double *laser, const double 
     s->n_lost = 0;
     s->step = 0;
     s->n_pp = 0;
+    s->n_mx = 0;
     s->ion = 0;
+    orc_set_antenna(s, 0, 1.0, NULL, 0.0); /* a load removes the antenna */
     for (int c = 0; c < ORC_NCOMP; ++c) memset(s->f[c], 0, (size_t)s->ncell * sizeof(double));
 
     if (laser) {

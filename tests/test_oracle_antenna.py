@@ -1,0 +1,144 @@
+"""Pins of the oracle's laser antenna on a lab-fixed plane (Sec. 2 of Vay et al.: the laser
+is injected at a plane fixed in the laboratory frame and drifting in the boosted frame).
+
+* A transversely uniform pulse (plane wave) crosses the moving boundary without any
+  reflection: behind the plane the field stays zero to round-off, and ahead of it the
+  field equals, to round-off, the same lab pulse loaded whole into the box by the
+  (separately pinned) lab-frame loader and propagated by the same scheme -- for a plane
+  at rest (gamma_b = 1) and receding planes (gamma_b = 4, 13), at two time steps.
+* With a Gaussian transverse profile the emission stays one-way to the paraxial error.
+* Lab-frame physics through the (separately pinned) stations: a lab station downstream
+  of the antenna records the lab pulse's time history; a station upstream records
+  nothing.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import EX, EY, EZ, BX, BY, BZ
+
+
+def beta(g):
+    return math.sqrt(1 - 1 / g ** 2)
+
+
+def empty(n, dx, dt):
+    s = oracle.Sim(2, n, (0, 0, 1), dx, dt, tile=(8, 1, 16))
+    s.set_particles(np.zeros(0, np.int32), np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0))
+    return s
+
+
+def plane_wave_case(gb, dt_frac, steps=450, waist=1e9):
+    """A box of 24 boosted wavelengths (D = gamma_b (1 + beta_b) lab wavelengths) at 32
+    cells each; the free pulse (1/e length 1.5 wavelengths) starts centred 7.6 boosted
+    wavelengths into the box, the plane at 14: z_center = 7.6 and z_lab = 14 gamma_b D in
+    lab units."""
+    D = gb * (1 + beta(gb))
+    dz = D / 32
+    dt = dt_frac * dz
+    n = (8, 1, 768)
+    laser = [0.5, 1.0, waist, 1.5, 7.6]
+    z_lab = 14 * gb * D
+    a = empty(n, (1.0, 1.0, dz), dt)
+    a.set_antenna(gb, laser, z_lab)
+    f = empty(n, (1.0, 1.0, dz), dt)
+    f.load_lab_frame(gb, laser=laser)
+    for _ in range(steps):
+        a.maxwell()
+        f.maxwell()
+    zp = (z_lab / gb - beta(gb) * steps * dt) / dz
+    return a, f, zp, n
+
+
+@pytest.mark.parametrize("gb", [1.0, 4.0, 13.0])
+@pytest.mark.parametrize("dt_frac", [0.5, 0.9])
+def test_plane_wave_crosses_the_moving_plane_without_reflection(gb, dt_frac):
+    steps = int((450 if gb > 1 else 800) * 0.5 / dt_frac)
+    a, f, zp, n = plane_wave_case(gb, dt_frac, steps=steps)
+    amp = np.abs(f.get_field(EX)).max()
+    k = np.arange(n[2])
+    assert 20 < zp < n[2] - 20
+    for c in (EX, BY):
+        fa, ff = a.get_field(c)[:, 0, 0], f.get_field(c)[:, 0, 0]
+        pos = k + (0.5 if c == BY else 0.0)
+        behind, ahead = pos <= zp, pos > zp
+        assert np.abs(fa[behind]).max() < 1e-12 * amp, c
+        assert np.abs(fa[ahead] - ff[ahead]).max() < 1e-10 * amp, c
+        # the crossing is under way or done: most of the pulse is ahead of the plane
+        assert np.abs(ff[ahead]).max() > 0.9 * amp
+    for c in (EY, EZ, BX, BZ):
+        assert np.abs(a.get_field(c)).max() < 1e-10 * amp
+
+
+def test_half_crossed_pulse_is_cut_at_the_plane():
+    """Midway through the crossing the field ahead of the plane is the free pulse and
+    behind it nothing, although the free pulse is strong there."""
+    a, f, zp, n = plane_wave_case(4.0, 0.5, steps=250)
+    ex_a, ex_f = a.get_field(EX)[:, 0, 0], f.get_field(EX)[:, 0, 0]
+    k = np.arange(n[2])
+    amp = np.abs(ex_f).max()
+    assert np.abs(ex_f[k <= zp]).max() > 0.3 * amp and np.abs(ex_f[k > zp]).max() > 0.3 * amp
+    assert np.abs(ex_a[k <= zp]).max() < 1e-12 * amp
+    assert np.abs(ex_a[k > zp] - ex_f[k > zp]).max() < 1e-10 * amp
+
+
+def test_gaussian_profile_stays_one_way():
+    """A 20-unit waist on a periodic 8-unit-wide strip: behind the plane the field stays
+    below 1e-4 of the pulse (the incident field is paraxial)."""
+    a, f, zp, n = plane_wave_case(4.0, 0.5, waist=20.0)
+    amp = np.abs(f.get_field(EX)).max()
+    k = np.arange(n[2])
+    for c in (EX, BY):
+        fa = a.get_field(c)
+        pos = k + (0.5 if c == BY else 0.0)
+        assert np.abs(fa[pos <= zp - 1]).max() < 1e-4 * amp
+        assert np.abs(fa[pos > zp + 1]).max() > 0.5 * amp
+
+
+def lab_history(gb, Z, steps=560):
+    """Antenna at the lab plane z_lab = 400 emitting the pulse whose free centre would be at
+    z_center = 5 at lab time 0: the centre leaves the antenna at lab time 395, in this
+    frame at t' = 31 and z' = 70 (inside the box, after the start).  A station at Z
+    records the lab history while the simulation runs."""
+    b = beta(gb)
+    D = gb * (1 + b)
+    dz = D / 32
+    dt = 0.5 * dz
+    n = (8, 1, 768)
+    a0, L, zc, z_lab = 0.5, 1.5, 5.0, 400.0
+    t_emit = gb * (z_lab - zc - b * z_lab)
+    assert 0.5 * gb * 3 * L < t_emit < steps * dt  # emitted during the run
+    s = empty(n, (1.0, 1.0, dz), dt)
+    s.set_antenna(gb, [a0, 1.0, 1e9, L, zc], z_lab)
+    times, ex, by = [], [], []
+    for _ in range(steps):
+        rec = s.station_record(gb, Z)
+        if rec is not None:
+            times.append(rec[0])
+            ex.append(rec[1][0, 0, 0])
+            by.append(rec[1][4, 0, 0])
+        s.step(1)  # no particles: the Maxwell phase, and the step count the station reads
+    return np.array(times), np.array(ex), np.array(by), (a0, L, zc, z_lab)
+
+
+def test_station_downstream_records_the_lab_pulse():
+    gb = 4.0
+    Z = 500.0
+    t, ex, by, (a0, L, zc, z_lab) = lab_history(gb, Z)
+    xi = Z - zc - t
+    k0 = 2 * math.pi
+    expect = a0 * k0 * np.exp(-(xi / L) ** 2) * np.cos(k0 * xi)
+    assert t.min() < Z - zc - 3 * L and t.max() > Z - zc + 3 * L
+    assert np.abs(ex - expect).max() < 0.05 * a0 * k0
+    assert np.abs(by - ex).max() < 0.05 * a0 * k0
+
+
+def test_station_upstream_records_nothing():
+    gb = 4.0
+    Z = 300.0  # upstream of the antenna at 400: a free pulse would pass here at t = 295
+    t, ex, by, (a0, L, zc, z_lab) = lab_history(gb, Z)
+    assert t.min() < Z - zc - 3 * L and t.max() > Z - zc + 3 * L
+    assert np.abs(ex).max() < 1e-10 * a0 * 2 * math.pi
+    assert np.abs(by).max() < 1e-10 * a0 * 2 * math.pi
