@@ -284,6 +284,28 @@ pic_status pic_set_stations(pic_ctx *ctx, int count, const double *z_lab, int ma
 pic_status pic_get_station(pic_ctx *ctx, int station, int *n_records, double *t_lab, size_t t_count, double *fields,
                            size_t f_count);
 
+/* Laser antenna on a plane fixed in the laboratory (Sec. 2: the laser enters through a
+ * plane fixed in the lab frame that drifts in the boosted frame).
+ *  laser: the lab pulse (as for pic_load_lab_frame; z_center = where its envelope centre
+ *    would be at lab time 0 had it always propagated freely), or NULL to remove the
+ *    antenna.  z_lab: the plane's lab position; at boosted time t' it sits at
+ *    z' = z_lab / gamma_b - beta_b t' (t' = dt x Maxwell phases since the load).
+ * The plane emits the pulse forward: downstream of it the field includes the free pulse,
+ * upstream it does not.  The grid is split at the plane into a total-field region (z
+ * positions above the plane's position at the time of the fields) and a scattered-field
+ * region (the field minus the incident pulse); the incident pulse E'_x = B'_y =
+ * exp(-(x^2 + y^2) / w0^2) g(z', t') is carried on a 1D lattice aligned with the grid's z
+ * lattice and advanced by the same leapfrog, so a plane wave crosses the moving boundary
+ * without reflection.  Each Maxwell phase adds the incident term to the B_y and E_x
+ * differences that straddle the plane (7 small launches) and moves the values the
+ * receding plane passed into the total field.  The call adds the incident field
+ * downstream of the plane now.  Needs a loaded state (else PIC_ERR_STATE), an absorbing
+ * z axis and the Yee solver (else PIC_ERR_ARG); not valid on a batch (PIC_ERR_ARG), but a
+ * batch steps its members' antennas.  A load removes the antenna.  Device memory: two
+ * doubles per lattice node (the box, the pulse's extent upstream and the distance light
+ * covers while the plane crosses the box). */
+pic_status pic_set_laser_antenna(pic_ctx *ctx, const pic_laser_lab *laser, double z_lab);
+
 /* Beam injection through a plane fixed in the laboratory (Sec. 2: the beam enters the
  * boosted frame through a transverse lab-fixed plane that drifts in this frame; the beam
  * still upstream of it is carried by frozen, drifting macro-particles).

@@ -34,7 +34,7 @@ EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error"
             "pic_load_particles", "pic_set_field", "pic_step", "pic_run_phases", "pic_get_field",
             "pic_num_particles", "pic_get_particles", "pic_get_diagnostics", "pic_set_profiling",
             "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc", "pic_autotune",
-            "pic_set_stations", "pic_get_station", "pic_set_injection"]
+            "pic_set_stations", "pic_get_station", "pic_set_injection", "pic_set_laser_antenna"]
 PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
@@ -147,6 +147,8 @@ def lib():
         L.pic_set_stations.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         L.pic_get_station.restype = st
         L.pic_get_station.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), vp, ctypes.c_size_t, vp, ctypes.c_size_t]
+        L.pic_set_laser_antenna.restype = st
+        L.pic_set_laser_antenna.argtypes = [vp, P(pic_laser_lab), ctypes.c_double]
         L.pic_set_injection.restype = st
         L.pic_set_injection.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int32]
         L.pic_autotune.restype = st
@@ -335,6 +337,12 @@ class Simulation:
         z = np.ascontiguousarray(z_lab, dtype=np.float64)
         self._stations = z.size
         _check(lib().pic_set_stations(self.h, z.size, _ptr(z), int(max_records)), self.h)
+
+    def set_antenna(self, laser, z_lab=0.0):
+        """pic_set_laser_antenna: the lab pulse laser = (a0, lambda0, waist, duration,
+        z_center) emitted forward through the lab plane z_lab (None: remove it)."""
+        la = _lab_structs(laser, None, None)[0] if laser is not None else None
+        _check(lib().pic_set_laser_antenna(self.h, ctypes.byref(la) if la else None, float(z_lab)), self.h)
 
     def set_injection(self, z_lab, first_id=-1, enable=True):
         """pic_set_injection: beam particles (id >= first_id; -1: the last lab-frame load's

@@ -442,6 +442,27 @@ cudaError_t launch_maxwell(int fp64, int solver, const Launch &L, int filtered, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_bhalf(int fp64, int solver, const Launch &L, int damp, cudaStream_t s)
+{
+    const unsigned nb = blocks_for(L.total_cells, 256);
+    const bool ck = solver == PIC_SOLVER_CK;
+    if (fp64)
+        ck ? k_bhalf<double, true><<<nb, 256, 0, s>>>(L, damp) : k_bhalf<double, false><<<nb, 256, 0, s>>>(L, damp);
+    else
+        ck ? k_bhalf<float, true><<<nb, 256, 0, s>>>(L, damp) : k_bhalf<float, false><<<nb, 256, 0, s>>>(L, damp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_efull(int fp64, const Launch &L, int filtered, cudaStream_t s)
+{
+    const unsigned nb = blocks_for(L.total_cells, 256);
+    if (fp64)
+        k_efull<double><<<nb, 256, 0, s>>>(L, filtered);
+    else
+        k_efull<float><<<nb, 256, 0, s>>>(L, filtered);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ghost(int fp64, const Launch &L, int axis, long long per_inst_max, cudaStream_t s)
 {
     const long long n = per_inst_max * L.ninst;

@@ -65,6 +65,10 @@ struct pic_ctx {
     double inj_z = 0.0;
     int32_t inj_first = -1;          // < 0: the beam of the last lab-frame load
     int32_t beam_first_id = INT_MAX; // first beam id of the last lab-frame load (INT_MAX: none)
+    // laser antenna (pic_set_laser_antenna)
+    bool ant_on = false;
+    AntDev ant{};
+    int64_t mx_phases = 0;  // Maxwell phases since the last load
     // lab-frame stations
     int nst = 0, st_max = 0;
     double *d_st_z = nullptr, *d_st_t = nullptr;
@@ -248,6 +252,16 @@ static void apply_injection(pic_ctx *c)
     const int32_t id0 = c->inj_first >= 0 ? c->inj_first : c->beam_first_id;
     c->h.inj_id0 = c->inj_on ? id0 : INT_MAX;
     c->h.inj_zb = c->inj_z / c->gamma_b;
+}
+
+// Removes the antenna (its lattice and counter).
+static void antenna_off(pic_ctx *c)
+{
+    if (c->ant.ge) dfree(c, c->ant.ge);
+    if (c->ant.gb) dfree(c, c->ant.gb);
+    if (c->ant.n) dfree(c, c->ant.n);
+    c->ant = AntDev{};
+    c->ant_on = false;
 }
 
 static pic_status upload_inst(pic_ctx *c)
@@ -708,6 +722,8 @@ static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg, double wm
     }
     fill_step_coef(h);
     apply_injection(c);
+    antenna_off(c);  // a load removes the antenna
+    c->mx_phases = 0;
     // cur, err, live, jsel, lost and the particle-phase counter
     CUDA_OR_FAIL(c, cudaMemsetAsync(h.cur, 0, 16 + sizeof(unsigned long long) + sizeof(int), s));
     CUDA_OR_FAIL(c, cudaMemsetAsync(h.J[0], 0, 3 * (size_t)h.cstride * c->es, s));
@@ -776,6 +792,72 @@ extern "C" pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t 
     ctx->h.ion = 0;  // particles loaded directly carry no ion background
     ctx->beam_first_id = INT_MAX;
     return load_internal(ctx, n, cell, off3, u3, w, id);
+}
+
+extern "C" pic_status pic_set_laser_antenna(pic_ctx *ctx, const pic_laser_lab *laser, double z_lab)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_set_laser_antenna on a batch");
+    if (laser && !(laser->lambda0 > 0 && laser->waist > 0 && laser->duration > 0 && std::isfinite(laser->a0) &&
+                   std::isfinite(laser->z_center) && std::isfinite(z_lab)))
+        return fail(ctx, PIC_ERR_ARG, "antenna laser parameters or plane invalid");
+    if (laser && ctx->bc[2] != 1) return fail(ctx, PIC_ERR_ARG, "the laser antenna needs an absorbing z axis");
+    if (laser && ctx->opt.solver != PIC_SOLVER_YEE) return fail(ctx, PIC_ERR_ARG, "the laser antenna needs the Yee solver");
+    if (!ctx->loaded) return fail(ctx, PIC_ERR_STATE, "pic_set_laser_antenna before any load");
+    cudaSetDevice(ctx->device);
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    antenna_off(ctx);
+    destroy_graph(ctx);  // the Maxwell phase changes
+    ctx->version++;      // a batch holding this instance re-reads its parameters
+    if (!laser) return PIC_OK;
+    // the boosted pulse, as for the loaded laser: lengths x gamma_b (1 + beta_b)
+    const double gb = ctx->gamma_b, b = std::sqrt(1.0 - 1.0 / (gb * gb)), doppler = gb * (1.0 + b);
+    const double kp = 6.283185307179586 / (laser->lambda0 * doppler), Lp = laser->duration * doppler;
+    const double zc = laser->z_center * doppler, amp = laser->a0 * kp, dz = ctx->dx[2];
+    AntDev A{};
+    A.zb = z_lab / gb;
+    A.beta = b;
+    A.t0 = (double)ctx->mx_phases * ctx->dt;
+    A.w0 = laser->waist;
+    A.xc = 0.5 * ctx->n[0] * ctx->dx[0];
+    A.yc = 0.5 * ctx->n[1] * ctx->dx[1];
+    // lattice: from below the pulse's tail (5 L') and the grid to beyond the grid by the
+    // distance light covers while the plane is still in the box (no echo of the lattice's
+    // end reaches the box meanwhile)
+    const double zp0 = (A.zb - A.beta * A.t0) / dz;
+    double lo = std::floor((zc + A.t0 - 5.0 * Lp) / dz) - 2.0;
+    if (lo > 0.0) lo = 0.0;
+    const double top = std::max((double)ctx->n[2], std::ceil(zp0) + 2.0);
+    const double stay = zp0 > -1.0 && b > 0.0 ? (zp0 + 1.0) / b : 0.0;
+    const double hi = top + std::ceil(stay) + 8.0;
+    if (!(hi - lo < 1e8)) return fail(ctx, PIC_ERR_ARG, "antenna lattice of %g nodes too long", hi - lo);
+    A.lo = (long long)lo;
+    A.na = (long long)(hi - lo) + 1;
+    std::vector<double> ge((size_t)A.na), gbv((size_t)A.na);
+    for (long long a = 0; a < A.na; ++a) {
+        const double ue = (A.lo + a) * dz - A.t0 - zc, ub = (A.lo + a + 0.5) * dz - A.t0 - zc;
+        ge[a] = amp * std::exp(-(ue / Lp) * (ue / Lp)) * std::cos(kp * ue);
+        gbv[a] = amp * std::exp(-(ub / Lp) * (ub / Lp)) * std::cos(kp * ub);
+    }
+    A.ge = (double *)dalloc(ctx, sizeof(double) * (size_t)A.na);
+    A.gb = (double *)dalloc(ctx, sizeof(double) * (size_t)A.na);
+    A.n = (int *)dalloc(ctx, sizeof(int));
+    ctx->ant = A;  // owned from here (antenna_off frees what was allocated)
+    if (!A.ge || !A.gb || !A.n) {
+        antenna_off(ctx);
+        return fail(ctx, PIC_ERR_OOM, "no device memory for the antenna lattice");
+    }
+    cudaStream_t s = ctx->stream;
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(A.ge, ge.data(), sizeof(double) * ge.size(), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(A.gb, gbv.data(), sizeof(double) * gbv.size(), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(ctx, cudaMemsetAsync(A.n, 0, sizeof(int), s));
+    // the pulse already emitted: the incident field above the plane
+    CUDA_OR_FAIL(ctx, launch_ant_add(ctx->fp64, ctx->d_inst, ctx->h, A, 0, s));
+    for (int a = 0; a < 3; ++a)  // periodic x / y: refresh the ghosts the gather reads
+        if (ctx->any_periodic[a]) CUDA_OR_FAIL(ctx, launch_ghost(ctx->fp64, ctx->L, a, ctx->ghost_max, s));
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(s));
+    ctx->ant_on = true;
+    return PIC_OK;
 }
 
 extern "C" pic_status pic_set_injection(pic_ctx *ctx, int enable, double z_lab, int32_t first_id)
@@ -1022,8 +1104,34 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
     }
     if (mask & PIC_PHASE_MAXWELL) {
         tm.begin(3);
-        CUDA_OR_FAIL(c, launch_maxwell(fp64, c->opt.solver, L, filtered, c->stream));
-        launches += 3;
+        std::vector<pic_ctx *> ants;  // instances with a laser antenna
+        if (c->ant_on) ants.push_back(c);
+        for (auto m : c->members)
+            if (m->ant_on) ants.push_back(m);
+        if (ants.empty()) {
+            CUDA_OR_FAIL(c, launch_maxwell(fp64, c->opt.solver, L, filtered, c->stream));
+            launches += 3;
+        } else {
+            // the antenna's boundary terms and lattice steps between the Yee sub-updates
+            cudaStream_t s = c->stream;
+            CUDA_OR_FAIL(c, launch_bhalf(fp64, c->opt.solver, L, 0, s));
+            for (auto m : ants) {
+                CUDA_OR_FAIL(c, launch_ant_bterm(fp64, m->d_inst, m->h, m->ant, 0, s));
+                CUDA_OR_FAIL(c, launch_ant_lattice(m->ant, m->dt, m->dx[2], 0, s));
+            }
+            CUDA_OR_FAIL(c, launch_efull(fp64, L, filtered, s));
+            for (auto m : ants) {
+                CUDA_OR_FAIL(c, launch_ant_eterm(fp64, m->d_inst, m->h, m->ant, s));
+                CUDA_OR_FAIL(c, launch_ant_lattice(m->ant, m->dt, m->dx[2], 1, s));
+            }
+            CUDA_OR_FAIL(c, launch_bhalf(fp64, c->opt.solver, L, 1, s));
+            for (auto m : ants) {
+                CUDA_OR_FAIL(c, launch_ant_bterm(fp64, m->d_inst, m->h, m->ant, 1, s));
+                CUDA_OR_FAIL(c, launch_ant_lattice(m->ant, m->dt, m->dx[2], 2, s));
+                CUDA_OR_FAIL(c, launch_ant_add(fp64, m->d_inst, m->h, m->ant, 1, s));
+            }
+            launches += 3 + 7 * (int)ants.size();
+        }
         for (int a = 0; a < 3; ++a)
             if (c->any_periodic[a]) {
                 CUDA_OR_FAIL(c, launch_ghost(fp64, L, a, c->ghost_max, c->stream));
@@ -1086,8 +1194,9 @@ extern "C" pic_status pic_step(pic_ctx *ctx, int n)
             CUDA_OR_FAIL(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
         }
         ctx->step++;
+        ctx->mx_phases++;
         if (ctx->is_batch)
-            for (auto m : ctx->members) m->step++;
+            for (auto m : ctx->members) m->step++, m->mx_phases++;
     }
     return PIC_OK;
 }
@@ -1109,6 +1218,11 @@ extern "C" pic_status pic_run_phases(pic_ctx *ctx, int mask)
         ctx->step++;
         if (ctx->is_batch)
             for (auto m : ctx->members) m->step++;
+    }
+    if (mask & PIC_PHASE_MAXWELL) {
+        ctx->mx_phases++;
+        if (ctx->is_batch)
+            for (auto m : ctx->members) m->mx_phases++;
     }
     return PIC_OK;
 }

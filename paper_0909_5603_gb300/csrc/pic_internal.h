@@ -199,6 +199,17 @@ struct StationDev {
     int max_records;
 };
 
+// Laser antenna of one instance (k_antenna.cu): the incident pulse on a 1D lattice
+// aligned with the grid's z lattice, and the lab plane it is emitted through
+struct AntDev {
+    double *ge, *gb;      // E_x on lattice nodes lo .. lo + na - 1, B_y half a node above
+    long long lo, na;
+    double zb, beta;      // the plane: z' = zb - beta t'
+    double t0;            // t' when the antenna was set
+    double w0, xc, yc;    // transverse profile exp(-((x - xc)^2 + (y - yc)^2) / w0^2)
+    int *n;               // Maxwell phases since the antenna was set (device counter)
+};
+
 // host-side launchers
 cudaError_t launch_stations(int fp64, const InstDev *d_inst, const StationDev &S, int nst, int plane, cudaStream_t s);
 cudaError_t launch_place(int fp64, const InstDev &I, const PlaceSrc &s, cudaStream_t st);
@@ -231,6 +242,15 @@ inline long long filter_pencils(const int n[3], int ndim, int axis)
     return cols * ((n[2] + kP - 1) / kP) * n[1];
 }
 cudaError_t launch_maxwell(int fp64, int solver, const Launch &L, int filtered, cudaStream_t s);
+// the three sub-updates of launch_maxwell, for interleaving the antenna's kernels
+cudaError_t launch_bhalf(int fp64, int solver, const Launch &L, int damp, cudaStream_t s);
+cudaError_t launch_efull(int fp64, const Launch &L, int filtered, cudaStream_t s);
+// antenna: what = 0 adds the incident field downstream of the plane (when set), 1 the
+// values the plane passed in the last phase; B_y / E_x terms of the boundary; 1D lattice
+cudaError_t launch_ant_add(int fp64, const InstDev *d_inst, const InstDev &I, const AntDev &A, int what, cudaStream_t s);
+cudaError_t launch_ant_bterm(int fp64, const InstDev *d_inst, const InstDev &I, const AntDev &A, int damp, cudaStream_t s);
+cudaError_t launch_ant_eterm(int fp64, const InstDev *d_inst, const InstDev &I, const AntDev &A, cudaStream_t s);
+cudaError_t launch_ant_lattice(const AntDev &A, double dt, double dz, int what, cudaStream_t s);
 cudaError_t launch_ghost(int fp64, const Launch &L, int axis, long long per_inst_max, cudaStream_t s);
 cudaError_t prepare_particles(int ndim, int order, int fp64, int pusher, size_t smem);
 cudaError_t launch_field_energy(int fp64, const Launch &L, double *sums, cudaStream_t s);
