@@ -278,6 +278,35 @@ def test_gauss_law_residual_constant(order, ndim):
     assert s.diagnostics()["field_energy"] > 1e-6
 
 
+@pytest.mark.parametrize("passes", [1, 3])
+def test_gauss_law_with_filter_conserves_filtered_charge(passes):
+    """With the current filtered, E changes by -dt div(F J) = -dt F div J (the binomial
+    filter is a convolution, which commutes with the differences on a periodic grid), so
+    div E - F rho is what stays constant, F the same 1-2-1 passes on the nodes; div E - rho
+    does not."""
+    rng = np.random.default_rng(22)
+    n = (16, 12, 16)
+    s2 = oracle.Sim(3, n, (0, 0, 0), (1.0, 1.0, 1.0), 0.45, order=2, filter_passes=passes, tile=(8, 4, 8))
+    nc = n[0] * n[1] * n[2]
+    cell = np.repeat(np.arange(nc), 2).astype(np.int32)
+    off = rng.random((cell.size, 3))
+    u = rng.normal(0, 0.3, (cell.size, 3))
+    s2.set_particles(cell, off, u, np.full(cell.size, 0.5))
+
+    def F(rho):
+        f = rho.copy()
+        for _ in range(passes):
+            for ax in (2, 1, 0):
+                f = 0.25 * np.roll(f, 1, ax) + 0.5 * f + 0.25 * np.roll(f, -1, ax)
+        return f
+
+    r0, q0 = s2.div_e() - F(s2.rho()), s2.div_e() - s2.rho()
+    s2.step(12)
+    r1, q1 = s2.div_e() - F(s2.rho()), s2.div_e() - s2.rho()
+    assert np.abs(r1 - r0).max() < 1e-12
+    assert np.abs(q1 - q0).max() > 1e-3
+
+
 def test_diagnostics_closed_forms():
     s = make(3, (8, 8, 8), dx=(1.0, 0.5, 2.0))
     s.set_field(EY, np.full((8, 8, 8), 0.3))
