@@ -285,6 +285,191 @@ __global__ void __launch_bounds__(256) k_filter_axis(Launch L, int axis, const l
     }
 }
 
+// The same filter with the number of passes P known at compile time (P <= 4, every
+// instance of the launch alike), in registers, without shared memory or barriers, on the
+// pencils of k_filter_axis.  Binomial weight C(2P, m) / 4^P of tap m (exact in FP32).
+__host__ __device__ constexpr double binomial_weight(int P, int m)
+{
+    double c = 1.0;
+    for (int t = 1; t <= m; ++t) c = c * (2 * P - t + 1) / t;
+    return c / (double)(1 << (2 * P));
+}
+
+// y and z axes: lane = x column (coalesced), each warp takes kPencil / 8 consecutive
+// cells along the axis and loads them with P halo cells per side into registers.  Away
+// from the ends the output is the (2P+1)-tap convolution; a window that wraps (periodic)
+// is loaded wrapped and convolved too; one that reaches past an absorbing face runs the
+// P passes, re-zeroing the outside after each.
+template <typename R, int P>
+__global__ void __launch_bounds__(256) k_filter_col(Launch L, int axis, const long long *pencil_start, int src_is_jt)
+{
+    constexpr int S = kPencil / 8;
+    constexpr int W = S + 2 * P;
+    const long long g = blockIdx.x;
+    if (g >= pencil_start[L.ninst]) return;
+    const int ii = find_instance_ll(pencil_start, L.ninst, g);
+    const InstDev &I = L.inst[ii];
+    if (!filter_active_axis(I, axis)) return;
+    const int n = I.n[axis];
+    const bool per = I.bc[axis] == 0;
+    const int nseg = (n + kPencil - 1) / kPencil;
+    long long r = g - pencil_start[ii];
+    const int qs = (int)(r % nseg) * kPencil + (threadIdx.x >> 5) * S;  // this thread's first cell
+    r /= nseg;
+    const int ncol = (I.n[0] + 31) / 32;
+    const int x = (int)(r % ncol) * 32 + (threadIdx.x & 31);
+    const int other = (int)(r / ncol);  // z for the y axis, y for the z axis
+    if (x >= I.n[0] || qs >= n) return;
+    const long long sa = axis == 1 ? I.sy : I.sz;
+    const long long lo = axis == 1 ? (x + I.gh[0]) + I.sy * I.gh[1] + I.sz * (long long)(other + I.gh[2])
+                                   : (x + I.gh[0]) + I.sy * (long long)(other + I.gh[1]) + I.sz * I.gh[2];
+    const bool inside = qs - P >= 0 && qs + S + P <= n;
+    void *const *src = src_is_jt ? I.Jt : I.J;
+    void *const *dst = src_is_jt ? I.J : I.Jt;
+    // all three windows first (the source and destination arrays differ)
+    R win[3][W];
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+        const R *__restrict__ a = (const R *)src[comp];
+        if (inside) {
+#pragma unroll
+            for (int m = 0; m < W; ++m) win[comp][m] = a[lo + (long long)(qs - P + m) * sa];
+        } else {
+#pragma unroll
+            for (int m = 0; m < W; ++m) {
+                int q = qs - P + m;
+                bool ok = true;
+                if (q < 0 || q >= n) {
+                    if (per) q = ((q % n) + n) % n;
+                    else ok = false;
+                }
+                win[comp][m] = ok ? a[lo + (long long)q * sa] : R(0);
+            }
+        }
+    }
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+        R w[W];
+#pragma unroll
+        for (int m = 0; m < W; ++m) w[m] = win[comp][m];
+        R out[S];
+        if (inside || per) {
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                R v = R(0);
+#pragma unroll
+                for (int m = 0; m <= 2 * P; ++m) v += R(binomial_weight(P, m)) * w[t + m];
+                out[t] = v;
+            }
+        } else {
+#pragma unroll
+            for (int pass = 1; pass <= P; ++pass) {
+                R nw[W];
+#pragma unroll
+                for (int m = 0; m < W; ++m) nw[m] = w[m];
+#pragma unroll
+                for (int m = pass; m < W - pass; ++m) {
+                    const int q = qs - P + m;
+                    nw[m] = (q < 0 || q >= n) ? R(0) : R(0.25) * w[m - 1] + R(0.5) * w[m] + R(0.25) * w[m + 1];
+                }
+#pragma unroll
+                for (int m = 0; m < W; ++m) w[m] = nw[m];
+            }
+#pragma unroll
+            for (int t = 0; t < S; ++t) out[t] = w[t + P];
+        }
+        R *__restrict__ b = (R *)dst[comp];
+#pragma unroll
+        for (int t = 0; t < S; ++t)
+            if (qs + t < n) b[lo + (long long)(qs + t) * sa] = out[t];
+    }
+}
+
+// x axis: warp w takes rows w, w + 8, w + 16, w + 24 of the pencil; per row it loads the
+// kPencil + 2P window of all three components with coalesced loads into its own slice of
+// shared memory (warp-synchronous, no block barrier) and each lane forms two outputs
+// from it.  Cells within P of an end convolve the wrapped window (periodic) or run the
+// passes (absorbing).
+template <typename R, int P>
+__global__ void __launch_bounds__(256) k_filter_row(Launch L, const long long *pencil_start, int src_is_jt)
+{
+    constexpr int W = kPencil + 2 * P;
+    __shared__ R sw[8][3][W];
+    const long long g = blockIdx.x;
+    if (g >= pencil_start[L.ninst]) return;
+    const int ii = find_instance_ll(pencil_start, L.ninst, g);
+    const InstDev &I = L.inst[ii];
+    if (!filter_active_axis(I, 0)) return;
+    const int n = I.n[0];
+    const bool per = I.bc[0] == 0;
+    const int nseg = (n + kPencil - 1) / kPencil;
+    long long r = g - pencil_start[ii];
+    const int q0 = (int)(r % nseg) * kPencil;
+    r /= nseg;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool inside = q0 - P >= 0 && q0 + kPencil + P <= n;
+    void *const *src = src_is_jt ? I.Jt : I.J;
+    void *const *dst = src_is_jt ? I.J : I.Jt;
+    R(*win)[W] = sw[warp];
+#pragma unroll 1
+    for (int rr = warp; rr < 32; rr += 8) {
+        const long long row = r * 32 + rr;
+        if (row >= (long long)I.n[1] * I.n[2]) break;
+        const int y = (int)(row % I.n[1]), z = (int)(row / I.n[1]);
+        const long long lo = I.gh[0] + I.sy * (long long)(y + I.gh[1]) + I.sz * (long long)(z + I.gh[2]);
+#pragma unroll
+        for (int i0 = 0; i0 < W; i0 += 32) {
+            const int i = i0 + lane;
+            if (i < W) {
+                int q = q0 - P + i;
+                bool ok = true;
+                if (!inside && (q < 0 || q >= n)) {
+                    if (per) q = ((q % n) + n) % n;
+                    else ok = false;
+                }
+#pragma unroll
+                for (int comp = 0; comp < 3; ++comp) win[comp][i] = ok ? ((const R *)src[comp])[lo + q] : R(0);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = lane + 32 * h;  // output q0 + t, window cells t .. t + 2P
+            const int q = q0 + t;
+            if (q >= n) continue;
+            const bool conv = per || (q - P >= 0 && q + P < n);
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                R w[2 * P + 1];
+#pragma unroll
+                for (int m = 0; m <= 2 * P; ++m) w[m] = win[comp][t + m];
+                R v = R(0);
+                if (conv) {
+#pragma unroll
+                    for (int m = 0; m <= 2 * P; ++m) v += R(binomial_weight(P, m)) * w[m];
+                } else {
+#pragma unroll
+                    for (int pass = 1; pass <= P; ++pass) {
+                        R nw[2 * P + 1];
+#pragma unroll
+                        for (int m = 0; m <= 2 * P; ++m) nw[m] = w[m];
+#pragma unroll
+                        for (int m = pass; m <= 2 * P - pass; ++m) {
+                            const int qq = q - P + m;
+                            nw[m] = (qq < 0 || qq >= n) ? R(0) : R(0.25) * w[m - 1] + R(0.5) * w[m] + R(0.25) * w[m + 1];
+                        }
+#pragma unroll
+                        for (int m = 0; m <= 2 * P; ++m) w[m] = nw[m];
+                    }
+                    v = w[P];
+                }
+                ((R *)dst[comp])[lo + q] = v;
+            }
+        }
+        __syncwarp();  // the window is reloaded for the next row
+    }
+}
+
 // Periodic ghost exchange of the six E/B components along one axis (after the whole
 // step); ghosts of earlier axes are included so corners come out right.
 template <typename R>
@@ -403,8 +588,30 @@ __global__ void k_dive(InstDev I, double *dense, long long ncell)
 // ------------------------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+template <typename R, int P>
+static void filter_fixed(const Launch &L, int axis, unsigned nb, const long long *start, int src_is_jt, cudaStream_t s)
+{
+    if (axis == 0)
+        k_filter_row<R, P><<<nb, 256, 0, s>>>(L, start, src_is_jt);
+    else
+        k_filter_col<R, P><<<nb, 256, 0, s>>>(L, axis, start, src_is_jt);
+}
+
+template <typename R>
+static void filter_axis(const Launch &L, int axis, int passes, unsigned nb, const long long *start, int src_is_jt,
+                        cudaStream_t s)
+{
+    switch (passes) {
+    case 1: filter_fixed<R, 1>(L, axis, nb, start, src_is_jt, s); break;
+    case 2: filter_fixed<R, 2>(L, axis, nb, start, src_is_jt, s); break;
+    case 3: filter_fixed<R, 3>(L, axis, nb, start, src_is_jt, s); break;
+    case 4: filter_fixed<R, 4>(L, axis, nb, start, src_is_jt, s); break;
+    default: k_filter_axis<R><<<nb, 256, 0, s>>>(L, axis, start, src_is_jt); break;
+    }
+}
+
 cudaError_t launch_filter(int fp64, const Launch &L, const long long *const pencil_start[3],
-                          const long long pencil_total[3], int ndim, cudaStream_t s)
+                          const long long pencil_total[3], int ndim, int passes, cudaStream_t s)
 {
     // axes in order x, (y,) z; sweep k reads J when k is even, Jt when odd
     int k = 0;
@@ -412,11 +619,10 @@ cudaError_t launch_filter(int fp64, const Launch &L, const long long *const penc
         if (ndim == 2 && axis == 1) continue;
         if (pencil_total[axis] > 0) {
             const unsigned nb = (unsigned)pencil_total[axis];
-            const int threads = 256;
             if (fp64)
-                k_filter_axis<double><<<nb, threads, 0, s>>>(L, axis, pencil_start[axis], k & 1);
+                filter_axis<double>(L, axis, passes, nb, pencil_start[axis], k & 1, s);
             else
-                k_filter_axis<float><<<nb, threads, 0, s>>>(L, axis, pencil_start[axis], k & 1);
+                filter_axis<float>(L, axis, passes, nb, pencil_start[axis], k & 1, s);
         }
         ++k;
     }

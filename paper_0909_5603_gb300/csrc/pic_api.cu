@@ -1097,7 +1097,10 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
         const int nin = c->is_batch ? (int)c->members.size() : 1;
         const long long *starts[3] = {c->d_pencil, c->d_pencil + (nin + 1), c->d_pencil + 2 * (nin + 1)};
         tm.begin(2);
-        CUDA_OR_FAIL(c, launch_filter(fp64, L, starts, c->pencil_total, c->ndim, c->stream));
+        int passes = c->opt.filter_passes;  // the compile-time kernels need one count for all
+        for (auto m : c->members)
+            if (m->opt.filter_passes != passes) passes = 0;
+        CUDA_OR_FAIL(c, launch_filter(fp64, L, starts, c->pencil_total, c->ndim, passes, c->stream));
         tm.end(2);
         filtered = 1;
         for (int a = 0; a < 3; ++a) launches += c->pencil_total[a] > 0 ? 1 : 0;

@@ -228,8 +228,9 @@ cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, i
                            double *w, int *id, cudaStream_t s);
 cudaError_t launch_particle_sums(int fp64, const Launch &L, double *sums, cudaStream_t s);
 cudaError_t launch_rho(int order, int fp64, const Launch &L, double *rho, cudaStream_t s);
+// passes: the filter passes of every instance of the launch (0 when they differ)
 cudaError_t launch_filter(int fp64, const Launch &L, const long long *const pencil_start[3],
-                          const long long pencil_total[3], int ndim, cudaStream_t s);
+                          const long long pencil_total[3], int ndim, int passes, cudaStream_t s);
 // pencils of the per-axis filter kernel for an instance: kPencil (64) cells along the
 // axis times 32 lines (x: 32 consecutive (y, z) rows; y, z: 32 consecutive x columns)
 inline long long filter_pencils(const int n[3], int ndim, int axis)
