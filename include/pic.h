@@ -234,6 +234,18 @@ pic_status pic_run_phases(pic_ctx *ctx, int phase_mask);
  * count >= n0 n1 n2.  J is the current used by the last Maxwell update (after filter). */
 pic_status pic_get_field(pic_ctx *ctx, int comp, double *host_out, size_t count);
 
+/* Copies ncomp components (as for pic_get_field) into host_out[ncomp][n2][n1][n0],
+ * count >= ncomp n0 n1 n2; comps[i] as pic_get_field.  Synchronises. */
+pic_status pic_get_fields(pic_ctx *ctx, const int *comps, int ncomp, double *host_out, size_t count);
+
+/* Gauss-law residual on the nodes: *max_abs = max |div E - rho| and, when rms is not NULL,
+ * *rms = sqrt(mean (div E - rho)^2), with div E and rho (particles and ion background)
+ * as PIC_DIVE and PIC_RHO, in FP64 on the device.  The Esirkepov deposit keeps div E - rho
+ * constant in time when the current is not filtered (with the binomial filter on, div E -
+ * F rho is the constant one, F the same passes on the nodes).  Synchronises; device
+ * memory for one n0 n1 n2 array of doubles during the call. */
+pic_status pic_get_gauss_residual(pic_ctx *ctx, double *max_abs, double *rms);
+
 /* Number of live particles (synchronises). */
 pic_status pic_num_particles(pic_ctx *ctx, int64_t *n_out);
 

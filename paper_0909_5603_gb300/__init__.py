@@ -34,7 +34,8 @@ EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error"
             "pic_load_particles", "pic_set_field", "pic_step", "pic_run_phases", "pic_get_field",
             "pic_num_particles", "pic_get_particles", "pic_get_diagnostics", "pic_set_profiling",
             "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc", "pic_autotune",
-            "pic_set_stations", "pic_get_station", "pic_set_injection", "pic_set_laser_antenna"]
+            "pic_set_stations", "pic_get_station", "pic_set_injection", "pic_set_laser_antenna",
+            "pic_get_fields", "pic_get_gauss_residual"]
 PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
@@ -147,6 +148,10 @@ def lib():
         L.pic_set_stations.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         L.pic_get_station.restype = st
         L.pic_get_station.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), vp, ctypes.c_size_t, vp, ctypes.c_size_t]
+        L.pic_get_fields.restype = st
+        L.pic_get_fields.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_size_t]
+        L.pic_get_gauss_residual.restype = st
+        L.pic_get_gauss_residual.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double)]
         L.pic_set_laser_antenna.restype = st
         L.pic_set_laser_antenna.argtypes = [vp, P(pic_laser_lab), ctypes.c_double]
         L.pic_set_injection.restype = st
@@ -337,6 +342,19 @@ class Simulation:
         z = np.ascontiguousarray(z_lab, dtype=np.float64)
         self._stations = z.size
         _check(lib().pic_set_stations(self.h, z.size, _ptr(z), int(max_records)), self.h)
+
+    def get_fields(self, comps):
+        """pic_get_fields: several components as one (ncomp, n2, n1, n0) array."""
+        c = np.ascontiguousarray(comps, dtype=np.int32)
+        out = np.empty((c.size, self.n[2], self.n[1], self.n[0]))
+        _check(lib().pic_get_fields(self.h, _ptr(c), c.size, _ptr(out), out.size), self.h)
+        return out
+
+    def gauss_residual(self):
+        """pic_get_gauss_residual: (max |div E - rho|, rms)."""
+        m, r = ctypes.c_double(), ctypes.c_double()
+        _check(lib().pic_get_gauss_residual(self.h, ctypes.byref(m), ctypes.byref(r)), self.h)
+        return m.value, r.value
 
     def set_antenna(self, laser, z_lab=0.0):
         """pic_set_laser_antenna: the lab pulse laser = (a0, lambda0, waist, duration,

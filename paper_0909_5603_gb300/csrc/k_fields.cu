@@ -8,6 +8,8 @@
 // zero ghost layers.
 #include "pic_internal.h"
 
+#include <algorithm>
+
 namespace pic {
 
 struct CellPos {
@@ -699,6 +701,36 @@ cudaError_t launch_unpack(int fp64, const InstDev &I, int comp, const double *de
 {
     if (fp64) k_unpack<double><<<blocks_for(ncell, 256), 256, 0, s>>>(I, comp, dense, ncell);
     else k_unpack<float><<<blocks_for(ncell, 256), 256, 0, s>>>(I, comp, dense, ncell);
+    return cudaGetLastError();
+}
+
+// max |a - b| and sum (a - b)^2 over n values (FP64); the maximum is kept as the bit
+// pattern of a non-negative double, which orders like the value
+__global__ void __launch_bounds__(256) k_residual(const double *a, const double *b, long long n,
+                                                  unsigned long long *max_bits, double *sumsq)
+{
+    double m = 0.0, q = 0.0;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+        const double d = fabs(a[g] - b[g]);
+        m = fmax(m, d);
+        q += d * d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(max_bits, (unsigned long long)__double_as_longlong(m));
+        atomicAdd(sumsq, q);
+    }
+}
+
+cudaError_t launch_residual(const double *a, const double *b, long long n, unsigned long long *max_bits, double *sumsq,
+                            cudaStream_t s)
+{
+    const long long blocks = std::min<long long>(blocks_for(n, 256), 152LL * 8);
+    k_residual<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(a, b, n, max_bits, sumsq);
     return cudaGetLastError();
 }
 

@@ -1288,6 +1288,45 @@ extern "C" pic_status pic_get_field(pic_ctx *ctx, int comp, double *host_out, si
     return check_device_error(ctx);
 }
 
+extern "C" pic_status pic_get_fields(pic_ctx *ctx, const int *comps, int ncomp, double *host_out, size_t count)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ncomp < 1 || !comps) return fail(ctx, PIC_ERR_ARG, "need at least one component");
+    if (!host_out || count / (size_t)ncomp < (size_t)ctx->ncell)
+        return fail(ctx, PIC_ERR_ARG, "need room for %d x %lld values", ncomp, ctx->ncell);
+    for (int i = 0; i < ncomp; ++i) {
+        const pic_status st = pic_get_field(ctx, comps[i], host_out + (size_t)i * ctx->ncell, (size_t)ctx->ncell);
+        if (st != PIC_OK) return st;
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_gauss_residual(pic_ctx *ctx, double *max_abs, double *rms)
+{
+    if (!ctx || !max_abs) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "getters take a member, not a batch");
+    pic_status st = pic_synchronize(ctx);
+    if (st != PIC_OK) return st;
+    double *rho = (double *)dalloc(ctx, sizeof(double) * (size_t)ctx->ncell);
+    if (!rho) return fail(ctx, PIC_ERR_OOM, "no device memory for the charge density");
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(rho, 0, sizeof(double) * (size_t)ctx->ncell, s);
+    if (e == cudaSuccess && ctx->loaded) e = launch_rho(ctx->order, ctx->fp64, ctx->L, rho, s);
+    if (e == cudaSuccess) e = launch_dive(ctx->fp64, ctx->h, ctx->d_dense, ctx->ncell, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_sums, 0, 2 * sizeof(double), s);
+    if (e == cudaSuccess)
+        e = launch_residual(ctx->d_dense, rho, ctx->ncell, (unsigned long long *)ctx->d_sums, ctx->d_sums + 1, s);
+    double host[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = d2h(ctx, host, ctx->d_sums, sizeof(host));
+    dfree(ctx, rho);
+    if (e != cudaSuccess) return fail(ctx, PIC_ERR_CUDA, "Gauss residual: %s", cudaGetErrorString(e));
+    unsigned long long bits;
+    std::memcpy(&bits, &host[0], sizeof(bits));
+    std::memcpy(max_abs, &bits, sizeof(double));
+    if (rms) *rms = std::sqrt(host[1] / (double)ctx->ncell);
+    return check_device_error(ctx);
+}
+
 static pic_status count_live(pic_ctx *c, int with_offsets, int *live)
 {
     CUDA_OR_FAIL(c, launch_scan(c->L, 1, c->d_start_ptr, c->stream));

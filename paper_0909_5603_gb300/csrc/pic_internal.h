@@ -258,6 +258,9 @@ cudaError_t launch_field_energy(int fp64, const Launch &L, double *sums, cudaStr
 cudaError_t launch_pack(int fp64, const InstDev &I, int comp, int filtered, double *dense, long long ncell, cudaStream_t s);
 cudaError_t launch_unpack(int fp64, const InstDev &I, int comp, const double *dense, long long ncell, cudaStream_t s);
 cudaError_t launch_dive(int fp64, const InstDev &I, double *dense, long long ncell, cudaStream_t s);
+// max |a - b| (as the bits of a non-negative double, atomicMax) and sum (a - b)^2
+cudaError_t launch_residual(const double *a, const double *b, long long n, unsigned long long *max_bits, double *sumsq,
+                            cudaStream_t s);
 
 // Read-only view of a pic_ctx (defined in pic_api.cu) for entry points in other files.
 struct CtxView {

@@ -327,6 +327,25 @@ def test_rho_dive_and_diagnostics_fp64():
     assert dg["n_particles"] == do["n_particles"] and dg["step"] == do["step"] == 2
 
 
+def test_get_fields_and_gauss_residual():
+    n = (20, 16, 24)
+    g, o = pair(3, n, (0, 1, 0), (1.0, 0.9, 1.1), 0.45, 2, FP64)
+    set_fields_both(g, o, synth.smooth_fields(n, 3, 0.1, seed=28))
+    load_both(g, o, synth.random_particles(n, 3, 5000, 0.5, seed=29))
+    g.step(2)
+    o.step(2)
+    comps = [pic.PIC_EX, pic.PIC_BZ, pic.PIC_JY, pic.PIC_RHO]
+    many = g.get_fields(comps)
+    for i, c in enumerate(comps[:3]):  # stored components: the same values
+        assert np.array_equal(many[i], g.get_field(c)), c
+    # rho is deposited anew by each call, with FP64 atomics in no fixed order
+    assert rel(many[3], g.get_field(pic.PIC_RHO)) <= 1e-13
+    r = o.div_e() - o.rho()
+    m, rms = g.gauss_residual()
+    assert abs(m - np.abs(r).max()) <= 1e-12 * np.abs(r).max()
+    assert abs(rms - np.sqrt(np.mean(r * r))) <= 1e-12 * np.sqrt(np.mean(r * r))
+
+
 @pytest.mark.parametrize("order", [1, 2])
 def test_gauss_law_on_gpu(order):
     """Esirkepov + Yee on the GPU keep div E - rho constant to round-off (FP64)."""
