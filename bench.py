@@ -50,7 +50,7 @@ def workload(nz=N_GRID[2]):
 # sources are the ones that were captured
 PROFILE = os.path.join(ROOT, "profiles", "k_particles_lwfa_128x128x128.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0909_5603_gb300", "csrc", f)
-                  for f in ("k_particles.cuh", "pic_device.cuh", "k_push.cuh", "k_push_f32.cu", "pic_internal.h")]
+                  for f in ("k_particles.cuh", "pic_device.cuh", "k_push.cuh", "k_push_f32.cu", "pic_instance.h")]
 
 
 def kernel_source_hash():
