@@ -508,6 +508,8 @@ __global__ void __launch_bounds__(256) k_ghost(Launch L, int axis, long long per
 template <typename R>
 __global__ void __launch_bounds__(256) k_field_energy(Launch L, double *sums)
 {
+    __shared__ double s_e[8];
+    __shared__ int s_ii[8];
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     CellPos c;
     const InstDev *Ip;
@@ -516,20 +518,43 @@ __global__ void __launch_bounds__(256) k_field_energy(Launch L, double *sums)
     if (cell_of(L, g, c, Ip)) {
         const InstDev &I = *Ip;
         ii = c.ii;
+        R s2 = R(0);  // the cell's E^2 + B^2 in the storage precision, then FP64
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double x = ((const R *)I.E[a])[c.p], y = ((const R *)I.B[a])[c.p];
-            e += x * x + y * y;
+            const R x = ((const R *)I.E[a])[c.p], y = ((const R *)I.B[a])[c.p];
+            s2 += x * x + y * y;
         }
-        e *= 0.5 * I.dx[0] * I.dx[1] * I.dx[2];
+        e = (double)s2 * (0.5 * I.dx[0] * I.dx[1] * I.dx[2]);
     }
-    // instances are contiguous in g: reduce per warp when the whole warp shares one
+    // instances are contiguous in g: reduce per warp when the whole warp shares one, then
+    // per block (one atomic per instance present in the block)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ii0 = __shfl_sync(0xffffffffu, ii, 0);
     const bool same = __all_sync(0xffffffffu, ii == ii0 || ii < 0);
     if (same) {
         for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-        if ((threadIdx.x & 31) == 0 && ii0 >= 0) atomicAdd(sums + 2 * L.ninst + ii0, e);
-    } else if (ii >= 0) {
-        atomicAdd(sums + 2 * L.ninst + ii, e);
+        if (lane == 0) {
+            s_e[warp] = e;
+            s_ii[warp] = ii0;
+        }
+    } else {
+        if (ii >= 0) atomicAdd(sums + 2 * L.ninst + ii, e);
+        if (lane == 0) s_ii[warp] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int cur = -1;
+        double acc = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (s_ii[w] < 0) continue;
+            if (s_ii[w] != cur) {
+                if (cur >= 0) atomicAdd(sums + 2 * L.ninst + cur, acc);
+                cur = s_ii[w];
+                acc = 0.0;
+            }
+            acc += s_e[w];
+        }
+        if (cur >= 0) atomicAdd(sums + 2 * L.ninst + cur, acc);
     }
 }
 

@@ -147,8 +147,15 @@ __global__ void __launch_bounds__(256) k_particle_sums(Launch L, double *sums /*
             int cell;
             R o[3], u[3], w;
             load_particle(I, cur, start + p, cell, o, u, w);
-            const double g2 = 1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
-            ke += (double)w * I.m * (sqrt(g2) - 1.0);
+            if (sizeof(R) == 8) {
+                const double g2 = 1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
+                ke += (double)w * I.m * (sqrt(g2) - 1.0);
+            } else {
+                // FP32 storage: gamma - 1 = u^2 / (1 + gamma) in FP32 (no cancellation; the
+                // stored momenta carry FP32 precision anyway), summed in FP64
+                const float uu = (float)u[0] * (float)u[0] + (float)u[1] * (float)u[1] + (float)u[2] * (float)u[2];
+                ke += (double)((float)w * (uu / (1.f + sqrtf(1.f + uu)))) * I.m;
+            }
             q += I.q * (double)w;
         }
     }
@@ -156,9 +163,21 @@ __global__ void __launch_bounds__(256) k_particle_sums(Launch L, double *sums /*
         ke += __shfl_down_sync(0xffffffffu, ke, o);
         q += __shfl_down_sync(0xffffffffu, q, o);
     }
+    // one pair of atomics per block (the tile's instance), not per warp
+    __shared__ double s_ke[8], s_q[8];
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(sums + 2 * ii + 0, ke);
-        atomicAdd(sums + 2 * ii + 1, q);
+        s_ke[threadIdx.x >> 5] = ke;
+        s_q[threadIdx.x >> 5] = q;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += s_ke[w];
+            b += s_q[w];
+        }
+        if (a != 0.0) atomicAdd(sums + 2 * ii + 0, a);
+        if (b != 0.0) atomicAdd(sums + 2 * ii + 1, b);
     }
 }
 

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/pic.h"
@@ -625,6 +626,28 @@ static pic_status ensure_particle_capacity(pic_ctx *c, int64_t n)
 }
 
 // Tile of a cell index (linear, x fastest).
+// Host loops over many particles: fn(t, begin, end) on T threads over contiguous ranges
+// of [0, n) in order (T = 1 below 2^18 items).
+static int host_workers(int64_t n)
+{
+    if (n < (1 << 18)) return 1;
+    const unsigned hw = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(hw ? hw : 1u, 16u));
+}
+
+template <typename F>
+static void parallel_ranges(int64_t n, int T, F fn)
+{
+    if (T <= 1) {
+        fn(0, (int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(T);
+    for (int t = 0; t < T; ++t) th.emplace_back(fn, t, n * t / T, n * (t + 1) / T);
+    for (auto &x : th) x.join();
+}
+
 static int tile_of_cell(const pic_ctx *c, int cell)
 {
     const InstDev &h = c->h;
@@ -754,28 +777,74 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
     InstDev &h = c->h;
     if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", (long long)n);
     if (n > 0 && (!cell || !off || !u || !w)) return fail(c, PIC_ERR_ARG, "particle arrays must not be NULL");
-    double wmax = 0.0;
-    for (int64_t p = 0; p < n; ++p) {
-        if (cell[p] < 0 || cell[p] >= c->ncell) return fail(c, PIC_ERR_ARG, "particle %lld: cell %d outside the grid", (long long)p, cell[p]);
-        for (int a = 0; a < 3; ++a) {
-            if (!activeaxis(c->ndim, a)) continue;
-            const double o = off[3 * p + a];
-            if (!(o >= 0.0 && o < 1.0)) return fail(c, PIC_ERR_ARG, "particle %lld: offset %g outside [0,1)", (long long)p, o);
-        }
-        if (!finite3(u + 3 * p) || !std::isfinite(w[p])) return fail(c, PIC_ERR_NAN, "particle %lld: non-finite momentum or weight", (long long)p);
-        wmax = std::max(wmax, std::fabs(w[p]));
-    }
-    // stable counting sort by tile id: seg (segment starts) and each particle's slot
+    // validation and a stable counting sort by tile id, on T host threads over contiguous
+    // ranges: each range finds its first invalid particle (the lowest over the ranges is
+    // the one reported), its largest |w| and its tile histogram; slots are then assigned
+    // range by range in order, which keeps the sort stable
+    const int T = host_workers(n);
+    std::vector<int64_t> bad(T, INT64_MAX);
+    std::vector<int> bad_kind(T, 0);
+    std::vector<double> wmaxs(T, 0.0);
+    std::vector<std::vector<int>> hist(T);
     std::vector<int> seg(h.ntiles + 1, 0), slot(n > 0 ? n : 1);
-    for (int64_t p = 0; p < n; ++p) {
-        slot[p] = tile_of_cell(c, cell[p]);
-        seg[slot[p] + 1]++;
+    parallel_ranges(n, T, [&](int t, int64_t b, int64_t e) {
+        for (int64_t p = b; p < e; ++p) {
+            int kind = 0;
+            if (cell[p] < 0 || cell[p] >= c->ncell) kind = 1;
+            for (int a = 0; a < 3 && !kind; ++a) {
+                if (!activeaxis(c->ndim, a)) continue;
+                const double o = off[3 * p + a];
+                if (!(o >= 0.0 && o < 1.0)) kind = 2;
+            }
+            if (!kind && (!finite3(u + 3 * p) || !std::isfinite(w[p]))) kind = 3;
+            if (kind) {
+                bad[t] = p;
+                bad_kind[t] = kind;
+                return;
+            }
+            wmaxs[t] = std::max(wmaxs[t], std::fabs(w[p]));
+        }
+        std::vector<int> &hc = hist[t];
+        hc.assign(h.ntiles, 0);
+        for (int64_t p = b; p < e; ++p) {
+            slot[p] = tile_of_cell(c, cell[p]);
+            hc[slot[p]]++;
+        }
+    });
+    int first = 0;
+    for (int t = 1; t < T; ++t)
+        if (bad[t] < bad[first]) first = t;
+    if (bad[first] != INT64_MAX) {
+        const int64_t p = bad[first];
+        if (bad_kind[first] == 1) return fail(c, PIC_ERR_ARG, "particle %lld: cell %d outside the grid", (long long)p, cell[p]);
+        if (bad_kind[first] == 2) {
+            for (int a = 0; a < 3; ++a) {
+                const double o = off[3 * p + a];
+                if (activeaxis(c->ndim, a) && !(o >= 0.0 && o < 1.0))
+                    return fail(c, PIC_ERR_ARG, "particle %lld: offset %g outside [0,1)", (long long)p, o);
+            }
+        }
+        return fail(c, PIC_ERR_NAN, "particle %lld: non-finite momentum or weight", (long long)p);
     }
-    for (int t = 0; t < h.ntiles; ++t) seg[t + 1] += seg[t];
+    double wmax = 0.0;
+    for (int t = 0; t < T; ++t) wmax = std::max(wmax, wmaxs[t]);
+    // segment starts, then each range's first slot in each tile
+    for (int t = 0; t < T; ++t)
+        for (int k = 0; k < h.ntiles; ++k) seg[k + 1] += hist[t][k];
+    for (int k = 0; k < h.ntiles; ++k) seg[k + 1] += seg[k];
     {
         std::vector<int> fill(seg.begin(), seg.end() - 1);
-        for (int64_t p = 0; p < n; ++p) slot[p] = fill[slot[p]]++;
+        for (int t = 0; t < T; ++t)
+            for (int k = 0; k < h.ntiles; ++k) {
+                const int m = hist[t][k];
+                hist[t][k] = fill[k];
+                fill[k] += m;
+            }
     }
+    parallel_ranges(n, T, [&](int t, int64_t b, int64_t e) {
+        std::vector<int> &f = hist[t];
+        for (int64_t p = b; p < e; ++p) slot[p] = f[slot[p]]++;
+    });
     pic_status st = ensure_particle_capacity(c, n);
     if (st != PIC_OK) return st;
     if ((st = place_from_host(c, n, cell, off, u, w, id, 0, slot)) != PIC_OK) return st;
