@@ -80,16 +80,18 @@ __global__ void __launch_bounds__(1024) k_scan(Launch L, int mode, int *const *d
 // Read-out of the particles in canonical order: per destination tile, the same source
 // walk as the step, into FP64 / int32 staging arrays at the scanned tile offsets.
 // -------------------------------------------------------------------------------------
+// read-out staging, values in the storage precision R (widened to FP64 on the host)
+template <typename R>
 struct Stage {
     int *cell;
-    double *off;  // 3 per particle
-    double *u;    // 3 per particle
-    double *w;
+    R *off;  // 3 per particle
+    R *u;    // 3 per particle
+    R *w;
     int *id;
 };
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_readout(Launch L, const int *const *start, Stage out)
+__global__ void __launch_bounds__(256) k_readout(Launch L, const int *const *start, Stage<R> out)
 {
     __shared__ SrcTable S;
     const int g = blockIdx.x;
@@ -105,11 +107,11 @@ __global__ void __launch_bounds__(256) k_readout(Launch L, const int *const *sta
         if (pos < 0 || pos >= I.cap) { atomicOr(I.err, kErrInternal); continue; }
         const long long q = dst0 + p;
         out.cell[q] = I.cell[cur][pos];
-        out.off[3 * q + 0] = (double)((const R *)I.off[cur][0])[pos];
-        out.off[3 * q + 1] = I.ndim == 3 ? (double)((const R *)I.off[cur][1])[pos] : 0.0;
-        out.off[3 * q + 2] = (double)((const R *)I.off[cur][2])[pos];
-        for (int a = 0; a < 3; ++a) out.u[3 * q + a] = (double)((const R *)I.u[cur][a])[pos];
-        out.w[q] = (double)((const R *)I.w[cur])[pos];
+        out.off[3 * q + 0] = ((const R *)I.off[cur][0])[pos];
+        out.off[3 * q + 1] = I.ndim == 3 ? ((const R *)I.off[cur][1])[pos] : R(0);
+        out.off[3 * q + 2] = ((const R *)I.off[cur][2])[pos];
+        for (int a = 0; a < 3; ++a) out.u[3 * q + a] = ((const R *)I.u[cur][a])[pos];
+        out.w[q] = ((const R *)I.w[cur])[pos];
         out.id[q] = I.id[cur] ? I.id[cur][pos] : (int)q;
     }
 }
@@ -144,9 +146,10 @@ __global__ void __launch_bounds__(256) k_particle_sums(Launch L, double *sums /*
         const int live = I.chunk_pre[cur][(long long)c * kPre + kDead];
         const int start = s0 + (c - c0) * I.R;
         for (int p = threadIdx.x; p < live; p += blockDim.x) {
-            int cell;
-            R o[3], u[3], w;
-            load_particle(I, cur, start + p, cell, o, u, w);
+            const int pos = start + p;  // momenta and weight only: half the particle's bytes
+            R u[3];
+            for (int a = 0; a < 3; ++a) u[a] = ((const R *)I.u[cur][a])[pos];
+            const R w = ((const R *)I.w[cur])[pos];
             if (sizeof(R) == 8) {
                 const double g2 = 1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
                 ke += (double)w * I.m * (sqrt(g2) - 1.0);
@@ -270,14 +273,16 @@ cudaError_t launch_scan(const Launch &L, int mode, int *const *dst, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, int *cell, double *off, double *u, double *w,
+cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, int *cell, void *off, void *u, void *w,
                            int *id, cudaStream_t s)
 {
-    Stage st{cell, off, u, w, id};
-    if (fp64)
+    if (fp64) {
+        Stage<double> st{cell, (double *)off, (double *)u, (double *)w, id};
         k_readout<double><<<L.total_tiles, 256, 0, s>>>(L, start, st);
-    else
+    } else {
+        Stage<float> st{cell, (float *)off, (float *)u, (float *)w, id};
         k_readout<float><<<L.total_tiles, 256, 0, s>>>(L, start, st);
+    }
     return cudaGetLastError();
 }
 

@@ -648,6 +648,28 @@ static void parallel_ranges(int64_t n, int T, F fn)
     for (auto &x : th) x.join();
 }
 
+// The first n floats of the n-double array d, widened to doubles in place.  The doubles
+// [lo, hi) read floats [lo, hi) and write the bytes of floats [2 lo, 2 hi); with
+// lo = ceil(hi / 2) those lie at or above hi, where every float has been read already,
+// so each such range runs in parallel and the ranges go from the top down.
+static void widen_in_place(double *d, size_t n)
+{
+    const float *f = reinterpret_cast<const float *>(d);
+    size_t hi = n;
+    while (hi > 1) {
+        const size_t lo = (hi + 1) / 2;
+        const int T = host_workers((int64_t)(hi - lo));
+        parallel_ranges((int64_t)(hi - lo), T, [&](int, int64_t b, int64_t e) {
+            for (int64_t j = (int64_t)lo + b; j < (int64_t)lo + e; ++j) d[j] = (double)f[j];
+        });
+        hi = lo;
+    }
+    if (hi == 1) {
+        const float v = f[0];
+        d[0] = (double)v;
+    }
+}
+
 static int tile_of_cell(const pic_ctx *c, int cell)
 {
     const InstDev &h = c->h;
@@ -1453,13 +1475,20 @@ extern "C" pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off
     }
     CUDA_OR_FAIL(ctx, launch_readout(ctx->fp64, ctx->L, ctx->d_start_ptr, ctx->st_cell, ctx->st_off, ctx->st_u, ctx->st_w,
                                      ctx->st_id, ctx->stream));
-    const size_t n = (size_t)live;
+    // values copied in the storage precision (FP32: half the bytes) into the caller's
+    // arrays, then widened there in place
+    const size_t n = (size_t)live, es = ctx->es;
     if (cell) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(cell, ctx->st_cell, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     if (id) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(id, ctx->st_id, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    if (off3) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(off3, ctx->st_off, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    if (u3) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(u3, ctx->st_u, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    if (w) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(w, ctx->st_w, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (off3) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(off3, ctx->st_off, 3 * n * es, cudaMemcpyDeviceToHost, ctx->stream));
+    if (u3) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(u3, ctx->st_u, 3 * n * es, cudaMemcpyDeviceToHost, ctx->stream));
+    if (w) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(w, ctx->st_w, n * es, cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!ctx->fp64) {
+        if (off3) widen_in_place(off3, 3 * n);
+        if (u3) widen_in_place(u3, 3 * n);
+        if (w) widen_in_place(w, n);
+    }
     return check_device_error(ctx);
 }
 

@@ -63,8 +63,9 @@ cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, bool inj
 int particle_chunk();
 int particle_threads();
 cudaError_t launch_scan(const Launch &L, int mode, int *const *dst, cudaStream_t s);
-cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, int *cell, double *off, double *u,
-                           double *w, int *id, cudaStream_t s);
+// off, u, w: staging in the storage precision (double or float)
+cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, int *cell, void *off, void *u,
+                           void *w, int *id, cudaStream_t s);
 cudaError_t launch_particle_sums(int fp64, const Launch &L, double *sums, cudaStream_t s);
 cudaError_t launch_rho(int order, int fp64, const Launch &L, double *rho, cudaStream_t s);
 // passes: the filter passes of every instance of the launch (0 when they differ)
