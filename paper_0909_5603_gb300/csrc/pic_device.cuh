@@ -127,6 +127,7 @@ __device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R disp, 
 // DoubleAcc (FP64 mode): FP64 shared atomics.
 // ------------------------------------------------------------------------------------
 struct FixedAcc {
+    static constexpr bool kSkipZero = false;  // zero adds are cheaper than the branch
     int *H;
     int *L;
     __device__ __forceinline__ void add(int idx, float x) const
@@ -144,6 +145,7 @@ struct FixedAcc {
 };
 
 struct DoubleAcc {
+    static constexpr bool kSkipZero = true;
     double *J;
     __device__ __forceinline__ void add(int idx, double x) const { atomicAdd(J + idx, x); }
 };
@@ -185,7 +187,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
                 for (int i = 0; i < W - 1; ++i) {
                     run += DSx[i];
                     const R v = fY * run;
-                    if (v != R(0)) acc.add(base + i + jd0 * j + jd01 * k, v);
+                    if (!Acc::kSkipZero || v != R(0)) acc.add(base + i + jd0 * j + jd01 * k, v);
                 }
             }
         }
@@ -200,7 +202,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
                 for (int j = 0; j < W - 1; ++j) {
                     run += DSy[j];
                     const R v = fX * run;
-                    if (v != R(0)) acc.add(jvol + base + i + jd0 * j + jd01 * k, v);
+                    if (!Acc::kSkipZero || v != R(0)) acc.add(jvol + base + i + jd0 * j + jd01 * k, v);
                 }
             }
         }
@@ -215,7 +217,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
                 for (int k = 0; k < W - 1; ++k) {
                     run += DSz[k];
                     const R v = fX * run;
-                    if (v != R(0)) acc.add(2 * jvol + base + i + jd0 * j + jd01 * k, v);
+                    if (!Acc::kSkipZero || v != R(0)) acc.add(2 * jvol + base + i + jd0 * j + jd01 * k, v);
                 }
             }
         }
@@ -230,7 +232,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
             for (int i = 0; i < W - 1; ++i) {
                 run += DSx[i];
                 const R v = fY * run;
-                if (v != R(0)) acc.add(base + i + jd01 * k, v);
+                if (!Acc::kSkipZero || v != R(0)) acc.add(base + i + jd01 * k, v);
             }
         }
 #pragma unroll
@@ -241,7 +243,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
             for (int k = 0; k < W - 1; ++k) {
                 run += DSz[k];
                 const R v = fX * run;
-                if (v != R(0)) acc.add(2 * jvol + base + i + jd01 * k, v);
+                if (!Acc::kSkipZero || v != R(0)) acc.add(2 * jvol + base + i + jd01 * k, v);
             }
         }
 #pragma unroll
@@ -249,7 +251,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
 #pragma unroll
             for (int i = 0; i < W; ++i) {
                 const R v = fy * (S0x[i] * S0z[k] + half * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) + third * DSx[i] * DSz[k]);
-                if (v != R(0)) acc.add(jvol + base + i + jd01 * k, v);
+                if (!Acc::kSkipZero || v != R(0)) acc.add(jvol + base + i + jd01 * k, v);
             }
         }
     }
