@@ -176,11 +176,22 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
     if (ND == 3) {
         const int wsy = shape_window<ORD, kDisp>(l0[1], o0[1], l1[1], o1[1], disp[1], S0y, DSy, nwy) - jlo_y;
         const int base = wsx + jd0 * wsy + jd01 * wsz;
+        // the transverse factor S0a S0b + DSa S0b / 2 + S0a DSb / 2 + DSa DSb / 3 as
+        // S0a (S0b + DSb / 2) + DSa (S0b / 2 + DSb / 3): per axis b two vectors, then two
+        // operations per window row
+        R Ay[W], Cy[W], Az[W], Cz[W];
+#pragma unroll
+        for (int m = 0; m < W; ++m) {
+            Ay[m] = S0y[m] + half * DSy[m];
+            Cy[m] = half * S0y[m] + third * DSy[m];
+            Az[m] = S0z[m] + half * DSz[m];
+            Cz[m] = half * S0z[m] + third * DSz[m];
+        }
 #pragma unroll
         for (int k = 0; k < W; ++k) {
 #pragma unroll
             for (int j = 0; j < W; ++j) {
-                const R Y = S0y[j] * S0z[k] + half * (DSy[j] * S0z[k] + S0y[j] * DSz[k]) + third * DSy[j] * DSz[k];
+                const R Y = S0y[j] * Az[k] + DSy[j] * Cz[k];
                 const R fY = fx * Y;
                 R run = R(0);
 #pragma unroll
@@ -195,7 +206,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
         for (int k = 0; k < W; ++k) {
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                const R X = S0x[i] * S0z[k] + half * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) + third * DSx[i] * DSz[k];
+                const R X = S0x[i] * Az[k] + DSx[i] * Cz[k];
                 const R fX = fy * X;
                 R run = R(0);
 #pragma unroll
@@ -210,7 +221,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
         for (int j = 0; j < W; ++j) {
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                const R X = S0x[i] * S0y[j] + half * (DSx[i] * S0y[j] + S0x[i] * DSy[j]) + third * DSx[i] * DSy[j];
+                const R X = S0x[i] * Ay[j] + DSx[i] * Cy[j];
                 const R fX = fz * X;
                 R run = R(0);
 #pragma unroll
