@@ -127,7 +127,9 @@ __device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R disp, 
 // DoubleAcc (FP64 mode): FP64 shared atomics.
 // ------------------------------------------------------------------------------------
 struct FixedAcc {
-    static constexpr bool kSkipZero = false;  // zero adds are cheaper than the branch
+    // 3D: zero adds are cheaper than the branch; the 2D3V loops (up to 16 particles per
+    // cell in a small window) keep skipping them, where the adds would contend
+    static constexpr bool kSkipZero = false;
     int *H;
     int *L;
     __device__ __forceinline__ void add(int idx, float x) const
@@ -243,7 +245,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
             for (int i = 0; i < W - 1; ++i) {
                 run += DSx[i];
                 const R v = fY * run;
-                if (!Acc::kSkipZero || v != R(0)) acc.add(base + i + jd01 * k, v);
+                if (v != R(0)) acc.add(base + i + jd01 * k, v);
             }
         }
 #pragma unroll
@@ -254,7 +256,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
             for (int k = 0; k < W - 1; ++k) {
                 run += DSz[k];
                 const R v = fX * run;
-                if (!Acc::kSkipZero || v != R(0)) acc.add(2 * jvol + base + i + jd01 * k, v);
+                if (v != R(0)) acc.add(2 * jvol + base + i + jd01 * k, v);
             }
         }
 #pragma unroll
@@ -262,7 +264,7 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
 #pragma unroll
             for (int i = 0; i < W; ++i) {
                 const R v = fy * (S0x[i] * S0z[k] + half * (DSx[i] * S0z[k] + S0x[i] * DSz[k]) + third * DSx[i] * DSz[k]);
-                if (!Acc::kSkipZero || v != R(0)) acc.add(jvol + base + i + jd01 * k, v);
+                if (v != R(0)) acc.add(jvol + base + i + jd01 * k, v);
             }
         }
     }
