@@ -162,7 +162,9 @@ struct DoubleAcc {
 // Wz = DSz (S0x + DSx/2) and the out-of-plane Jy = f_y' (S0x S0z + DSx S0z / 2 +
 // S0x DSz / 2 + DSx DSz / 3) with f_y' = (q w / dV) v_y.  The loops run over the whole
 // window: entries beyond the nodes a particle touches are exactly zero (the running sum
-// ends at exactly zero too) and are skipped by the accumulator's zero test.
+// ends at exactly zero too).  The FP64 accumulator and the 2D3V loops skip zero entries;
+// the 3D FP32 fixed-point accumulator adds them (cheaper than the branch; the window lies
+// inside the J tile).
 // ------------------------------------------------------------------------------------
 template <int ND, int ORD, bool kDisp, typename R, typename Acc>
 __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3], const int l1[3], const R o1[3],
