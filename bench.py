@@ -61,16 +61,38 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(particles):
-    """DRAM bytes per launch scaled from the capture, or None when the kernel changed."""
+def profiled_value(key):
+    """A per-particle figure of the particle kernel's ncu capture, or None when the capture
+    is absent or the kernel sources changed since it was taken."""
     try:
         with open(PROFILE) as f:
-            kv = dict(line.split(":", 1) for line in f if line.startswith(("dram_bytes_per_particle", "kernel_source_sha256")))
-    except (OSError, ValueError):
+            kv = dict(line.split(":", 1) for line in f if line.startswith((key, "kernel_source_sha256")))
+        if kv.get("kernel_source_sha256", "").strip() != kernel_source_hash():
+            return None
+        return float(kv[key])
+    except (OSError, ValueError, KeyError):
         return None
-    if kv.get("kernel_source_sha256", "").strip() != kernel_source_hash():
+
+
+def profiled_traffic(particles):
+    """DRAM bytes per launch scaled from the capture, or None when the kernel changed."""
+    per = profiled_value("dram_bytes_per_particle")
+    return None if per is None else per * particles
+
+
+def issue_roofline(kern_ms, particles, clocks):
+    """The bound that applies to the particle kernel, instruction issue: warp instructions
+    per launch (the capture's count per particle times the particles) over the measured
+    launch time, against 4 warp instructions per SM-cycle on 152 SMs at the sampled SM
+    clock (2070 MHz when no sample).  None when the capture is stale or absent."""
+    per = profiled_value("warp_instructions_per_particle")
+    if per is None or not kern_ms or kern_ms <= 0:
         return None
-    return float(kv["dram_bytes_per_particle"]) * particles
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    achieved = per * particles / (kern_ms * 1e-3) / 1e9
+    peak = 152 * 4 * mhz * 1e-3
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "G warp-instructions/s",
+            "frac": achieved / peak, "warp_instructions_per_particle": per, "sm_mhz": mhz}
 
 
 def measured_peaks():
@@ -314,6 +336,7 @@ def run_ours(args, rank, world):
             "phase_ms_per_step": {k: tm[k] / max(tm["steps"], 1) for k in
                                   ("ms_particles", "ms_scan", "ms_filter", "ms_maxwell", "ms_other")},
             "clocks": clk.summary()}
+    line["issue_roofline"] = issue_roofline(kern_ms, 0.5 * (nb + na), line["clocks"])
     print(json.dumps(line), flush=True)
 
 
