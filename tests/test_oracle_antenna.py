@@ -25,12 +25,13 @@ def beta(g):
 
 
 def empty(n, dx, dt):
-    s = oracle.Sim(2, n, (0, 0, 1), dx, dt, tile=(8, 1, 16))
+    ndim = 3 if n[1] > 1 else 2
+    s = oracle.Sim(ndim, n, (0, 0, 1), dx, dt, tile=(8, 8, 16) if ndim == 3 else (8, 1, 16))
     s.set_particles(np.zeros(0, np.int32), np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0))
     return s
 
 
-def plane_wave_case(gb, dt_frac, steps=450, waist=1e9):
+def plane_wave_case(gb, dt_frac, steps=450, waist=1e9, ny=1):
     """A box of 24 boosted wavelengths (D = gamma_b (1 + beta_b) lab wavelengths) at 32
     cells each; the free pulse (1/e length 1.5 wavelengths) starts centred 7.6 boosted
     wavelengths into the box, the plane at 14: z_center = 7.6 and z_lab = 14 gamma_b D in
@@ -38,7 +39,7 @@ def plane_wave_case(gb, dt_frac, steps=450, waist=1e9):
     D = gb * (1 + beta(gb))
     dz = D / 32
     dt = dt_frac * dz
-    n = (8, 1, 768)
+    n = (8, ny, 768)
     laser = [0.5, 1.0, waist, 1.5, 7.6]
     z_lab = 14 * gb * D
     a = empty(n, (1.0, 1.0, dz), dt)
@@ -68,6 +69,21 @@ def test_plane_wave_crosses_the_moving_plane_without_reflection(gb, dt_frac):
         assert np.abs(fa[ahead] - ff[ahead]).max() < 1e-10 * amp, c
         # the crossing is under way or done: most of the pulse is ahead of the plane
         assert np.abs(ff[ahead]).max() > 0.9 * amp
+    for c in (EY, EZ, BX, BZ):
+        assert np.abs(a.get_field(c)).max() < 1e-10 * amp
+
+
+def test_plane_wave_without_reflection_3d():
+    """The same in 3D (periodic x and y): the moving boundary treats every transverse
+    column alike."""
+    a, f, zp, n = plane_wave_case(4.0, 0.5, steps=300, ny=8)
+    amp = np.abs(f.get_field(EX)).max()
+    k = np.arange(n[2])
+    for c in (EX, BY):
+        fa, ff = a.get_field(c), f.get_field(c)
+        pos = k + (0.5 if c == BY else 0.0)
+        assert np.abs(fa[pos <= zp]).max() < 1e-12 * amp, c
+        assert np.abs(fa[pos > zp] - ff[pos > zp]).max() < 1e-10 * amp, c
     for c in (EY, EZ, BX, BZ):
         assert np.abs(a.get_field(c)).max() < 1e-10 * amp
 
