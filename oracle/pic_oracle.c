@@ -855,11 +855,14 @@ void orc_set_solver(orc_sim *s, int solver) { s->solver = solver; }
  * advances them) and a scattered-field region (at or below it), which holds the field
  * minus the incident pulse.  The incident field is T times g propagated on a 1D lattice aligned
  * with the grid's z lattice by the same leapfrog (so a plane wave crosses the boundary
- * without any reflection), started from samples of g.  Each z difference that joins a
- * value of one region to a value of the other takes the far value in the near one's
- * representation: the incident value there is added (forward difference of E_x in the
- * B update) or subtracted, which adds h T g_E / dz to B_y and dt T g_B / dz to E_x in
- * both cases.  At the end of each Maxwell phase the values the receding plane has passed
+ * without any reflection), started from samples of g.  Every difference stencil reads
+ * its neighbours in its own node's representation: a node in the total-field region adds
+ * the incident value of neighbours in the scattered-field region, and the other way
+ * round it is subtracted -- the update's own curl evaluated on the incident pulse of the
+ * other region.  Under the Yee scheme that is h T g_E / dz added to B_y in each B half
+ * update and dt T g_B / dz to E_x in the E update; the low-dispersion solver's averaged
+ * differences also reach across the plane from the B_z nodes (through dE_x/dy on the
+ * neighbouring z rows) and spread the B_y term over the neighbouring columns.  At the end of each Maxwell phase the values the receding plane has passed
  * (between its positions at t^n and t^{n+1}) enter the total-field region: their incident
  * value at t^{n+1} is added.  Setting the antenna adds the incident field to the
  * total-field region.
@@ -960,37 +963,89 @@ void orc_set_antenna(orc_sim *s, int enable, double gb, const double *laser, dou
     ant_add_incident(s, zp0, INFINITY);
 }
 
-/* The incident term to add to B_y at (i, j, k + 1/2) in a B half update (times h), and
- * to E_x at (i, j, k) in the E update (times dt), for the plane at zp (cells). */
-static double ant_b_term(const orc_sim *s, int i, int j, int k, double zp)
+/* Two shallow copies of s whose fields are the incident pulse on one side of the plane
+ * at zp (cells) and zero elsewhere: v[1] holds it where the node lies above the plane,
+ * v[0] where it lies at or below it.  Only E_x (nodes k) and B_y (half nodes k + 1/2)
+ * of the incident pulse are nonzero.  The solver's own difference functions read them
+ * like the real fields.  Release with ant_views_free. */
+static void ant_views(const orc_sim *s, double zp, orc_sim v[2])
 {
-    if (!s->ant) return 0.0;
-    double g;
-    if (k <= zp && zp < k + 0.5) { /* B_y total field, E_x at k scattered */
-        g = ant_ge(s, k);
-    } else if (k + 0.5 <= zp && zp < k + 1) { /* B_y scattered, E_x at k + 1 total */
-        if (k + 1 >= s->n[2]) return 0.0;
-        g = ant_ge(s, k + 1);
-    } else {
-        return 0.0;
+    size_t nc = (size_t)s->ncell;
+    double *zero = (double *)calloc(nc, sizeof(double));
+    for (int side = 0; side < 2; ++side) {
+        v[side] = *s;
+        for (int c = 0; c < ORC_NCOMP; ++c) v[side].f[c] = zero;
+        v[side].f[ORC_EX] = (double *)calloc(nc, sizeof(double));
+        v[side].f[ORC_BY] = (double *)calloc(nc, sizeof(double));
     }
-    return ant_profile(s, (i + 0.5) * s->dx[0], j * s->dx[1]) * g / s->dx[2];
+    for (int k = 0; k < s->n[2]; ++k)
+        for (int j = 0; j < s->n[1]; ++j)
+            for (int i = 0; i < s->n[0]; ++i) {
+                int64_t id = node_index(s, i, j, k);
+                double T = ant_profile(s, (i + 0.5) * s->dx[0], j * s->dx[1]); /* E_x and B_y share x, y */
+                v[k + STAG[ORC_EX][2] > zp].f[ORC_EX][id] = T * ant_ge(s, k);
+                v[k + STAG[ORC_BY][2] > zp].f[ORC_BY][id] = T * ant_gb(s, k);
+            }
 }
 
-static double ant_e_term(const orc_sim *s, int i, int j, int k, double zp)
+static void ant_views_free(orc_sim v[2])
 {
-    if (!s->ant) return 0.0;
-    double g;
-    if (k - 0.5 <= zp && zp < k) { /* E_x total field, B_y at k - 1/2 scattered */
-        if (k - 1 < 0) return 0.0;
-        g = ant_gb(s, k - 1);
-    } else if (k <= zp && zp < k + 0.5) { /* E_x scattered, B_y at k + 1/2 total */
-        g = ant_gb(s, k);
-    } else {
-        return 0.0;
+    free(v[0].f[ORC_EY]); /* the shared zero array */
+    for (int side = 0; side < 2; ++side) {
+        free(v[side].f[ORC_EX]);
+        free(v[side].f[ORC_BY]);
     }
-    return ant_profile(s, (i + 0.5) * s->dx[0], j * s->dx[1]) * g / s->dx[2];
 }
+
+/* The incident part of the curl a node of component comp (height k + its z staggering,
+ * in cells) must add so that its difference stencil reads every neighbour in the node's
+ * own representation: a node above the plane (total field) adds the incident pulse of
+ * the neighbours at or below it, a node at or below (scattered field) subtracts that of
+ * the neighbours above.  curl is the update's own curl component evaluated on a view
+ * (which holds the incident pulse of one side only). */
+static double ant_term(const orc_sim v[2], int comp, int k, double zp,
+                       double (*curl)(const orc_sim *, int, int, int), int i, int j)
+{
+    int above = k + STAG[comp][2] > zp;
+    double c = curl(&v[!above], i, j, k);
+    return above ? c : -c;
+}
+
+/* The components of curl E at the B nodes (forward differences, averaged under the
+ * low-dispersion solver) and of curl B at the E nodes (backward differences). */
+typedef double (*diff_fn)(const orc_sim *, int, int, int, int, int);
+static diff_fn faraday_diff(const orc_sim *s) { return s->solver == ORC_SOLVER_CK ? dfwd_ck : dfwd; }
+static double curl_e_x(const orc_sim *s, int i, int j, int k)
+{
+    diff_fn d = faraday_diff(s);
+    return d(s, ORC_EZ, 1, i, j, k) - d(s, ORC_EY, 2, i, j, k);
+}
+static double curl_e_y(const orc_sim *s, int i, int j, int k)
+{
+    diff_fn d = faraday_diff(s);
+    return d(s, ORC_EX, 2, i, j, k) - d(s, ORC_EZ, 0, i, j, k);
+}
+static double curl_e_z(const orc_sim *s, int i, int j, int k)
+{
+    diff_fn d = faraday_diff(s);
+    return d(s, ORC_EY, 0, i, j, k) - d(s, ORC_EX, 1, i, j, k);
+}
+static double curl_b_x(const orc_sim *s, int i, int j, int k)
+{
+    return dbwd(s, ORC_BZ, 1, i, j, k) - dbwd(s, ORC_BY, 2, i, j, k);
+}
+static double curl_b_y(const orc_sim *s, int i, int j, int k)
+{
+    return dbwd(s, ORC_BX, 2, i, j, k) - dbwd(s, ORC_BZ, 0, i, j, k);
+}
+static double curl_b_z(const orc_sim *s, int i, int j, int k)
+{
+    return dbwd(s, ORC_BY, 0, i, j, k) - dbwd(s, ORC_BX, 1, i, j, k);
+}
+
+/* nodes whose stencils can reach across the plane at zp (one cell each way, plus the
+ * staggering) */
+static int near_plane(int k, double zp) { return k >= zp - 3.0 && k <= zp + 3.0; }
 
 /* B <- B - h curl E (h = dt / 2), optionally damped afterwards. */
 static void half_b(orc_sim *s, int damp)
@@ -999,21 +1054,31 @@ static void half_b(orc_sim *s, int damp)
     double *nb[3];
     for (int c = 0; c < 3; ++c) nb[c] = (double *)malloc((size_t)nc * sizeof(double));
     double h = 0.5 * s->dt;
+    orc_sim av[2];
+    double zp = 0.0;
+    if (s->ant) {
+        zp = ant_plane(s, s->ant_n);
+        ant_views(s, zp, av);
+    }
     for (int k = 0; k < s->n[2]; ++k)
         for (int j = 0; j < s->n[1]; ++j)
             for (int i = 0; i < s->n[0]; ++i) {
                 int64_t id = node_index(s, i, j, k);
-                double (*d)(const orc_sim *, int, int, int, int, int) = s->solver == ORC_SOLVER_CK ? dfwd_ck : dfwd;
-                double cx = d(s, ORC_EZ, 1, i, j, k) - d(s, ORC_EY, 2, i, j, k);
-                double cy = d(s, ORC_EX, 2, i, j, k) - d(s, ORC_EZ, 0, i, j, k);
-                double cz = d(s, ORC_EY, 0, i, j, k) - d(s, ORC_EX, 1, i, j, k);
-                if (s->ant) cy -= ant_b_term(s, i, j, k, ant_plane(s, s->ant_n));
+                double cx = curl_e_x(s, i, j, k);
+                double cy = curl_e_y(s, i, j, k);
+                double cz = curl_e_z(s, i, j, k);
+                if (s->ant && near_plane(k, zp)) {
+                    cx += ant_term(av, ORC_BX, k, zp, curl_e_x, i, j);
+                    cy += ant_term(av, ORC_BY, k, zp, curl_e_y, i, j);
+                    cz += ant_term(av, ORC_BZ, k, zp, curl_e_z, i, j);
+                }
                 int c[3] = {i, j, k};
                 double f = damp ? damp_factor(s, c) : 1.0;
                 nb[0][id] = f * (s->f[ORC_BX][id] - h * cx);
                 nb[1][id] = f * (s->f[ORC_BY][id] - h * cy);
                 nb[2][id] = f * (s->f[ORC_BZ][id] - h * cz);
             }
+    if (s->ant) ant_views_free(av);
     for (int c = 0; c < 3; ++c) {
         memcpy(s->f[ORC_BX + c], nb[c], (size_t)nc * sizeof(double));
         free(nb[c]);
@@ -1027,20 +1092,31 @@ static void full_e(orc_sim *s)
     double *ne[3];
     for (int c = 0; c < 3; ++c) ne[c] = (double *)malloc((size_t)nc * sizeof(double));
     double dt = s->dt;
+    orc_sim av[2];
+    double zp = 0.0;
+    if (s->ant) {
+        zp = ant_plane(s, s->ant_n);
+        ant_views(s, zp, av);
+    }
     for (int k = 0; k < s->n[2]; ++k)
         for (int j = 0; j < s->n[1]; ++j)
             for (int i = 0; i < s->n[0]; ++i) {
                 int64_t id = node_index(s, i, j, k);
-                double cx = dbwd(s, ORC_BZ, 1, i, j, k) - dbwd(s, ORC_BY, 2, i, j, k);
-                double cy = dbwd(s, ORC_BX, 2, i, j, k) - dbwd(s, ORC_BZ, 0, i, j, k);
-                double cz = dbwd(s, ORC_BY, 0, i, j, k) - dbwd(s, ORC_BX, 1, i, j, k);
-                if (s->ant) cx += ant_e_term(s, i, j, k, ant_plane(s, s->ant_n));
+                double cx = curl_b_x(s, i, j, k);
+                double cy = curl_b_y(s, i, j, k);
+                double cz = curl_b_z(s, i, j, k);
+                if (s->ant && near_plane(k, zp)) {
+                    cx += ant_term(av, ORC_EX, k, zp, curl_b_x, i, j);
+                    cy += ant_term(av, ORC_EY, k, zp, curl_b_y, i, j);
+                    cz += ant_term(av, ORC_EZ, k, zp, curl_b_z, i, j);
+                }
                 int c[3] = {i, j, k};
                 double f = damp_factor(s, c);
                 ne[0][id] = f * (s->f[ORC_EX][id] + dt * (cx - s->f[ORC_JX][id]));
                 ne[1][id] = f * (s->f[ORC_EY][id] + dt * (cy - s->f[ORC_JY][id]));
                 ne[2][id] = f * (s->f[ORC_EZ][id] + dt * (cz - s->f[ORC_JZ][id]));
             }
+    if (s->ant) ant_views_free(av);
     for (int c = 0; c < 3; ++c) {
         memcpy(s->f[ORC_EX + c], ne[c], (size_t)nc * sizeof(double));
         free(ne[c]);
