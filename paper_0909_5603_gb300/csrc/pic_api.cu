@@ -427,8 +427,9 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     // 32-bit fixed-point halves in FP32 mode) + alignment slack
     c->smem = 128 + 6 * boxb + 3 * (size_t)h.jdim[0] * h.jdim[1] * h.jdim[2] * 8;
     if (c->smem > 200 * 1024) {
+        const size_t smem = c->smem;
         delete c;
-        return fail(nullptr, PIC_ERR_ARG, "tile too large: %zu bytes of shared memory per CTA", c->smem);
+        return fail(nullptr, PIC_ERR_ARG, "tile too large: %zu bytes of shared memory per CTA", smem);
     }
     c->ncell = (long long)c->n[0] * c->n[1] * c->n[2];
     {

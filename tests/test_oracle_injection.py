@@ -27,7 +27,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import EX, EY, EZ, BX, BY, BZ
+from oracle import EX, EZ, BY
 
 
 def beta(g):
