@@ -375,11 +375,13 @@ void orc_sort(orc_sim *s)
             u[3 * d + a] = s->u[3 * p + a];
         }
     }
-    memcpy(s->cell, cell, (size_t)s->np * sizeof(int32_t));
-    memcpy(s->id, id, (size_t)s->np * sizeof(int32_t));
-    memcpy(s->off, off, (size_t)s->np * 3 * sizeof(double));
-    memcpy(s->u, u, (size_t)s->np * 3 * sizeof(double));
-    memcpy(s->w, w, (size_t)s->np * sizeof(double));
+    if (s->np > 0) { /* an empty set may have no arrays yet */
+        memcpy(s->cell, cell, (size_t)s->np * sizeof(int32_t));
+        memcpy(s->id, id, (size_t)s->np * sizeof(int32_t));
+        memcpy(s->off, off, (size_t)s->np * 3 * sizeof(double));
+        memcpy(s->u, u, (size_t)s->np * 3 * sizeof(double));
+        memcpy(s->w, w, (size_t)s->np * sizeof(double));
+    }
     free(cell);
     free(id);
     free(off);
