@@ -52,7 +52,7 @@ typedef struct pic_ctx pic_ctx;
 typedef enum {
     PIC_OK = 0,
     PIC_ERR_ARG = 1,            /* invalid argument, size or pointer */
-    PIC_ERR_CFL = 2,            /* dt above the Yee Courant limit */
+    PIC_ERR_CFL = 2,            /* dt above the field solver's Courant limit */
     PIC_ERR_CUDA = 3,           /* a CUDA runtime or driver call failed */
     PIC_ERR_OOM = 4,            /* the allocator returned no memory */
     PIC_ERR_STATE = 5,          /* call not valid in this state (e.g. step before load) */
@@ -144,7 +144,8 @@ void pic_default_options(pic_options *o);
 
 /* Creates a simulation instance on a boosted-frame grid.
  *  grid: dimensions and boundaries; dx: cell sizes (> 0); dt: time step, at most the
- *  Yee Courant limit 1 / sqrt(sum_a 1/dx_a^2) over the active axes (else PIC_ERR_CFL);
+ *  field solver's Courant limit over the active axes, 1 / sqrt(sum_a 1/dx_a^2) for Yee,
+ *  min_a dx_a for PIC_SOLVER_CK (else PIC_ERR_CFL);
  *  gamma_boost >= 1: Lorentz factor of the boosted frame relative to the lab (Sec. 2),
  *  used by pic_load_lab_frame; shape_order: 1 (linear) or 2 (quadratic) particle shape
  *  for gather and deposit; opt: NULL for defaults.  Periodic axes need at least 3 tiles
