@@ -178,6 +178,40 @@ def test_filter_binomial_impulse_absorbing():
     assert np.abs(out - expect).max() < 1e-15
 
 
+@pytest.mark.parametrize("bcx", [0, 1])
+def test_filter_passes_at_the_faces(bcx):
+    """Each pass is the 1-2-1 matrix of the axis: tridiagonal with nothing beyond an
+    absorbing face (what leaves does not come back in the next pass), circulant on a
+    periodic axis.  Random currents next to the faces after three passes equal the cube of
+    that matrix applied along x and along z (the axes commute), to round-off."""
+    passes = 3
+    nx, nz = 12, 10
+    s = make(2, (nx, 1, nz), bc=(bcx, 0, 1), filter_passes=passes)
+    rng = np.random.default_rng(11)
+    J = np.zeros((nz, 1, nx))
+    J[:, 0, :2] = rng.normal(size=(nz, 2))
+    J[:, 0, -2:] = rng.normal(size=(nz, 2))
+    J[:2, 0, :] += rng.normal(size=(2, nx))
+    s.set_field(JY, J)
+    s.filter()
+
+    def matrix(n, periodic):
+        A = 0.5 * np.eye(n) + 0.25 * np.eye(n, k=1) + 0.25 * np.eye(n, k=-1)
+        if periodic:
+            A[0, -1] = A[-1, 0] = 0.25
+        return A
+
+    Ax = np.linalg.matrix_power(matrix(nx, bcx == 0), passes)
+    Az = np.linalg.matrix_power(matrix(nz, False), passes)
+    expect = Az @ J[:, 0, :] @ Ax.T
+    assert np.abs(s.get_field(JY)[:, 0, :] - expect).max() < 1e-14
+    # a plausible mistake, the (2N+1)-tap binomial applied once and cut at the faces,
+    # differs near an absorbing face (what left in one pass would come back in the next)
+    row = np.array([math.comb(2 * passes, j) for j in range(2 * passes + 1)]) / 4.0 ** passes
+    once = sum(row[m + passes] * np.eye(nz, k=m) for m in range(-passes, passes + 1))
+    assert np.abs(once - Az).max() > 1e-2
+
+
 def _yee_mode(ndim, pol, n, dx, dt, m, steps):
     s = make(ndim, n, dx=dx, dt=dt)
     axes = [a for a in range(3) if a != pol and (ndim == 3 or a != 1)]
