@@ -74,3 +74,36 @@ def test_null_handles(L):
     L.pic_destroy(None)
     out = ctypes.c_void_p()
     assert L.pic_batch_create(0, None, ctypes.byref(out)) == pic.PIC_ERR_ARG
+
+
+def test_courant_limit_follows_the_solver(L):
+    """Yee: 1/sqrt(3) on a unit cube; the low-dispersion solver: min dx = 1.  dt = 0.9 is
+    refused under Yee and passes the check under the other solver (without a device the
+    call then stops at the allocation; with one it creates a context, destroyed here)."""
+    assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.9)[0] == pic.PIC_ERR_CFL
+    o = pic.pic_default_options()
+    o.solver = pic.PIC_SOLVER_CK
+    st, h = _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.9, opt=o)
+    if h.value:
+        L.pic_destroy(h)
+    assert st != pic.PIC_ERR_CFL
+    assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 1.1, opt=o)[0] == pic.PIC_ERR_CFL
+
+
+def test_binding_constants_match_the_header():
+    """Every enumerator of include/pic.h has the same value in the Python binding."""
+    src = open(os.path.join(ROOT, "include", "pic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    found = 0
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        value = -1
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            name, _, expr = item.partition("=")
+            name = name.strip()
+            value = int(expr.strip()) if expr.strip() else value + 1
+            assert getattr(pic, name) == value, name
+            found += 1
+    assert found >= 30
