@@ -69,11 +69,32 @@ def test_argument_validation_before_any_device_call(L):
 
 
 def test_null_handles(L):
+    """Every call on a NULL handle answers PIC_ERR_ARG (pic_destroy: a no-op)."""
     assert L.pic_step(None, 1) == pic.PIC_ERR_ARG
     assert L.pic_synchronize(None) == pic.PIC_ERR_ARG
     L.pic_destroy(None)
     out = ctypes.c_void_p()
     assert L.pic_batch_create(0, None, ctypes.byref(out)) == pic.PIC_ERR_ARG
+    N, z = None, ctypes.c_double(0.0)
+    for call in (lambda: L.pic_load_particles(N, 0, N, N, N, N, N),
+                 lambda: L.pic_set_laser_antenna(N, N, z),
+                 lambda: L.pic_set_injection(N, 0, z, 0),
+                 lambda: L.pic_set_field(N, 0, N, 0),
+                 lambda: L.pic_load_lab_frame(N, N, N, N),
+                 lambda: L.pic_run_phases(N, pic.PIC_PHASE_ALL),
+                 lambda: L.pic_get_field(N, 0, N, 0),
+                 lambda: L.pic_get_fields(N, N, 0, N, 0),
+                 lambda: L.pic_get_gauss_residual(N, N, N),
+                 lambda: L.pic_num_particles(N, N),
+                 lambda: L.pic_get_particles(N, N, N, N, N, N, 0, N),
+                 lambda: L.pic_get_diagnostics(N, N),
+                 lambda: L.pic_set_profiling(N, 0, 0),
+                 lambda: L.pic_get_timings(N, N),
+                 lambda: L.pic_set_stations(N, 0, N, 0),
+                 lambda: L.pic_get_station(N, 0, N, N, 0, N, 0),
+                 lambda: L.pic_get_rho_noalloc(N, N, 0),
+                 lambda: L.pic_autotune(N, N, ctypes.c_double(0.1), ctypes.c_double(1.0), 1, N, N, N, N, 1, N, N)):
+        assert call() == pic.PIC_ERR_ARG
 
 
 def test_courant_limit_follows_the_solver(L):
