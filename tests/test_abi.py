@@ -66,6 +66,20 @@ def test_argument_validation_before_any_device_call(L):
     o = pic.pic_default_options()
     o.precision = 7
     assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.5, opt=o)[0] == pic.PIC_ERR_ARG
+    for field, value in (("filter_passes", 9), ("filter_passes", -1), ("absorb_cells", -1),
+                         ("absorb_strength", 2.0), ("absorb_strength", -0.1), ("mass", 0.0),
+                         ("charge", float("nan")), ("solver", 5), ("pusher", 3)):
+        o = pic.pic_default_options()
+        setattr(o, field, value)
+        assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.5, opt=o)[0] == pic.PIC_ERR_ARG, field
+    o = pic.pic_default_options()
+    o.tile[1] = 128
+    assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), 0.5, opt=o)[0] == pic.PIC_ERR_ARG
+    assert _create(3, (16, 16, 16), (0, 0, 0), (1, float("nan"), 1), 0.5)[0] == pic.PIC_ERR_ARG
+    assert _create(3, (16, 16, 16), (0, 2, 0), (1, 1, 1), 0.5)[0] == pic.PIC_ERR_ARG
+    assert _create(3, (16, 7, 16), (0, 0, 0), (1, 1, 1), 0.5)[0] == pic.PIC_ERR_ARG
+    for dt in (0.0, float("inf"), float("nan")):
+        assert _create(3, (16, 16, 16), (0, 0, 0), (1, 1, 1), dt)[0] == pic.PIC_ERR_ARG
 
 
 def test_null_handles(L):
