@@ -89,6 +89,10 @@ def test_null_handles(L):
     L.pic_destroy(None)
     out = ctypes.c_void_p()
     assert L.pic_batch_create(0, None, ctypes.byref(out)) == pic.PIC_ERR_ARG
+    members = (ctypes.c_void_p * 2)(None, None)
+    assert L.pic_batch_create(2, members, ctypes.byref(out)) == pic.PIC_ERR_ARG
+    assert L.pic_batch_create(-1, members, ctypes.byref(out)) == pic.PIC_ERR_ARG
+    assert L.pic_batch_create(2, members, None) == pic.PIC_ERR_ARG
     N, z = None, ctypes.c_double(0.0)
     for call in (lambda: L.pic_load_particles(N, 0, N, N, N, N, N),
                  lambda: L.pic_set_laser_antenna(N, N, z),
