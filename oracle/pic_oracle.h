@@ -89,8 +89,10 @@ int64_t orc_num_frozen(const orc_sim *s);
 /* Laser antenna on the lab plane z = z_lab (in this frame z' = z_lab / gamma_b - beta_b t'):
  * laser[5] as for orc_load_lab_frame; the lab pulse is emitted forward by the plane
  * (total-field / scattered-field split at the plane, incident field propagated on a 1D
- * lattice by the same leapfrog).  Adds the incident field downstream of the plane now;
- * enable = 0 (or laser NULL) removes it.  A load removes it. */
+ * lattice by the same leapfrog).  Under either field solver: every difference that
+ * straddles the plane reads the far value in the near node's representation.  Adds the
+ * incident field downstream of the plane now; enable = 0 (or laser NULL) removes it.  A
+ * load removes it. */
 void orc_set_antenna(orc_sim *s, int enable, double gamma_b, const double *laser, double z_lab);
 /* Test helper: rounds offsets (kept below 1), momenta, weights, E and B to FP32. */
 void orc_round_state_fp32(orc_sim *s);
