@@ -311,10 +311,12 @@ pic_status pic_get_station(pic_ctx *ctx, int station, int *n_records, double *t_
  * lattice and advanced by the same leapfrog, so a plane wave crosses the moving boundary
  * without reflection.  Each Maxwell phase adds the incident term to the B_y and E_x
  * differences that straddle the plane (7 small launches) and moves the values the
- * receding plane passed into the total field.  The call adds the incident field
- * downstream of the plane now.  Needs a loaded state (else PIC_ERR_STATE), an absorbing
- * z axis and the Yee solver (else PIC_ERR_ARG); not valid on a batch (PIC_ERR_ARG), but a
- * batch steps its members' antennas.  A load removes the antenna.  Device memory: two
+ * receding plane passed into the total field; under the low-dispersion solver
+ * (PIC_SOLVER_CK) the averaged Faraday differences spread the B_y term over the
+ * neighbouring columns and add a B_z term at the nodes on either side of the plane (3D).
+ * The call adds the incident field downstream of the plane now.  Needs a loaded state
+ * (else PIC_ERR_STATE) and an absorbing z axis (else PIC_ERR_ARG); not valid on a batch
+ * (PIC_ERR_ARG), but a batch steps its members' antennas.  A load removes the antenna.  Device memory: two
  * doubles per lattice node (the box, the pulse's extent upstream and the distance light
  * covers while the plane crosses the box). */
 pic_status pic_set_laser_antenna(pic_ctx *ctx, const pic_laser_lab *laser, double z_lab);

@@ -15,6 +15,12 @@
 //    update is damped;
 //  * after the phase, values the receding plane passed join the total field: the
 //    incident value there is added.
+// Under the low-dispersion solver every Faraday difference is averaged over its
+// transverse neighbours (7/12 on itself, 1/12 on the edge and 1/48 on the corner ones),
+// so the same rule -- each stencil reads its neighbours in its own node's representation
+// -- spreads the B_y term over the neighbouring columns (the profile T replaced by its
+// weighted average) and adds a B_z term: the averaged dE_x/dy at a B_z node next to the
+// plane reads E_x on the z row across it.  The E update keeps the Yee differences.
 // One thread per transverse cell; the plane touches one or two z planes.  FP64
 // arithmetic, the result added in the working precision.
 #include "pic_internal.h"
@@ -46,6 +52,28 @@ __device__ __forceinline__ double ant_profile(const AntDev &A, const InstDev &I,
     const double x = (i + 0.5) * I.dx[0] - A.xc;
     const double y = I.ndim == 3 ? j * I.dx[1] - A.yc : 0.0;
     return exp(-(x * x + y * y) / (A.w0 * A.w0));
+}
+
+// the profile at E_x's (i + 1/2, j) as a neighbour in a difference stencil: outside the
+// box an absorbing axis reads 0 (the ghost value), a periodic one wraps
+__device__ __forceinline__ double ant_profile_nb(const AntDev &A, const InstDev &I, int i, int j)
+{
+    if (i < 0 || i >= I.n[0]) {
+        if (I.bc[0] != 0) return 0.0;
+        i = (i + I.n[0]) % I.n[0];
+    }
+    if (I.ndim == 3 && (j < 0 || j >= I.n[1])) {
+        if (I.bc[1] != 0) return 0.0;
+        j = (j + I.n[1]) % I.n[1];
+    }
+    return ant_profile(A, I, i, j);
+}
+
+// weight of a transverse neighbour of a low-dispersion difference (offsets db, dc)
+__device__ __forceinline__ double ck_weight(int db, int dc)
+{
+    const int e = (db != 0) + (dc != 0);
+    return e == 0 ? 7.0 / 12.0 : (e == 1 ? 1.0 / 12.0 : 1.0 / 48.0);
 }
 
 template <typename R>
@@ -90,8 +118,10 @@ __global__ void __launch_bounds__(256) k_ant_add(const InstDev *Ip, AntDev A, in
     }
 }
 
-// B_y at the half node next to the plane, after a B half update (damp: the second one)
-template <typename R>
+// B_y at the half node next to the plane, after a B half update (damp: the second one);
+// CK: the low-dispersion solver's terms (B_y spread over the neighbouring columns, and
+// in 3D B_z at the nodes on either side of the plane)
+template <typename R, bool CK>
 __global__ void __launch_bounds__(256) k_ant_bterm(const InstDev *Ip, AntDev A, int damp)
 {
     const InstDev &I = *Ip;
@@ -101,6 +131,25 @@ __global__ void __launch_bounds__(256) k_ant_bterm(const InstDev *Ip, AntDev A, 
     const double zp = ant_plane(A, I, *A.n);
     if (!(zp >= 0.0 && zp < I.n[2])) return;
     const int k = (int)floor(zp);
+    const double h = 0.5 * I.dt;
+    if (CK && I.ndim == 3) {
+        // B_z at (i + 1/2, j + 1/2, kz): its averaged dE_x/dy reads E_x at kz - 1, kz,
+        // kz + 1; the node below the plane (kz = k) reads the incident E_x of row k + 1
+        // above it and subtracts it, the node above (kz = k + 1) adds that of row k
+        R *Bz = (R *)I.B[2];
+        for (int side = 0; side < 2; ++side) {
+            const int kz = k + side;
+            if (kz >= I.n[2]) continue;
+            const int dk = side == 0 ? 1 : -1;
+            const double g = ant_ge(A, kz + dk);
+            double S = 0.0;
+            for (int di = -1; di <= 1; ++di)
+                S += ck_weight(dk, di) * (ant_profile_nb(A, I, i + di, j + 1) - ant_profile_nb(A, I, i + di, j));
+            const double f = damp ? damp_at<R>(I, i, j, kz) : 1.0;
+            const double term = (side == 0 ? -h : h) * S * g / I.dx[1];
+            Bz[padded(I, i, j, kz)] += (R)(f * term);
+        }
+    }
     double g;
     if (zp < k + 0.5) {  // B_y at k + 1/2 total field, E_x at k scattered
         g = ant_ge(A, k);
@@ -108,9 +157,17 @@ __global__ void __launch_bounds__(256) k_ant_bterm(const InstDev *Ip, AntDev A, 
         if (k + 1 >= I.n[2]) return;
         g = ant_ge(A, k + 1);
     }
+    double T;
+    if (CK) {
+        T = 0.0;
+        for (int di = -1; di <= 1; ++di)
+            for (int dj = -1; dj <= 1; ++dj) T += ck_weight(di, dj) * ant_profile_nb(A, I, i + di, j + dj);
+    } else {
+        T = ant_profile(A, I, i, j);
+    }
     const double f = damp ? damp_at<R>(I, i, j, k) : 1.0;
     R *By = (R *)I.B[1];
-    By[padded(I, i, j, k)] += (R)(f * (0.5 * I.dt) * (ant_profile(A, I, i, j) * g / I.dx[2]));
+    By[padded(I, i, j, k)] += (R)(f * h * (T * g / I.dx[2]));
 }
 
 // E_x at the node next to the plane, after the (damped) E update
@@ -164,13 +221,17 @@ cudaError_t launch_ant_add(int fp64, const InstDev *d_inst, const InstDev &I, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_ant_bterm(int fp64, const InstDev *d_inst, const InstDev &I, const AntDev &A, int damp, cudaStream_t s)
+cudaError_t launch_ant_bterm(int fp64, int ck, const InstDev *d_inst, const InstDev &I, const AntDev &A, int damp,
+                             cudaStream_t s)
 {
     const unsigned nb = blocks_of((long long)I.n[0] * I.n[1]);
-    if (fp64)
-        k_ant_bterm<double><<<nb, 256, 0, s>>>(d_inst, A, damp);
-    else
-        k_ant_bterm<float><<<nb, 256, 0, s>>>(d_inst, A, damp);
+    if (fp64) {
+        if (ck) k_ant_bterm<double, true><<<nb, 256, 0, s>>>(d_inst, A, damp);
+        else k_ant_bterm<double, false><<<nb, 256, 0, s>>>(d_inst, A, damp);
+    } else {
+        if (ck) k_ant_bterm<float, true><<<nb, 256, 0, s>>>(d_inst, A, damp);
+        else k_ant_bterm<float, false><<<nb, 256, 0, s>>>(d_inst, A, damp);
+    }
     return cudaGetLastError();
 }
 

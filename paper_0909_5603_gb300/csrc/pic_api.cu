@@ -894,7 +894,6 @@ extern "C" pic_status pic_set_laser_antenna(pic_ctx *ctx, const pic_laser_lab *l
                    std::isfinite(laser->z_center) && std::isfinite(z_lab)))
         return fail(ctx, PIC_ERR_ARG, "antenna laser parameters or plane invalid");
     if (laser && ctx->bc[2] != 1) return fail(ctx, PIC_ERR_ARG, "the laser antenna needs an absorbing z axis");
-    if (laser && ctx->opt.solver != PIC_SOLVER_YEE) return fail(ctx, PIC_ERR_ARG, "the laser antenna needs the Yee solver");
     if (!ctx->loaded) return fail(ctx, PIC_ERR_STATE, "pic_set_laser_antenna before any load");
     cudaSetDevice(ctx->device);
     CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1211,7 +1210,7 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
             cudaStream_t s = c->stream;
             CUDA_OR_FAIL(c, launch_bhalf(fp64, c->opt.solver, L, 0, s));
             for (auto m : ants) {
-                CUDA_OR_FAIL(c, launch_ant_bterm(fp64, m->d_inst, m->h, m->ant, 0, s));
+                CUDA_OR_FAIL(c, launch_ant_bterm(fp64, c->opt.solver == PIC_SOLVER_CK, m->d_inst, m->h, m->ant, 0, s));
                 CUDA_OR_FAIL(c, launch_ant_lattice(m->ant, m->dt, m->dx[2], 0, s));
             }
             CUDA_OR_FAIL(c, launch_efull(fp64, L, filtered, s));
@@ -1221,7 +1220,7 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
             }
             CUDA_OR_FAIL(c, launch_bhalf(fp64, c->opt.solver, L, 1, s));
             for (auto m : ants) {
-                CUDA_OR_FAIL(c, launch_ant_bterm(fp64, m->d_inst, m->h, m->ant, 1, s));
+                CUDA_OR_FAIL(c, launch_ant_bterm(fp64, c->opt.solver == PIC_SOLVER_CK, m->d_inst, m->h, m->ant, 1, s));
                 CUDA_OR_FAIL(c, launch_ant_lattice(m->ant, m->dt, m->dx[2], 2, s));
                 CUDA_OR_FAIL(c, launch_ant_add(fp64, m->d_inst, m->h, m->ant, 1, s));
             }

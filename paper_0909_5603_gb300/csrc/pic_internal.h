@@ -89,7 +89,8 @@ cudaError_t launch_efull(int fp64, const Launch &L, int filtered, cudaStream_t s
 // antenna: what = 0 adds the incident field downstream of the plane (when set), 1 the
 // values the plane passed in the last phase; B_y / E_x terms of the boundary; 1D lattice
 cudaError_t launch_ant_add(int fp64, const InstDev *d_inst, const InstDev &I, const AntDev &A, int what, cudaStream_t s);
-cudaError_t launch_ant_bterm(int fp64, const InstDev *d_inst, const InstDev &I, const AntDev &A, int damp, cudaStream_t s);
+cudaError_t launch_ant_bterm(int fp64, int ck, const InstDev *d_inst, const InstDev &I, const AntDev &A, int damp,
+                             cudaStream_t s);
 cudaError_t launch_ant_eterm(int fp64, const InstDev *d_inst, const InstDev &I, const AntDev &A, cudaStream_t s);
 cudaError_t launch_ant_lattice(const AntDev &A, double dt, double dz, int what, cudaStream_t s);
 cudaError_t launch_ghost(int fp64, const Launch &L, int axis, long long per_inst_max, cudaStream_t s);
