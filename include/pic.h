@@ -362,15 +362,17 @@ pic_status pic_autotune(const pic_grid *grid, const double dx[3], double dt, dou
  * Same result as pic_get_field(ctx, PIC_RHO, host_out, count) -- rho on the nodes,
  * n0 n1 n2 doubles, x fastest -- but the deposit goes into a fixed work grid that the
  * library owns (a device array of PIC_NOALLOC_RHO_MAX_CELLS doubles, 8 MiB, present on
- * every GPU that loads the library until the process exits) instead of per-context
- * memory.  It is for callers that must not enter a device allocator when they read the
+ * every GPU on which a context was created, until the process exits) instead of
+ * per-context memory.  It is for callers that must not enter a device allocator when they read the
  * density: code running under a device-memory budget that is already fully committed,
  * code called back from inside another library's memory pool, or a tight loop that has
  * to stay out of allocator locks.  The call itself allocates nothing (no cudaMalloc, no
  * cudaFree, no allocating library routine).
  *  - Grids of more than PIC_NOALLOC_RHO_MAX_CELLS cells are rejected with PIC_ERR_ARG.
- *  - The first call on a device looks up the work grid's device address there
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - CUDA loads the library's code lazily, and loading the part that holds the work grid
+ *    allocates it; pic_create does that load on its device, so this call never does.
+ *    Each call looks the grid's device address up afresh (cudaGetSymbolAddress, with
+ *    ctx's device current).
  *  - Every call shares the one work grid, which keeps the last call's contents; each call
  *    clears the part it uses first.  Calls that overlap on the GPU (several threads or
  *    streams at once) race on it: serialise them.

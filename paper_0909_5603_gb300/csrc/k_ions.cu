@@ -112,6 +112,12 @@ cudaError_t launch_ion_current(int fp64, const Launch &L, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t preload_rho_ion()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, k_rho_ion);
+}
+
 cudaError_t launch_rho_ion(const Launch &L, long long ncell, double *rho, cudaStream_t s)
 {
     if (ncell <= 0) return cudaSuccess;

@@ -295,6 +295,16 @@ cudaError_t launch_particle_sums(int fp64, const Launch &L, double *sums, cudaSt
     return cudaGetLastError();
 }
 
+// Loads the density kernels of one (order, precision) on the current device: CUDA loads
+// kernels lazily, on their first launch or attribute query.
+cudaError_t preload_rho(int order, int fp64)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = order == 1 ? (fp64 ? cudaFuncGetAttributes(&a, k_rho<1, double>) : cudaFuncGetAttributes(&a, k_rho<1, float>))
+                               : (fp64 ? cudaFuncGetAttributes(&a, k_rho<2, double>) : cudaFuncGetAttributes(&a, k_rho<2, float>));
+    return e == cudaSuccess ? preload_rho_ion() : e;
+}
+
 cudaError_t launch_rho(int order, int fp64, const Launch &L, double *rho, cudaStream_t s)
 {
     if (order == 1) {

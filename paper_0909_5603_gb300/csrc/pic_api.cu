@@ -540,7 +540,8 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
                cudaMemcpyAsync(c->d_cell_start, cstart, sizeof(cstart), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
                cudaMemcpyAsync(c->d_start_ptr, &dptr_start, sizeof(int *), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
                cudaMemcpyAsync(c->d_pencil, pencils, sizeof(pencils), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
-               prepare_particles(c->ndim, c->order, c->fp64, o.pusher, c->smem) == cudaSuccess;
+               prepare_particles(c->ndim, c->order, c->fp64, o.pusher, c->smem) == cudaSuccess &&
+               noalloc_load_grid(c->order, c->fp64) == cudaSuccess;
     if (!okc || upload_inst(c) != PIC_OK) {
         cudaError_t e = cudaGetLastError();
         dfree_all(c);

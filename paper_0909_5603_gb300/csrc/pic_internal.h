@@ -95,6 +95,12 @@ cudaError_t launch_ant_eterm(int fp64, const InstDev *d_inst, const InstDev &I, 
 cudaError_t launch_ant_lattice(const AntDev &A, double dt, double dz, int what, cudaStream_t s);
 cudaError_t launch_ghost(int fp64, const Launch &L, int axis, long long per_inst_max, cudaStream_t s);
 cudaError_t prepare_particles(int ndim, int order, int fp64, int pusher, size_t smem);
+// Loads, on the current device, the no-allocation charge work grid (pic_get_rho_noalloc)
+// and the density kernels that read-out launches: CUDA loads code and device arrays on
+// first use, so pic_create calls this and the read-out itself never triggers a load.
+cudaError_t noalloc_load_grid(int order, int fp64);
+cudaError_t preload_rho(int order, int fp64);
+cudaError_t preload_rho_ion();
 cudaError_t launch_field_energy(int fp64, const Launch &L, double *sums, cudaStream_t s);
 cudaError_t launch_pack(int fp64, const InstDev &I, int comp, int filtered, double *dense, long long ncell, cudaStream_t s);
 cudaError_t launch_unpack(int fp64, const InstDev &I, int comp, const double *dense, long long ncell, cudaStream_t s);

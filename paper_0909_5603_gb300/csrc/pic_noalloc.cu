@@ -7,7 +7,6 @@
 // density.  The deposit kernel is the same one (launch_rho); only its destination
 // differs.
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/pic.h"
 #include "pic_internal.h"
@@ -20,38 +19,40 @@ using namespace pic;
 
 namespace {
 
-// The work grid: PIC_NOALLOC_RHO_MAX_CELLS doubles (8 MiB) in every GPU that loads the
-// library, held until the process exits.  In host code this name is only a host-side
-// stand-in; its device address comes from cudaGetSymbolAddress (scratch_on_device).
+// The work grid: PIC_NOALLOC_RHO_MAX_CELLS doubles (8 MiB) in every GPU on which a context
+// was created, held until the process exits.  In host code this name is only a host-side
+// stand-in; its device address comes from cudaGetSymbolAddress with the device current.
 static __device__ __align__(256) double g_rho_scratch[PIC_NOALLOC_RHO_MAX_CELLS];
 
-constexpr int kMaxDevices = 128;
-std::mutex g_setup_mutex;
-double *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the work grid on `device`, looked up once per device with that
-// device current.  Returns nullptr (and fills msg) when the lookup fails.
-double *scratch_on_device(int device, char *msg, size_t msglen)
+// Device address of the work grid on the current device, looked up on every call (cheap
+// once the module is loaded, and never stale if another component resets the device's
+// primary context).  Returns nullptr (and fills msg) when the lookup fails.
+double *scratch_on_device(char *msg, size_t msglen)
 {
-    if (device < 0 || device >= kMaxDevices) {
-        snprintf(msg, msglen, "device ordinal %d outside the supported range", device);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_rho_scratch);
+    if (e != cudaSuccess || !p) {
+        snprintf(msg, msglen, "cudaGetSymbolAddress of the no-allocation work grid failed: %s", cudaGetErrorString(e));
         return nullptr;
     }
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_rho_scratch);
-        if (e != cudaSuccess || !p) {
-            snprintf(msg, msglen, "cudaGetSymbolAddress of the no-allocation work grid failed: %s",
-                     cudaGetErrorString(e));
-            return nullptr;
-        }
-        g_scratch_addr[device] = static_cast<double *>(p);
-    }
-    return g_scratch_addr[device];
+    return static_cast<double *>(p);
 }
 
 }  // namespace
+
+namespace pic {
+
+// CUDA loads a module lazily, on the first use of one of its symbols, and loading this
+// one allocates the work grid: pic_create (with its device current) does that first use,
+// and loads the density kernels the read-out launches.
+cudaError_t noalloc_load_grid(int order, int fp64)
+{
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_rho_scratch);
+    return e == cudaSuccess ? preload_rho(order, fp64) : e;
+}
+
+}  // namespace pic
 
 extern "C" pic_status pic_get_rho_noalloc(pic_ctx *ctx, double *host_out, size_t count)
 {
@@ -71,7 +72,7 @@ extern "C" pic_status pic_get_rho_noalloc(pic_ctx *ctx, double *host_out, size_t
     if (cudaSetDevice(v.device) != cudaSuccess) return ctx_fail(ctx, PIC_ERR_CUDA, "cudaSetDevice failed");
     pic_status st = pic_synchronize(ctx);  // also reports a sticky device error
     if (st != PIC_OK) return st;
-    double *grid = scratch_on_device(v.device, msg, sizeof(msg));
+    double *grid = scratch_on_device(msg, sizeof(msg));
     if (!grid) return ctx_fail(ctx, PIC_ERR_CUDA, msg);
     // the array keeps the previous call's contents: clear the part this grid uses
     const size_t bytes = sizeof(double) * (size_t)v.ncell;
