@@ -19,7 +19,6 @@ namespace pic {
 constexpr int kNT = 256;          // threads per particle CTA
 constexpr int kNW = kNT / 32;
 constexpr int kChunk = kNT;       // particles per chunk: one per thread
-constexpr int kFlushChunks = 2047 / kChunk;  // fixed-point J flush interval (see FixedAcc)
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 
 // -------------------------------------------------------------------------------------
@@ -281,12 +280,15 @@ __device__ __forceinline__ R interp(const R *f, int bx, int bxy, int i0, int j0,
     return acc;
 }
 
-// Global index of J tile element e (component, local x, y, z) after wrapping (periodic)
-// or clipping (absorbing, returns -1) its guard cells.
-__device__ __forceinline__ long long j_global_index(const InstDev &I, const int T0[3], int ND, int e, int jvol, int &comp)
+// Global index of J tile element e (component stride jst, local x, y, z) after wrapping
+// (periodic) or clipping (absorbing, returns -1) its guard cells; -1 for the padding
+// entries jvol .. jst - 1 of a component.
+__device__ __forceinline__ long long j_global_index(const InstDev &I, const int T0[3], int ND, int e, int jvol, int jst,
+                                                    int &comp)
 {
-    comp = e / jvol;
-    const int rem = e - comp * jvol;
+    comp = e / jst;
+    const int rem = e - comp * jst;
+    if (rem >= jvol) return -1;
     const int lx = rem % I.jdim[0];
     const int ly = (rem / I.jdim[0]) % I.jdim[1];
     const int lz = rem / (I.jdim[0] * I.jdim[1]);
@@ -302,31 +304,110 @@ __device__ __forceinline__ long long j_global_index(const InstDev &I, const int 
     return (gidx[0] + I.gh[0]) + I.sy * (gidx[1] + I.gh[1]) + I.sz * (gidx[2] + I.gh[2]);
 }
 
-// FP32 tile: value = (H + L 2^-16) / scale, added to global J; the tile is cleared.
-__device__ __forceinline__ void flush_j_fixed(const InstDev &I, const int T0[3], int ND, int *H, int *Lo, int jvol,
-                                              float inv_scale, int tid, int nt)
+// FP32 tile, after a chunk: T += A * inv[component], A = 0 over the entries this thread
+// owns, 4 at a time (components start on multiples of 4 entries, jst apart; the arrays
+// start 16-byte aligned).
+__device__ __forceinline__ void fold_chunk(int *A, float *T, int jst, const float inv[3], int tid, int nt)
 {
-    for (int e = tid; e < 3 * jvol; e += nt) {
-        const int hv = H[e], lv = Lo[e];
-        if ((hv | lv) == 0) continue;
-        H[e] = 0;
-        Lo[e] = 0;
-        int comp;
-        const long long gi = j_global_index(I, T0, ND, e, jvol, comp);
-        if (gi < 0) continue;
-        const float v = ((float)hv + (float)lv * (1.0f / 65536.0f)) * inv_scale;
-        atomicAdd((float *)I.J[comp] + gi, v);
+    int4 *A4 = reinterpret_cast<int4 *>(A);
+    float4 *T4 = reinterpret_cast<float4 *>(T);
+    const int q1 = jst >> 2, q2 = jst >> 1, n4 = 3 * (jst >> 2);
+    for (int e = tid; e < n4; e += nt) {
+        const float s = e >= q2 ? inv[2] : e >= q1 ? inv[1] : inv[0];
+        const int4 a = A4[e];
+        float4 t = T4[e];
+        t.x = __fmaf_rn((float)a.x, s, t.x);
+        t.y = __fmaf_rn((float)a.y, s, t.y);
+        t.z = __fmaf_rn((float)a.z, s, t.z);
+        t.w = __fmaf_rn((float)a.w, s, t.w);
+        T4[e] = t;
+        A4[e] = make_int4(0, 0, 0, 0);
+    }
+}
+
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// FP32 tile: value = T + A * inv[component] (the last chunk's accumulator and scale),
+// added to global J.  Each J-tile row (component, y,
+// z) is cut into groups of 4 entries aligned with the 16-byte groups of the global row;
+// a group whose entries all lie inside the interior along x (entries before the row or
+// after its end add 0 to the padded row) is added with one vector reduction, the others
+// entry by entry with wrap-around (periodic) or clipping (absorbing) along x.  Rows
+// outside the box along y or z wrap or are dropped as a whole.
+__device__ __forceinline__ void flush_j_chunk(const InstDev &I, const int T0[3], int ND, const int *A, const float *T,
+                                              int jst, const float inv[3], int warp, int lane)
+{
+    const int jd0 = I.jdim[0], jd1 = I.jdim[1], jd2 = I.jdim[2];
+    const int rows = 3 * jd1 * jd2;
+    const int gx0 = T0[0] + I.jlo;              // global x of tile entry 0 (unpadded)
+    const int a0 = (4 - ((gx0 + I.gh[0]) & 3)) & 3;  // first entry on a 16-byte boundary
+    const int lx0 = a0 > 0 ? a0 - 4 : 0;         // first group start (may be negative: pads)
+    const int ng = (jd0 - lx0 + 3) >> 2;
+    const int lpr = ng <= 4 ? 4 : ng <= 8 ? 8 : ng <= 16 ? 16 : 32;  // lanes per row
+    const int rpw = 32 / lpr;
+    for (int rb = warp * rpw; rb < rows; rb += kNW * rpw) {
+        const int row = rb + lane / lpr;
+        if (row >= rows) continue;
+        const int comp = row / (jd1 * jd2);
+        const int ryz = row - comp * jd1 * jd2;
+        const int lz = ryz / jd1, ly = ryz - lz * jd1;
+        int gy = ND == 3 ? T0[1] + I.jlo + ly : 0;
+        int gz = T0[2] + I.jlo + lz;
+        bool keep = true;
+        if (ND == 3 && (gy < 0 || gy >= I.n[1])) {
+            if (I.bc[1] != 0) keep = false;
+            gy += gy < 0 ? I.n[1] : -I.n[1];
+        }
+        if (gz < 0 || gz >= I.n[2]) {
+            if (I.bc[2] != 0) keep = false;
+            gz += gz < 0 ? I.n[2] : -I.n[2];
+        }
+        const int e0 = comp * jst + ryz * jd0;
+        const float sc = comp == 0 ? inv[0] : comp == 1 ? inv[1] : inv[2];
+        float *grow = (float *)I.J[comp] + I.gh[0] + I.sy * (gy + I.gh[1]) + I.sz * (gz + I.gh[2]);
+        for (int g = lane % lpr; g < ng; g += lpr) {
+            const int lx = lx0 + 4 * g;
+            float v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int x = lx + q;
+                v[q] = 0.f;
+                if (x >= 0 && x < jd0) v[q] = __fmaf_rn((float)A[e0 + x], sc, T[e0 + x]);
+            }
+            if (!keep) continue;
+            const int gx = gx0 + lx;  // global x of the group's first entry
+            const int xr0 = lx < 0 ? gx0 : gx, xr1 = min(gx + 3, gx0 + jd0 - 1);  // real entries
+            if (xr0 >= 0 && xr1 < I.n[0] && gx + I.gh[0] >= 0 && gx + 3 + I.gh[0] < I.P[0]) {
+                if ((v[0] != 0.f) | (v[1] != 0.f) | (v[2] != 0.f) | (v[3] != 0.f))
+                    red_add_v4(grow + gx, v[0], v[1], v[2], v[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int x = lx + q;
+                    if (x < 0 || x >= jd0 || v[q] == 0.f) continue;
+                    int gxq = gx + q;
+                    if (gxq < 0 || gxq >= I.n[0]) {
+                        if (I.bc[0] != 0) continue;
+                        gxq += gxq < 0 ? I.n[0] : -I.n[0];
+                    }
+                    atomicAdd(grow + gxq, v[q]);
+                }
+            }
+        }
     }
 }
 
 __device__ __forceinline__ void flush_j_double(const InstDev &I, const int T0[3], int ND, const double *J, int jvol,
-                                               int tid, int nt)
+                                               int jst, int tid, int nt)
 {
-    for (int e = tid; e < 3 * jvol; e += nt) {
+    for (int e = tid; e < 3 * jst; e += nt) {
         const double v = J[e];
         if (v == 0.0) continue;
         int comp;
-        const long long gi = j_global_index(I, T0, ND, e, jvol, comp);
+        const long long gi = j_global_index(I, T0, ND, e, jvol, jst, comp);
         if (gi < 0) continue;
         atomicAdd((double *)I.J[comp] + gi, v);
     }
@@ -337,7 +418,7 @@ __device__ __forceinline__ void flush_j_double(const InstDev &I, const int T0[3]
 template <int ND, int ORD, typename R, int PUSHER, bool INJ>
 __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launch L)
 {
-    constexpr bool kFixed = sizeof(R) == 4;  // FP32: fixed-point integer J accumulation
+    constexpr bool kFixed = sizeof(R) == 4;  // FP32: fixed-point chunk accumulator + FP32 tile
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ SrcTable S;
     __shared__ uint64_t bar;
@@ -347,6 +428,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     __shared__ int s_pcell[2][kNT], s_pid[2][kNT];
     __shared__ R s_poff[2][3][kNT], s_pu[2][3][kNT], s_pw[2][kNT];
     __shared__ int s_cnt[2][kNW][kBuckets];  // per-warp bucket counts, double-buffered per chunk
+    __shared__ __align__(16) unsigned s_bmax[3][kNW];  // FP32: per-warp contribution bounds of the chunk
 
     const int g = blockIdx.x;
     const int ii = find_instance(L.tile_start, L.ninst, g);
@@ -375,8 +457,9 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     }
 
     // shared-memory carve-up (base rounded up to 128 bytes for TMA): 6 field boxes, then
-    // the J tile: 3 components of jvol cells, as FP64 values (FP64 mode) or as two 32-bit
-    // integer arrays H and L of 3 jvol each (FP32 mode) -- 8 bytes per cell either way
+    // the J tile: 3 components of jvol cells, jst = jvol rounded up to a multiple of 4 apart,
+    // as FP64 values (FP64 mode) or as the 32-bit integer chunk accumulator A and the FP32
+    // tile T of 3 jst entries each (FP32 mode) -- 8 bytes per entry either way
     const int boxn = I.box[0] * I.box[1] * I.box[2];
     const int box_bytes = boxn * (int)sizeof(R);
     const int box_stride = (box_bytes + 127) & ~127;
@@ -384,8 +467,10 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     R *sF = reinterpret_cast<R *>(sbase);
     unsigned char *sJraw = sbase + 6 * box_stride;
     const int jvol = I.jdim[0] * I.jdim[1] * I.jdim[2];
-    int *sJH = reinterpret_cast<int *>(sJraw);
-    int *sJL = sJH + 3 * jvol;
+    const int jst = (jvol + 3) & ~3;
+    const int jv4 = 3 * (jst >> 2);  // J-tile entries in groups of 4
+    int *sJA = reinterpret_cast<int *>(sJraw);
+    float *sJT = reinterpret_cast<float *>(sJA + 4 * jv4);
     double *sJD = reinterpret_cast<double *>(sJraw);
 
     if (tid == 0) {
@@ -398,7 +483,8 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
         for (int c = 0; c < 6; ++c)
             tma_load_3d(sbase + c * box_stride, I.tmap + c, x, y, z, &bar);
     }
-    for (int e = tid; e < 6 * jvol; e += kNT) sJH[e] = 0;  // zeroes the FP64 tile too
+    for (int e = tid; e < 2 * jv4; e += kNT)  // A and T (or the FP64 tile)
+        reinterpret_cast<int4 *>(sJraw)[e] = make_int4(0, 0, 0, 0);
     for (int e = tid; e < 2 * kNW * kBuckets; e += kNT) (&s_cnt[0][0][0])[e] = 0;
     if (tid < kBuckets) s_run[tid] = 0;
     build_sources(I, in, tx, ty, tz, S);  // ends with __syncthreads
@@ -413,7 +499,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     if (tid == 0 && S.count != count) atomicOr(I.err, kErrInternal);
 
     // per-instance constants in the working precision (host-formed); in FP32 mode the
-    // current factor qdv carries the fixed-point scale (see FixedAcc)
+    // current factor qdv carries the fixed-point scale (see ChunkAcc)
     const StepCoef<R> &K = coef<R>(I);
     const R h = K.h;
     const R qdv = K.qdv;
@@ -461,6 +547,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
         return p;
     };
     int pos_next = stage(tid, 0);
+    float inv[3] = {1.f, 1.f, 1.f};  // FP32: the current chunk's per-component 1 / scale
 
     for (int base = 0, r = 0; base < count; base += kChunk, ++r) {
         int bucket = 28;  // 0..26 direction, 27 dead, 28 no particle
@@ -473,6 +560,12 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
         if (base + kChunk < count) pos_next = stage(base + kChunk + tid, pb ^ 1);
         if (slot < count && (pos < 0 || pos >= I.cap)) atomicOr(I.err, kErrInternal);
         int l[3] = {0, 0, 0}, cc[3] = {0, 0, 0};
+        // deposit inputs; a lane without a particle deposits zero from inside the tile
+        R o[3] = {R(0.5), R(0.5), R(0.5)};
+        int l1[3] = {0, 0, 0};
+        R disp[3] = {R(0), R(0), R(0)};
+        R fx = R(0), fy = R(0), fz = R(0);
+        o1[0] = o1[1] = o1[2] = R(0.5);
         bool have = false;
         if (pos >= 0 && pos < I.cap) {
             const int c = s_pcell[pb][tid];
@@ -487,7 +580,6 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             if (!have) atomicOr(I.err, kErrInternal);
         }
         if (have) {
-            R o[3];
             o[0] = s_poff[pb][0][tid];
             o[1] = ND == 3 ? s_poff[pb][1][tid] : R(0);
             o[2] = s_poff[pb][2][tid];
@@ -543,7 +635,6 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             bool bad = false;
             o1[0] = o[0]; o1[1] = o[1]; o1[2] = o[2];
             int kstep[3] = {0, 0, 0};
-            R disp[3] = {R(0), R(0), R(0)};
             R vy;
             if (sizeof(R) == 4) {
                 const float gn = sqrtf(1.f + (float)u[0] * (float)u[0] + (float)u[1] * (float)u[1] + (float)u[2] * (float)u[2]);
@@ -572,18 +663,15 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
                 disp[0] = disp[1] = disp[2] = R(0);
             }
 
-            // ---- Esirkepov deposit into the shared J tile
+            // ---- Esirkepov deposit inputs
             {
-                const int l1[3] = {l[0] + kstep[0], l[1] + kstep[1], l[2] + kstep[2]};
+                l1[0] = l[0] + kstep[0];
+                l1[1] = l[1] + kstep[1];
+                l1[2] = l[2] + kstep[2];
                 const R qw = qdv * w;
-                const R fx = -qw * jfx, fy = ND == 3 ? -qw * jfy : qw * vy, fz = -qw * jfz;
-                // FP32: the current follows the computed displacement (see shape_window)
-                if (kFixed)
-                    deposit_esirkepov<ND, ORD, true, R>(l, o, l1, o1, disp, fx, fy, fz, I.jlo, jlo_y, jd0, jd01,
-                                                        jvol, FixedAcc{sJH, sJL});
-                else
-                    deposit_esirkepov<ND, ORD, false, R>(l, o, l1, o1, disp, fx, fy, fz, I.jlo, jlo_y, jd0, jd01,
-                                                         jvol, DoubleAcc{sJD});
+                fx = -qw * jfx;
+                fy = ND == 3 ? -qw * jfy : qw * vy;
+                fz = -qw * jfz;
             }
 
             // ---- new cell, destination tile, bucket
@@ -602,12 +690,63 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             if (dead) {
                 bucket = kDead;
             } else {
-                const int ddx = axis_dir(tx, cn[0] / I.ts[0], I.nt[0], I.bc[0]);
-                const int ddy = ND == 3 ? axis_dir(ty, cn[1] / I.ts[1], I.nt[1], I.bc[1]) : 0;
-                const int ddz = axis_dir(tz, cn[2] / I.ts[2], I.nt[2], I.bc[2]);
-                bucket = (ddz + 1) * 9 + (ddy + 1) * 3 + (ddx + 1);
+                // the new tile from the tile-local cell (a move stays below one cell, so it
+                // is this tile or a neighbour; across a periodic face the coordinate wraps)
+                const int l1v[3] = {l[0] + kstep[0], l[1] + kstep[1], l[2] + kstep[2]};
+                const int tl[3] = {tsx, tsy, tsz}, to[3] = {tx, ty, tz};
+                int dd[3] = {0, 0, 0};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (ND == 2 && a == 1) continue;
+                    int tn = to[a] + (l1v[a] < 0 ? -1 : (l1v[a] >= tl[a] ? 1 : 0));
+                    tn += tn < 0 ? I.nt[a] : (tn >= I.nt[a] ? -I.nt[a] : 0);
+                    dd[a] = axis_dir(to[a], tn, I.nt[a], I.bc[a]);
+                }
+                bucket = (dd[2] + 1) * 9 + (dd[1] + 1) * 3 + (dd[0] + 1);
             }
             cell_new = cn[0] + I.n[0] * (cn[1] + I.n[1] * cn[2]);
+        }
+
+        // ---- Esirkepov deposit into the shared J tile, by every lane of the warp.  FP32:
+        // the chunk's per-component scale (see ChunkAcc) from the warps' bounds, after a
+        // barrier that also completes the previous chunk's fold of A into T.
+        if constexpr (kFixed) {
+            // |f_a| (|d_a| + 2^-18): a particle that changes its nodes forms its weight changes
+            // from differences of weights, whose rounding (< 2^-19 in the running sums) is
+            // not relative to a small displacement
+            const float eps = 0x1p-18f;
+            const float bnd[3] = {fabsf(fx) * (fabsf(disp[0]) + eps),
+                                  ND == 3 ? fabsf(fy) * (fabsf(disp[1]) + eps) : fabsf(fy),
+                                  fabsf(fz) * (fabsf(disp[2]) + eps)};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(bnd[a]));
+                if (lane == 0) s_bmax[a][warp] = m;
+            }
+            __syncthreads();
+            float sc[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const uint4 m0 = reinterpret_cast<const uint4 *>(s_bmax[a])[0];
+                const uint4 m1 = reinterpret_cast<const uint4 *>(s_bmax[a])[1];
+                const unsigned m = max(max(max(m0.x, m0.y), max(m0.z, m0.w)), max(max(m1.x, m1.y), max(m1.z, m1.w)));
+                // the largest contribution is at most K times the bound (see ChunkAcc): K =
+                // S_max^2 in 3D and for the out-of-plane current of 2D3V, S_max for the
+                // in-plane ones; S_max = 3/4 (order 2) or 1 (order 1)
+                constexpr float Smax = ORD == 2 ? 0.75f : 1.0f;
+                const float K = (ND == 3 || a == 1) ? Smax * Smax : Smax;
+                // inv = K bound / (0.999 2^22), scale = 1 / inv (correctly rounded, so
+                // scale x inv = 1 to FP32 precision)
+                const float bk = K * __uint_as_float(m);
+                inv[a] = bk > 1e-30f ? bk * (1.0f / (0.999f * 4194304.0f)) : 1.0f;
+                sc[a] = __frcp_rn(inv[a]);
+            }
+            // the current follows the computed displacement (see shape_window)
+            deposit_esirkepov<ND, ORD, true, true, R>(l, o, l1, o1, disp, fx * sc[0], fy * sc[1], fz * sc[2], I.jlo,
+                                                      jlo_y, jd0, jd01, jst, ChunkAcc{sJA});
+        } else {
+            deposit_esirkepov<ND, ORD, false, false, R>(l, o, l1, o1, disp, fx, fy, fz, I.jlo, jlo_y, jd0, jd01,
+                                                        jst, DoubleAcc{sJD});
         }
 
         // ---- stable ranking of the chunk by bucket: order (warp, lane), one barrier per
@@ -665,11 +804,10 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
             if (id_out) id_out[p] = pid;
         }
 
-        // ---- FP32: fold the fixed-point J into global memory before it could overflow
-        if (kFixed && (r + 1) % kFlushChunks == 0 && base + kChunk < count) {
-            __syncthreads();
-            flush_j_fixed(I, T0, ND, sJH, sJL, jvol, I.jinv, tid, kNT);
-            __syncthreads();
+        // ---- FP32: fold the chunk accumulator into the FP32 tile (the last chunk's is
+        // added by the flush)
+        if constexpr (kFixed) {
+            if (base + kChunk < count) fold_chunk(sJA, sJT, jst, inv, tid, kNT);
         }
     }
     __syncthreads();  // all deposits and bucket totals complete
@@ -687,10 +825,10 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
     if (tid == 0 && s_run[kDead] > 0) atomicAdd(I.lost, (unsigned long long)s_run[kDead]);
 
     // ---- flush the J tile
-    if (kFixed)
-        flush_j_fixed(I, T0, ND, sJH, sJL, jvol, I.jinv, tid, kNT);
+    if constexpr (kFixed)
+        flush_j_chunk(I, T0, ND, sJA, sJT, jst, inv, warp, lane);
     else
-        flush_j_double(I, T0, ND, sJD, jvol, tid, kNT);
+        flush_j_double(I, T0, ND, sJD, jvol, jst, tid, kNT);
 }
 
 }  // namespace pic

@@ -235,7 +235,7 @@ static void fill_step_coef(InstDev &h)
     h.cd = d;
     StepCoef<float> f;
     f.h = (float)d.h;
-    f.qdv = (float)d.qdv * h.jscale;
+    f.qdv = (float)d.qdv;
     for (int a = 0; a < 3; ++a) {
         f.jf[a] = (float)d.jf[a];
         f.dtdx[a] = (float)d.dtdx[a];
@@ -400,7 +400,6 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     h.inj_id0 = INT_MAX;
     h.q = o.charge;
     h.m = o.mass;
-    h.jscale = h.jinv = 1.0f;  // until a load sets the FP32 current scale
     fill_step_coef(h);
     // gather box (tile + guard) and J tile geometry; the box starts one cell before the
     // tile (padded x coordinate T0 + 4, 16-byte aligned) and its x extent is a multiple of
@@ -423,9 +422,10 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     h.jlo = -shape_order;
     for (int a = 0; a < 3; ++a) h.jdim[a] = activeaxis(c->ndim, a) ? ts[a] + (shape_order == 2 ? 5 : 3) : 1;
     const size_t boxb = ((size_t)h.box[0] * h.box[1] * h.box[2] * c->es + 127) / 128 * 128;
-    // 6 field boxes + the J tile at 8 bytes per cell and component (FP64 values, or the two
-    // 32-bit fixed-point halves in FP32 mode) + alignment slack
-    c->smem = 128 + 6 * boxb + 3 * (size_t)h.jdim[0] * h.jdim[1] * h.jdim[2] * 8;
+    // 6 field boxes + the J tile at 8 bytes per cell and component (FP64 values, or the
+    // 32-bit chunk accumulator and the FP32 tile in FP32 mode; each component rounded up to
+    // a multiple of 4 entries) + alignment slack
+    c->smem = 128 + 6 * boxb + 3 * (((size_t)h.jdim[0] * h.jdim[1] * h.jdim[2] + 3) / 4 * 4) * 8;
     if (c->smem > 200 * 1024) {
         const size_t smem = c->smem;
         delete c;
@@ -723,7 +723,7 @@ static pic_status place_from_host(pic_ctx *c, int64_t n, const int32_t *cell, co
 // After the particles are in place: the initial tile layout (every tile's particles in
 // its own segment, all in the "stays" bucket), the FP32 current scale, and a reset of
 // the step state.
-static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg, double wmax)
+static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg)
 {
     InstDev &h = c->h;
     const int R = h.R;
@@ -755,18 +755,6 @@ static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg, double wm
     CUDA_OR_FAIL(c, cudaMemcpyAsync(h.pop, pop.data(), sizeof(int) * pop.size(), cudaMemcpyHostToDevice, s));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(h.chunk_pre[0], pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, s));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(h.chunk_cb[0], cbv.data(), sizeof(int) * cbv.size(), cudaMemcpyHostToDevice, s));
-    // FP32 fixed-point current scale: the power of two that maps the bound |q| max(w) / dV
-    // on any single current contribution to at most 2^20
-    {
-        const double bound = std::fabs(c->opt.charge) * wmax / (c->dx[0] * c->dx[1] * c->dx[2]);
-        int e = 0;
-        if (bound > 0.0) {
-            std::frexp(bound, &e);  // bound < 2^e
-            e = std::max(-100, std::min(100, e));
-        }
-        h.jscale = bound > 0.0 ? (float)std::ldexp(1.0, 20 - e) : 1.0f;
-        h.jinv = bound > 0.0 ? (float)std::ldexp(1.0, e - 20) : 1.0f;
-    }
     fill_step_coef(h);
     apply_injection(c);
     antenna_off(c);  // a load removes the antenna
@@ -803,12 +791,11 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
     if (n > 0 && (!cell || !off || !u || !w)) return fail(c, PIC_ERR_ARG, "particle arrays must not be NULL");
     // validation and a stable counting sort by tile id, on T host threads over contiguous
     // ranges: each range finds its first invalid particle (the lowest over the ranges is
-    // the one reported), its largest |w| and its tile histogram; slots are then assigned
+    // the one reported) and its tile histogram; slots are then assigned
     // range by range in order, which keeps the sort stable
     const int T = host_workers(n);
     std::vector<int64_t> bad(T, INT64_MAX);
     std::vector<int> bad_kind(T, 0);
-    std::vector<double> wmaxs(T, 0.0);
     std::vector<std::vector<int>> hist(T);
     std::vector<int> seg(h.ntiles + 1, 0), slot(n > 0 ? n : 1);
     parallel_ranges(n, T, [&](int t, int64_t b, int64_t e) {
@@ -826,7 +813,6 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
                 bad_kind[t] = kind;
                 return;
             }
-            wmaxs[t] = std::max(wmaxs[t], std::fabs(w[p]));
         }
         std::vector<int> &hc = hist[t];
         hc.assign(h.ntiles, 0);
@@ -850,8 +836,6 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
         }
         return fail(c, PIC_ERR_NAN, "particle %lld: non-finite momentum or weight", (long long)p);
     }
-    double wmax = 0.0;
-    for (int t = 0; t < T; ++t) wmax = std::max(wmax, wmaxs[t]);
     // segment starts, then each range's first slot in each tile
     for (int t = 0; t < T; ++t)
         for (int k = 0; k < h.ntiles; ++k) seg[k + 1] += hist[t][k];
@@ -872,7 +856,7 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
     pic_status st = ensure_particle_capacity(c, n);
     if (st != PIC_OK) return st;
     if ((st = place_from_host(c, n, cell, off, u, w, id, 0, slot)) != PIC_OK) return st;
-    return finish_load(c, seg, wmax);
+    return finish_load(c, seg);
 }
 
 extern "C" pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3, const double *u3,
@@ -1120,10 +1104,7 @@ extern "C" pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *lase
     if ((st = place_from_host(ctx, nb, P.cell.data(), P.off.data(), P.mom.data(), P.weight.data(), P.id.data(), 0,
                               beam_slot)) != PIC_OK)
         return st;
-    // weight bound: the plateau weight (the profile never exceeds 1) and the beam's
-    double wmax = n_plasma > 0 ? PG.gb * PG.n0 * 1.0 * PG.dV / PG.ppc : 0.0;
-    for (int64_t p = 0; p < nb; ++p) wmax = std::max(wmax, std::fabs(P.weight[p]));
-    return finish_load(ctx, seg, wmax);
+    return finish_load(ctx, seg);
 }
 
 // ------------------------------------------------------------------------------------

@@ -65,7 +65,8 @@ __device__ __forceinline__ int shape_stag(int l, R o, R w[ORD + 1])
 // 3e-8 / d, 6e-6 for a thermal particle moving 0.005 cells per step.  Taking the computed
 // displacement keeps J at FP32 precision relative to the motion; the rounding then
 // appears only as a charge-conservation residual of at most half an ulp times the shape
-// slope per particle and step.
+// slope per particle and step.  With kDisp a particle that changes its nodes gets DS from
+// the slopes over the two parts of its move (below), not from a difference of weights.
 template <int ORD, bool kDisp, typename R>
 __device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R disp, R S0[ORD + 2], R DS[ORD + 2],
                                             int &nw)
@@ -104,7 +105,44 @@ __device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R disp, 
         const R c0 = (i < ORD + 1) ? w1[i < ORD + 1 ? i : 0] : R(0);
         const R c1 = (i >= 1) ? w1[i >= 1 ? i - 1 : 0] : R(0);
         S0[i] = s0 == 0 ? a0 : a1;
-        DS[i] = (s1 == 0 ? c0 : c1) - S0[i];
+        if (!kDisp) DS[i] = (s1 == 0 ? c0 : c1) - S0[i];
+    }
+    if (kDisp) {
+        // The move crosses one knot of the shape (order 2: the half-integer between the two
+        // nearest nodes, 3/2 above the window start; order 1: the cell face, 1 above it).
+        // Each weight is one polynomial piece on either side of the knot, so its change is
+        // the integral of its slope over the two sub-moves, e0 up to the knot and e1 beyond
+        // it: DS_i = e0 S'_i(mid0) + e1 S'_i(mid1), the slopes taken at the sub-moves'
+        // midpoints (exact: the slope is linear, order 2, or constant, order 1, on a
+        // piece).  e0 = knot - x0 is one rounding of a small constant minus the offset and
+        // e1 = d - e0, so DS carries an error relative to the displacement rather than the
+        // weights' rounding (~1e-7 absolute), which a small move would not resolve.
+        const R xk = ORD == 2 ? R(1.5) : R(1);
+        const R e0 = (xk - R(l0 - ws)) - o0;
+        const R e1 = disp - e0;
+        R sum = R(0);
+#pragma unroll
+        for (int i = 0; i < ORD + 2; ++i) {
+            const R dk = xk - R(i);  // the knot relative to node i
+            const R m0 = dk - R(0.5) * e0, m1 = dk + R(0.5) * e1;
+            R g0, g1;
+            if (ORD == 2) {
+                const R a0 = fabs(m0), a1 = fabs(m1);
+                // S = 3/4 - x^2 (|x| < 1/2), (3/2 - |x|)^2 / 2 (|x| < 3/2): S' = -2x, -sign(x)(3/2 - |x|)
+                g0 = a0 < R(0.5) ? R(-2) * m0 : (a0 < R(1.5) ? copysign(R(1.5) - a0, -m0) : R(0));
+                g1 = a1 < R(0.5) ? R(-2) * m1 : (a1 < R(1.5) ? copysign(R(1.5) - a1, -m1) : R(0));
+            } else {
+                // S = 1 - |x| (|x| < 1): S' = -sign(x)
+                g0 = fabs(m0) < R(1) ? copysign(R(1), -m0) : R(0);
+                g1 = fabs(m1) < R(1) ? copysign(R(1), -m1) : R(0);
+            }
+            if (i < ORD + 1) {
+                DS[i] = e0 * g0 + e1 * g1;
+                sum += DS[i];
+            } else {
+                DS[i] = -sum;  // the running sum over the window ends at exactly zero
+            }
+        }
     }
     nw = ORD + 2;
     return ws;
@@ -113,36 +151,40 @@ __device__ __forceinline__ int shape_window(int l0, R o0, int l1, R o1, R disp, 
 // ------------------------------------------------------------------------------------
 // Shared-memory J accumulation policies for the deposit.
 //
-// FixedAcc (FP32 mode): contributions arrive pre-scaled so that each is at most 2^20 in
-// magnitude: any single current contribution is bounded by |q| w / dV (the Esirkepov
-// running sum never exceeds the displacement in cells, which is below dt / dx since
-// |v| < c, and the transverse factor is at most 1), so the instance's scale is the power
-// of two that maps |q| max(w) / dV to at most 2^20.  Each contribution is split into its
-// nearest integer H and the remainder rounded to 2^-16, L, and both are added with native
-// 32-bit integer shared atomics.  A cell receives at most one contribution per particle,
-// and the tile is folded into global memory at least every 2047 particles, so
-// |sum H| < 2^31 and |sum L| < 2^26: no overflow, a resolution of 2^-36 of the bound, and a
-// sum that does not depend on the order of the additions.  The float -> integer rounding
-// adds 1.5 * 2^23 (exact for |x| <= 2^22).
-// DoubleAcc (FP64 mode): FP64 shared atomics.
+// ChunkAcc (FP32 mode): one 32-bit integer shared atomic per contribution, block floating
+// point per chunk of 256 particles and per component.  The running sum of the Esirkepov
+// weight changes along an axis is the charge flux through a cell face, at most |d| for a
+// displacement d (its rate is the next lower-order spline, whose peak is 1), and the
+// transverse factor is the time average of a product of the moving weights, at most
+// S_max^2 (S_max in 2D3V; S_max, the shape's peak, is 1 for order 1 and 3/4 for order 2):
+// any contribution to component a is at most S_max^2 |f_a d_a| (S_max |f_a d_a| in the
+// 2D3V plane, S_max^2 |f_y| for its out-of-plane current, f_y carrying v_y; |d_a| is
+// widened by 2^-18 for the rounding of the node-crossing weight changes).  Each chunk takes, per component, the
+// scale that maps the chunk's largest such bound to 0.999 2^22: every contribution then
+// stays within 2^22, the range in which the rounding below is exact, and 256
+// contributions to one entry stay below 2^30, so the integer sums cannot overflow.  Each
+// contribution is rounded to the nearest integer (one FMA against 1.5 * 2^23, whose float
+// spacing is 1 up to 2^24, and an integer subtraction of that constant's bits) and added
+// to the
+// chunk accumulator A; after the chunk every thread folds the entries it owns into an
+// FP32 tile, T += A / scale, A = 0.  The resolution is 2^-22 of the chunk's largest
+// contribution bound per component, comparable with FP32 accumulation of a cell holding
+// a few contributions, and the chunk sums do not depend on the order of the additions.
+// DoubleAcc (FP64 mode): FP64 shared atomics, zero contributions skipped.
 // ------------------------------------------------------------------------------------
-struct FixedAcc {
-    // 3D: zero adds are cheaper than the branch; the 2D3V loops (up to 16 particles per
-    // cell in a small window) keep skipping them, where the adds would contend
-    static constexpr bool kSkipZero = false;
-    int *H;
-    int *L;
+struct ChunkAcc {
+    static constexpr bool kSkipZero = false;  // 3D: zero adds cost less than the branch
+    int *A;
+    // adds round(a * b)
+    __device__ __forceinline__ void add_prod(int idx, float a, float b) const
+    {
+        const float y = __fmaf_rn(a, b, 12582912.0f);  // 1.5 * 2^23 + a b, rounded to an integer
+        atomicAdd(A + idx, __float_as_int(y) - 0x4B400000);
+    }
     __device__ __forceinline__ void add(int idx, float x) const
     {
-        const float M = 12582912.0f;  // 1.5 * 2^23
-        const float y = __fadd_rn(x, M);
-        const int hi = __float_as_int(y) - 0x4B400000;
-        const float r = __fsub_rn(x, __fsub_rn(y, M));   // exact, |r| <= 1/2
-        const float z = __fmaf_rn(r, 65536.0f, M);
-        const int lo = __float_as_int(z) - 0x4B400000;
-        // unconditional: a zero add costs less than the branches around it
-        atomicAdd(H + idx, hi);
-        atomicAdd(L + idx, lo);
+        const float y = __fadd_rn(x, 12582912.0f);
+        atomicAdd(A + idx, __float_as_int(y) - 0x4B400000);
     }
 };
 
@@ -150,23 +192,113 @@ struct DoubleAcc {
     static constexpr bool kSkipZero = true;
     double *J;
     __device__ __forceinline__ void add(int idx, double x) const { atomicAdd(J + idx, x); }
+    __device__ __forceinline__ void add_prod(int idx, double a, double b) const { atomicAdd(J + idx, a * b); }
 };
+
+template <typename R, typename Acc>
+__device__ __forceinline__ void acc_put(const Acc &acc, int idx, R a, R b)
+{
+    if (Acc::kSkipZero) {
+        const R v = a * b;
+        if (v != R(0)) acc.add(idx, v);
+    } else {
+        acc.add_prod(idx, a, b);
+    }
+}
 
 // ------------------------------------------------------------------------------------
 // Esirkepov charge-conserving deposit of one particle into the shared J tile (three
-// components of jvol cells each, tile origin at node jlo).  With S0, DS the old shape and
-// its change per axis, in 3D
+// components of jvol cells each).  With S0, DS the old shape and its change per axis on a
+// common window, in 3D
 //   Wx = DSx (S0y S0z + DSy S0z / 2 + S0y DSz / 2 + DSy DSz / 3)   (cyclic for y, z),
 //   Jx(i+1/2) - Jx(i-1/2) = f_x Wx(i),  f_x = -(q w / dV) dx / dt,
-// summed along x from zero at the window start; in 2D3V (x-z plane) Wx = DSx (S0z + DSz/2),
-// Wz = DSz (S0x + DSx/2) and the out-of-plane Jy = f_y' (S0x S0z + DSx S0z / 2 +
-// S0x DSz / 2 + DSx DSz / 3) with f_y' = (q w / dV) v_y.  The loops run over the whole
-// window: entries beyond the nodes a particle touches are exactly zero (the running sum
-// ends at exactly zero too).  The FP64 accumulator and the 2D3V loops skip zero entries;
-// the 3D FP32 fixed-point accumulator adds them (cheaper than the branch; the window lies
-// inside the J tile).
+// summed along x from zero at the window start.  The transverse factor is evaluated as
+// S0a (S0b + DSb / 2) + DSa (S0b / 2 + DSb / 3) (two products per window row), and the
+// running sums along the component's own axis, times f, are formed once per particle.
+//
+// WX, WY, WZ: window extents covered (each ORD + 1 or ORD + 2).  A particle that keeps
+// its nodes along an axis has ORD + 1 non-zero entries there (the entry beyond is zero
+// and so is the running sum at the window's last entry), so a warp whose particles all
+// keep their x and y nodes can cover ORD + 1 entries along x and y and lose nothing.
 // ------------------------------------------------------------------------------------
-template <int ND, int ORD, bool kDisp, typename R, typename Acc>
+template <int WX, int WY, int WZ, typename R, typename Acc>
+__device__ __forceinline__ void esirkepov3d(const R *S0x, const R *DSx, const R *S0y, const R *DSy, const R *S0z,
+                                            const R *DSz, R fx, R fy, R fz, int base, int jd0, int jd01, int jvol,
+                                            const Acc &acc)
+{
+    const R half = R(0.5), third = R(1.0 / 3.0);
+    R Ay[WY], Cy[WY], Az[WZ], Cz[WZ];
+#pragma unroll
+    for (int m = 0; m < WY; ++m) {
+        Ay[m] = S0y[m] + half * DSy[m];
+        Cy[m] = half * S0y[m] + third * DSy[m];
+    }
+#pragma unroll
+    for (int m = 0; m < WZ; ++m) {
+        Az[m] = S0z[m] + half * DSz[m];
+        Cz[m] = half * S0z[m] + third * DSz[m];
+    }
+    R rx[WX - 1], ry[WY - 1], rz[WZ - 1];
+    {
+        R run = R(0);
+#pragma unroll
+        for (int i = 0; i < WX - 1; ++i) {
+            run += DSx[i];
+            rx[i] = fx * run;
+        }
+        run = R(0);
+#pragma unroll
+        for (int j = 0; j < WY - 1; ++j) {
+            run += DSy[j];
+            ry[j] = fy * run;
+        }
+        run = R(0);
+#pragma unroll
+        for (int k = 0; k < WZ - 1; ++k) {
+            run += DSz[k];
+            rz[k] = fz * run;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < WZ; ++k) {
+#pragma unroll
+        for (int j = 0; j < WY; ++j) {
+            const R Y = S0y[j] * Az[k] + DSy[j] * Cz[k];
+            const int row = base + jd0 * j + jd01 * k;
+#pragma unroll
+            for (int i = 0; i < WX - 1; ++i) acc_put<R>(acc, row + i, Y, rx[i]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < WZ; ++k) {
+#pragma unroll
+        for (int i = 0; i < WX; ++i) {
+            const R X = S0x[i] * Az[k] + DSx[i] * Cz[k];
+            const int col = jvol + base + i + jd01 * k;
+#pragma unroll
+            for (int j = 0; j < WY - 1; ++j) acc_put<R>(acc, col + jd0 * j, X, ry[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < WY; ++j) {
+#pragma unroll
+        for (int i = 0; i < WX; ++i) {
+            const R X = S0x[i] * Ay[j] + DSx[i] * Cy[j];
+            const int col = 2 * jvol + base + i + jd0 * j;
+#pragma unroll
+            for (int k = 0; k < WZ - 1; ++k) acc_put<R>(acc, col + jd01 * k, X, rz[k]);
+        }
+    }
+}
+
+// The deposit of one particle; every lane of the warp calls it (a lane without a particle
+// passes f = 0 and a position inside the tile).  In 2D3V (x-z plane) Wx = DSx (S0z +
+// DSz/2), Wz = DSz (S0x + DSx/2) and the out-of-plane Jy = f_y' (S0x S0z + DSx S0z / 2 +
+// S0x DSz / 2 + DSx DSz / 3) with f_y' = (q w / dV) v_y; the 2D3V loops skip zero
+// contributions (up to 16 particles per cell contend there).  kNarrow (3D): the warp
+// covers ORD + 1 entries along x and y when none of its particles changes its x or y
+// nodes (one vote per warp), ORD + 2 otherwise.
+template <int ND, int ORD, bool kDisp, bool kNarrow, typename R, typename Acc>
 __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3], const int l1[3], const R o1[3],
                                                   const R disp[3], R fx, R fy, R fz, int jlo, int jlo_y, int jd0,
                                                   int jd01, int jvol, const Acc &acc)
@@ -180,62 +312,10 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
     if (ND == 3) {
         const int wsy = shape_window<ORD, kDisp>(l0[1], o0[1], l1[1], o1[1], disp[1], S0y, DSy, nwy) - jlo_y;
         const int base = wsx + jd0 * wsy + jd01 * wsz;
-        // the transverse factor S0a S0b + DSa S0b / 2 + S0a DSb / 2 + DSa DSb / 3 as
-        // S0a (S0b + DSb / 2) + DSa (S0b / 2 + DSb / 3): per axis b two vectors, then two
-        // operations per window row
-        R Ay[W], Cy[W], Az[W], Cz[W];
-#pragma unroll
-        for (int m = 0; m < W; ++m) {
-            Ay[m] = S0y[m] + half * DSy[m];
-            Cy[m] = half * S0y[m] + third * DSy[m];
-            Az[m] = S0z[m] + half * DSz[m];
-            Cz[m] = half * S0z[m] + third * DSz[m];
-        }
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                const R Y = S0y[j] * Az[k] + DSy[j] * Cz[k];
-                const R fY = fx * Y;
-                R run = R(0);
-#pragma unroll
-                for (int i = 0; i < W - 1; ++i) {
-                    run += DSx[i];
-                    const R v = fY * run;
-                    if (!Acc::kSkipZero || v != R(0)) acc.add(base + i + jd0 * j + jd01 * k, v);
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                const R X = S0x[i] * Az[k] + DSx[i] * Cz[k];
-                const R fX = fy * X;
-                R run = R(0);
-#pragma unroll
-                for (int j = 0; j < W - 1; ++j) {
-                    run += DSy[j];
-                    const R v = fX * run;
-                    if (!Acc::kSkipZero || v != R(0)) acc.add(jvol + base + i + jd0 * j + jd01 * k, v);
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                const R X = S0x[i] * Ay[j] + DSx[i] * Cy[j];
-                const R fX = fz * X;
-                R run = R(0);
-#pragma unroll
-                for (int k = 0; k < W - 1; ++k) {
-                    run += DSz[k];
-                    const R v = fX * run;
-                    if (!Acc::kSkipZero || v != R(0)) acc.add(2 * jvol + base + i + jd0 * j + jd01 * k, v);
-                }
-            }
-        }
+        if (kNarrow && !__any_sync(0xffffffffu, nwx > ORD + 1 || nwy > ORD + 1))
+            esirkepov3d<ORD + 1, ORD + 1, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
+        else
+            esirkepov3d<W, W, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
     } else {
         // fy carries the out-of-plane factor (q w / dV) v_y here
         const int base = wsx + jd01 * wsz;

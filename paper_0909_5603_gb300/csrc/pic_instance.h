@@ -59,7 +59,7 @@ constexpr int kErrCapacity = 8;     // more particles than the buffers hold
 template <typename R>
 struct StepCoef {
     R h;          // q dt / (2 m)
-    R qdv;        // q / dV, times the fixed-point current scale in FP32 mode
+    R qdv;        // q / dV
     R jf[3];      // dx_a / dt
     R dtdx[3];    // dt / dx_a
     R half_dt;    // dt / 2
@@ -113,7 +113,6 @@ struct InstDev {
     const void *damp[3];      // absorbing-layer factor per cell index along each axis
                               // (working precision; null on periodic / inactive axes)
     FastDiv div_n0, div_n1;   // cell index -> (i, j, k)
-    float jscale, jinv;       // FP32 fixed-point current: scale (a power of two) and 1/scale
     // ion background of a lab-frame plasma load: lab-stationary ions, i.e. in this frame
     // a rigid density gamma_b n0 p(gamma_b (z + beta_b t)) of charge -q on [0, Lz) at t = 0
     int ion;            // 0: none
