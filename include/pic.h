@@ -223,20 +223,31 @@ pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, cons
 /* Overwrites one field component (PIC_EX .. PIC_JZ) with count = n0 n1 n2 host values. */
 pic_status pic_set_field(pic_ctx *ctx, int comp, const double *host, size_t count);
 
-/* Advances n >= 0 steps (all phases).  Asynchronous; the step is replayed from a CUDA
- * graph captured on first use unless profiling is on.  PIC_ERR_STATE before any load. */
+/* Advances n >= 0 steps of the relativistic PIC loop in the boosted frame (Sec. 2: field
+ * gather, Vay or Boris push, charge-conserving current deposit, binomial filtering of the
+ * current, Yee Maxwell update; plus the ion background's current, the stations, the
+ * antenna and the injection plane when set).  Asynchronous; the step is replayed from a
+ * CUDA graph captured on first use unless profiling is on.  A device error of a step
+ * (PIC_ERR_PARTICLE_SPEED, PIC_ERR_TIMEOUT, ...) is reported by the next synchronising
+ * call.  PIC_ERR_STATE before any load; PIC_ERR_ARG for n < 0. */
 pic_status pic_step(pic_ctx *ctx, int n);
 
 /* Runs the selected phases (PIC_PHASE_* mask) of one step, for unit testing a phase in
  * isolation; a full step is PIC_PHASE_ALL. */
 pic_status pic_run_phases(pic_ctx *ctx, int phase_mask);
 
-/* Copies one component (PIC_EX .. PIC_JZ, PIC_RHO, PIC_DIVE) into host_out[count],
- * count >= n0 n1 n2.  J is the current used by the last Maxwell update (after filter). */
+/* Copies one component (PIC_EX .. PIC_JZ, PIC_RHO, PIC_DIVE) of the boosted-frame grid
+ * (Sec. 2: the fields the boosted-frame PIC loop evolves, before any transform back to
+ * the lab, which the stations do) into host_out[count], count >= n0 n1 n2, FP64, in the
+ * staggered layout above.  J is the current used by the last Maxwell update (after the
+ * filter).  PIC_RHO deposits the particles' charge with their shape (plus the ion
+ * background) into per-context FP64 memory; PIC_DIVE is the node divergence of E.
+ * Synchronises; PIC_ERR_ARG for an unknown component or a short buffer. */
 pic_status pic_get_field(pic_ctx *ctx, int comp, double *host_out, size_t count);
 
-/* Copies ncomp components (as for pic_get_field) into host_out[ncomp][n2][n1][n0],
- * count >= ncomp n0 n1 n2; comps[i] as pic_get_field.  Synchronises. */
+/* Copies ncomp components (as for pic_get_field, Sec. 2) into
+ * host_out[ncomp][n2][n1][n0], count >= ncomp n0 n1 n2; comps[i] as pic_get_field.
+ * Synchronises; PIC_ERR_ARG for an unknown component, ncomp < 1 or a short buffer. */
 pic_status pic_get_fields(pic_ctx *ctx, const int *comps, int ncomp, double *host_out, size_t count);
 
 /* Gauss-law residual on the nodes: *max_abs = max |div E - rho| and, when rms is not NULL,
@@ -250,12 +261,23 @@ pic_status pic_get_gauss_residual(pic_ctx *ctx, double *max_abs, double *rms);
 /* Number of live particles (synchronises). */
 pic_status pic_num_particles(pic_ctx *ctx, int64_t *n_out);
 
-/* Copies the live particles, in canonical order, into host arrays with room for cap
- * particles (any pointer may be NULL to skip that array); *n_out = count. */
+/* Copies the live macro-particles of the boosted frame (Sec. 2: the plasma and beam
+ * particles the PIC loop pushes), in canonical order, into host arrays with room for cap
+ * particles (any pointer may be NULL to skip that array); *n_out = count.  Layout as in
+ * the conventions above (cell int32, off3/u3 3 doubles per particle, w, id int32 -- ids
+ * are int32 like the cell index: a context holds fewer than 2^31 particles).
+ * Synchronises; PIC_ERR_ARG when cap is below the count (*n_out still set).  The first
+ * call allocates a device staging buffer (9 values per particle of capacity) that the
+ * context keeps. */
 pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off3, double *u3, double *w,
                              int32_t *id, int64_t cap, int64_t *n_out);
 
-/* FP64 global diagnostics (computed on the device, then copied). */
+/* FP64 global diagnostics of the boosted frame, computed on the device and copied to
+ * *out: field energy sum (E^2 + B^2) dV / 2, particles' kinetic energy sum w (gamma - 1)
+ * m, total charge, live and removed particle counts, step and time.  The paper judges
+ * its runs by the energy they reach (Sec. 3.1) and the boosted-frame instability by the
+ * growth of the field (Sec. 2); error_flags holds the sticky device error word.
+ * Synchronises. */
 pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out);
 
 /* Profiling: when on, pic_step launches each kernel directly (no graph) between CUDA
@@ -267,8 +289,10 @@ pic_status pic_get_timings(pic_ctx *ctx, pic_timings *out);
 /* Waits for all work of ctx; reports a sticky device error. */
 pic_status pic_synchronize(pic_ctx *ctx);
 
-/* Groups n >= 1 instances created with identical ndim, shape order, precision, pusher,
- * field solver, tile, threads and device into a batch whose pic_step advances all of them in one
+/* Batching of independent boosted-frame instances (the paper has no counterpart; it
+ * serves scans over the boost, the parameter Sec. 1 ties the speed-up to).  Groups n >= 1
+ * instances created with identical ndim, shape order, precision, pusher, field solver,
+ * tile, threads and device into a batch whose pic_step advances all of them in one
  * launch per phase (one flattened tile list over all instances), captured in one graph.
  * The members keep their own memory and stay readable with the getters; destroy the
  * batch before its members.  Only pic_step, pic_run_phases, pic_synchronize,

@@ -19,8 +19,8 @@
  *   Yee FDTD (Yee 1966), charge-conserving current deposition (Esirkepov, Comput. Phys.
  *   Commun. 135, 144 (2001)), B-spline shape factors of order 1 and 2, SplitMix64
  *   (Steele, Lea, Flood, OOPSLA 2014).
- * Readings where the paper is silent (absorbing layer, crossing rule, seeds, 2D3V
- * geometry) are the ones listed in the design notes; each is marked "reading" below.
+ * Where the paper is silent (absorbing layer, crossing rule, seeds, 2D3V geometry) the
+ * choice taken is stated where it is used and marked "reading" below.
  *
  * Parity pins: every public function here is pinned by a closed form, invariant or
  * brute-force check in tests/test_oracle_*.py.
@@ -91,7 +91,8 @@ double orc_shape(int order, double x)
  *   u^{n+1/2} = s [u' + (u'.t) t + u' x t].
  * Where sigma < 0 the root is taken in its cancellation-free form
  *   gamma^2 = 2 (tau^2 + u*^2) / (sqrt(sigma^2 + 4 (tau^2 + u*^2)) - sigma)
- * (algebraically identical; reading of the design notes).
+ * (algebraically the same root; a reading: the paper gives no formula, and this form
+ * avoids the cancellation of sigma + sqrt(...) when sigma < 0).
  * ---------------------------------------------------------------------------------- */
 void orc_push_vay(double u[3], const double E[3], const double B[3], double q_over_m, double dt)
 {
