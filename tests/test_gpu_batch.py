@@ -82,10 +82,13 @@ def errors(a, b):
 
 
 def test_scan_batch_fp32_against_oracle():
-    """After 100 steps each instance is within 1e-5 of the FP64 oracle, or -- where the
-    coarse boosted grid is numerically unstable and amplifies every rounding difference
-    (fields grown 10-100x from the laser's) -- within 8x of the floor that FP32 storage
-    alone sets: the FP64 oracle with its state rounded to FP32 after every step."""
+    """After 100 steps each instance is within 1e-5 of the FP64 oracle (normwise, per field
+    and for the momenta).  The one exception is a reading: an instance whose coarse
+    boosted grid is numerically unstable (max |E| grown more than 3x above the laser's
+    amplitude; the paper's Sec. 2 instability) amplifies every rounding difference, and
+    there a field may exceed 1e-5 if it stays within 8x of the floor that FP32 storage
+    alone sets: the FP64 oracle with its state rounded to FP32 after every step.  The
+    instances and fields that use the exception are printed."""
     ds = [small_instance(i, n) for i, n in CASES]
     sims = [make_gpu(d, FP32) for d in ds]
     batch = pic.Batch(sims)
@@ -105,10 +108,16 @@ def test_scan_batch_fp32_against_oracle():
             d["gamma_boost"] * (1 + np.sqrt(1 - 1 / d["gamma_boost"] ** 2))))
         print(f"gamma_b {d['gamma_boost']:.1f} n {d['n'][0]} ppc {d['plasma'][3]} max|E|/laser {growth:.1f}: "
               + " ".join(f"{k} {v:.1e} (floor {floor[k]:.1e})" for k, v in gpu.items()))
-        rows.append((d["gamma_boost"], gpu, floor))
-    for gb, gpu, floor in rows:
+        rows.append((d, gpu, floor, growth))
+    over = []
+    for d, gpu, floor, growth in rows:
         for k, v in gpu.items():
-            assert v <= max(1e-5, 8 * floor[k]), (gb, k, v, floor[k])
+            if v <= 1e-5:
+                continue
+            over.append(f"gamma_b {d['gamma_boost']:.1f} n {d['n'][0]} {k} {v:.2e} floor {floor[k]:.2e} "
+                        f"growth {growth:.1f}")
+            assert growth > 3.0 and v <= 8 * floor[k], over[-1]
+    print("above 1e-5 (unstable instances, within 8x the FP32 storage floor):", over or "none")
 
 
 def test_scan_batch_fp64_equals_instances_stepped_alone():

@@ -99,26 +99,36 @@ def test_lwfa_stage_fp32_100_steps(gb):
     """The boosted LWFA stage (ramped plasma n/n_c = 1/900 with its ions, a0 = 2 laser,
     order 2, 3-pass filter, Vay, absorbing box) downscaled to 16 x 16 x 96 cells with a
     2-period laser centred in the box: FP32 storage with the FP64 gamma solve against the
-    FP64 oracle after 100 steps, every field and the particles within 1e-5 (normwise).
-    The boosts are those of the precision sweep at scale (bench.py --precision-sweep)."""
+    FP64 oracle after 50 and 100 steps, every field and the particles within 1e-5
+    (normwise), at every boost.  One reading: at gamma_b = 100 this coarse grid is
+    numerically unstable (fields grow about 20x by step 50, the paper's Sec. 2
+    instability) and the error passes through a transient near step 50; there the step-50
+    bar is 3e-5, and 1e-5 holds again at step 100.  The boosts are those of the precision
+    sweep at scale (bench.py --precision-sweep)."""
     w = synth.lwfa_stage((16, 16, 96), gb, 2)
     lz = w["n"][2] * w["dx"][2]
     doppler = gb * (1 + np.sqrt(1 - 1 / gb ** 2))
     laser = (2.0, 1.0, 20.0, 2.0, 0.5 * lz / doppler)
     g, o = pair(3, w["n"], (1, 1, 1), w["dx"], w["dt"], gb, FP32, passes=3, absorb=4)
     load(g, o, gb, laser, w["plasma"])
-    errs = {}
-    for block in (10, 40, 50):
+    report = {}
+    for block, step in ((10, 10), (40, 50), (50, 100)):
         g.step(block)
         o.step(block)
-    for c in COMPS + JCOMPS:
-        errs[NAMES[c]] = rel2(g.get_field(c), o.get_field(c))
-    pg, po = g.get_particles(), o.get_particles()
-    # a particle at the -z face may leave in one precision and not yet in the other
-    common, ig, io = np.intersect1d(pg["id"], po["id"], return_indices=True)
-    assert max(pg["id"].size, po["id"].size) - common.size <= 1e-4 * po["id"].size
-    errs["u"] = rel2(pg["u"][ig], po["u"][io])
-    print(f"gamma_b {gb}: FP32 vs FP64 oracle after 100 steps (normwise) "
-          + " ".join(f"{k} {v:.2e}" for k, v in errs.items()))
-    for k, v in errs.items():
-        assert v <= 1e-5, (k, v)
+        if step not in (50, 100):
+            continue
+        errs = {}
+        for c in COMPS + JCOMPS:
+            errs[NAMES[c]] = rel2(g.get_field(c), o.get_field(c))
+        pg, po = g.get_particles(), o.get_particles()
+        # a particle at the -z face may leave in one precision and not yet in the other
+        common, ig, io = np.intersect1d(pg["id"], po["id"], return_indices=True)
+        assert max(pg["id"].size, po["id"].size) - common.size <= 1e-4 * po["id"].size
+        errs["u"] = rel2(pg["u"][ig], po["u"][io])
+        print(f"gamma_b {gb}: FP32 vs FP64 oracle after {step} steps (normwise) "
+              + " ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+        report[step] = errs
+    for step, errs in report.items():
+        bar = 3e-5 if (gb == 100.0 and step == 50) else 1e-5
+        for k, v in errs.items():
+            assert v <= bar, (step, k, v)
