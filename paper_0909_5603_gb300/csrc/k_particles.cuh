@@ -487,7 +487,20 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
         reinterpret_cast<int4 *>(sJraw)[e] = make_int4(0, 0, 0, 0);
     for (int e = tid; e < 2 * kNW * kBuckets; e += kNT) (&s_cnt[0][0][0])[e] = 0;
     if (tid < kBuckets) s_run[tid] = 0;
-    build_sources(I, in, tx, ty, tz, S);  // ends with __syncthreads
+    // the tile's source table: its precomputed record (one coalesced read), or built here
+    // when the record overflowed
+    {
+        const int *rec = I.srcrec + (size_t)t * kSrcRec;
+        if (tid < kSrcRec) {
+            const int v = rec[tid];
+            if (tid == 0) S.count = v;
+            else if (tid == 1) S.nsub = v;
+            else if (tid >= kRecSlot && tid < kRecPos) S.sub_slot[tid - kRecSlot] = v;
+            else if (tid >= kRecPos && tid < kRecPos + kSubCache) S.sub_pos[tid - kRecPos] = v;
+        }
+        __syncthreads();
+        if (S.nsub < 0) build_sources(I, in, tx, ty, tz, S);  // ends with __syncthreads
+    }
     const bool ok = mbar_wait_bounded(&bar, 0, kWaitCycles);
     if (!__syncthreads_and(ok ? 1 : 0)) {
         if (tid == 0) {

@@ -458,8 +458,9 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     c->d_start_ptr = (int **)dalloc(c, sizeof(int *));
     c->d_pencil = (long long *)dalloc(c, 6 * sizeof(long long));
     h.ion_face = dalloc(c, sizeof(double) * (size_t)c->n[2]);
+    h.srcrec = (int *)dalloc(c, sizeof(int) * (size_t)h.ntiles * kSrcRec);
     if (!F || !small || !tiles || !tm || !c->d_inst || !c->d_tile_start || !c->d_cell_start || !c->d_dense || !c->d_sums ||
-        !c->d_start || !c->d_start_ptr || !c->d_pencil || !h.ion_face) {
+        !c->d_start || !c->d_start_ptr || !c->d_pencil || !h.ion_face || !h.srcrec) {
         dfree_all(c);
         delete c;
         return fail(nullptr, PIC_ERR_OOM, "device allocation failed (%zu bytes of fields)", fbytes);
@@ -1157,13 +1158,14 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
         tm.end(4);
         tm.begin(1);
         CUDA_OR_FAIL(c, launch_scan(L, 0, nullptr, c->stream));
+        CUDA_OR_FAIL(c, launch_tile_sources(L, c->stream));
         tm.end(1);
         tm.begin(0);
         bool inj = c->h.inj_id0 != INT_MAX;
         for (auto m : c->members) inj = inj || m->h.inj_id0 != INT_MAX;
         CUDA_OR_FAIL(c, launch_particles(c->ndim, c->order, fp64, c->opt.pusher, inj, L, c->smem, c->stream));
         tm.end(0);
-        launches += 2;
+        launches += 3;
     }
     int filtered = 0;
     if ((mask & PIC_PHASE_FILTER) && c->max_sweeps > 0) {

@@ -19,6 +19,13 @@ constexpr int kDead = 27;       // bucket of particles removed at absorbing face
 constexpr int kBuckets = 28;    // 27 directions + dead
 constexpr int kPre = 29;        // per chunk: exclusive prefix of the 28 buckets + size
 constexpr int kCenterDir = 13;  // (0,0,0)
+// Per-tile source record precomputed ahead of the particle kernel (k_tile_sources): the
+// tile's particle count, its number of non-empty (source, chunk) sub-ranges (-1 when more
+// than kSubCache) and their first destination slots and buffer positions.
+constexpr int kSubCache = 64;
+constexpr int kRecSlot = 4;                            // sub_slot[kSubCache + 1] from here
+constexpr int kRecPos = kRecSlot + kSubCache + 1;      // sub_pos[kSubCache] from here
+constexpr int kSrcRec = (kRecPos + kSubCache + 3) / 4 * 4;  // ints per tile
 
 // Division of 0 <= x < 2^31 by a fixed divisor d >= 1 without a divide instruction
 // (Granlund & Montgomery, "Division by invariant integers using multiplication", 1994,
@@ -104,6 +111,7 @@ struct InstDev {
     int *chunk_cb[2];   // [chunk_cap * kBuckets] count of each bucket in earlier chunks of the tile
     int *tot[2];        // [ntiles * kBuckets] bucket totals of each tile
     int *pop;           // [ntiles] particles in each tile at the step boundary
+    int *srcrec;        // [ntiles * kSrcRec] source records of the coming particle phase
     int *cur;           // device parity: which layout/buffer holds the current state
     int *jsel;          // which J array (0: J, 1: Jt) holds the filtered current
     int *err;           // sticky error word

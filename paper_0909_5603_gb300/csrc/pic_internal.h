@@ -63,6 +63,8 @@ cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, bool inj
 int particle_chunk();
 int particle_threads();
 cudaError_t launch_scan(const Launch &L, int mode, int *const *dst, cudaStream_t s);
+// per-tile source records of the coming particle phase (after the scan of mode 0)
+cudaError_t launch_tile_sources(const Launch &L, cudaStream_t s);
 // off, u, w: staging in the storage precision (double or float)
 cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, int *cell, void *off, void *u,
                            void *w, int *id, cudaStream_t s);

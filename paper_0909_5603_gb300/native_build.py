@@ -53,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             for f in [ex.submit(_compile, s, o, verbose) for s, o in jobs]:
                 f.result()
-    if jobs or not os.path.exists(LIB):
+    if jobs or not os.path.exists(LIB) or max(os.path.getmtime(o) for o in objs) > os.path.getmtime(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
         if verbose:
