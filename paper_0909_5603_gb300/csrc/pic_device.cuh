@@ -360,8 +360,11 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
 //           = 2 (tau^2 + u*^2) / (sqrt(...) - sigma)            (sigma < 0, same value),
 //   t = tau / gamma,  s = 1 / (1 + t^2),  u_new = s (u' + (u'.t) t + u' x t).
 // FP32 form: sigma is the one quantity that cancels at large gamma (gamma'^2 ~ tau^2), so
-// gamma'^2, tau^2 and their difference are formed in FP64 from the FP32 operands; the
-// roots are FP32, taken on the cancellation-free branch.
+// where it can cancel gamma'^2, tau^2 and their difference are formed in FP64 from the
+// FP32 operands; the roots are FP32, taken on the cancellation-free branch.  Where it
+// cannot -- tau^2 < gamma'^2 / 4 for every particle of the warp (one vote), so that
+// sigma > 3 gamma'^2 / 4 and its FP32 difference is within a few ulp of sigma -- the
+// difference is taken in FP32: GB300's FP64 rate is a small fraction of its FP32 one.
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ void push_vay(float u[3], const float E[3], const float B[3], float h)
 {
@@ -373,10 +376,18 @@ __device__ __forceinline__ void push_vay(float u[3], const float E[3], const flo
     const float up2 = u[2] + 2.f * h * E[2] + h * (v0 * B[1] - v1 * B[0]);
     const float t0 = h * B[0], t1 = h * B[1], t2 = h * B[2];
     const float ustar = up0 * t0 + up1 * t1 + up2 * t2;
-    const double gp2 = 1.0 + (double)up0 * up0 + (double)up1 * up1 + (double)up2 * up2;
-    const double tau2d = (double)t0 * t0 + (double)t1 * t1 + (double)t2 * t2;
-    const float sigma = (float)(gp2 - tau2d);
-    const float tau2 = (float)tau2d;
+    const float gp2f = __fmaf_rn(up0, up0, __fmaf_rn(up1, up1, __fmaf_rn(up2, up2, 1.f)));
+    const float tau2f = __fmaf_rn(t0, t0, __fmaf_rn(t1, t1, t2 * t2));
+    float sigma, tau2;
+    if (__all_sync(__activemask(), tau2f < 0.25f * gp2f)) {
+        sigma = gp2f - tau2f;
+        tau2 = tau2f;
+    } else {
+        const double gp2 = 1.0 + (double)up0 * up0 + (double)up1 * up1 + (double)up2 * up2;
+        const double tau2d = (double)t0 * t0 + (double)t1 * t1 + (double)t2 * t2;
+        sigma = (float)(gp2 - tau2d);
+        tau2 = (float)tau2d;
+    }
     const float q4 = tau2 + ustar * ustar;
     const float root = sqrtf(sigma * sigma + 4.f * q4);
     const float g2 = sigma >= 0.f ? 0.5f * (sigma + root) : 2.f * q4 / (root - sigma);

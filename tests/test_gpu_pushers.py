@@ -45,8 +45,9 @@ def momenta(s):
 
 @pytest.mark.parametrize("prec,tol", [(FP32, 2e-7), (FP64, 1e-14)])
 def test_force_free_vay_vs_boris_up_to_gamma_1e4(prec, tol):
-    """E = -v x B: Vay leaves u unchanged at every gamma (to the storage precision, thanks
-    to the FP64 sigma in FP32 mode); Boris leaves the kick h^3 B^3 beta^2 / gamma^2."""
+    """E = -v x B: Vay leaves u unchanged at every gamma (to the storage precision; here
+    tau^2 << gamma'^2, so FP32 mode forms sigma in FP32); Boris leaves the kick
+    h^3 B^3 beta^2 / gamma^2."""
     gammas = np.array([10.0, 100.0, 1e3, 1e4])
     uz = np.sqrt(gammas ** 2 - 1)
     beta = uz / gammas
@@ -133,3 +134,25 @@ def test_exb_drift_gpu():
     d -= np.round(d / n) * n
     vmean = d / (nsteps * dt)
     assert np.linalg.norm(vmean - vd) < 5e-3 * np.linalg.norm(vd)
+
+
+def test_vay_cancelling_sigma_fp32_matches_fp64_solve():
+    """sigma = gamma'^2 - tau^2 cancels when |h B| ~ gamma': FP32 mode takes the FP64
+    difference there (one warp vote: any particle with tau^2 >= gamma'^2 / 4).  A warp of
+    particles around tau^2 = gamma'^2 (ratios 0.25 .. 4) in a uniform strong B: one push
+    in FP32 storage against the FP64 Vay push of the same FP32 inputs (the oracle's),
+    within 2e-6 of |u| (a 90-degree rotation per step, a few dozen FP32 operations)."""
+    import oracle
+    oracle.build()
+    Bm = 400.0  # tau = h B = -100 at dt = 0.5, q/m = -1
+    ratios = np.geomspace(0.25, 4.0, 32)
+    uz = np.float32(100.0 * np.sqrt(ratios)).astype(np.float64)  # gamma'^2 ~ uz^2 vs tau^2 = 1e4
+    u0 = np.stack([np.zeros_like(uz), 0.3 * uz, uz], axis=1).astype(np.float32).astype(np.float64)
+    s = box(FP32, pic.PIC_PUSHER_VAY)
+    uniform(s, (0.0, 0.0, 0.0), (Bm, 0.0, 0.0))
+    load(s, u0)
+    s.run_phases(pic.PIC_PHASE_PARTICLES)
+    got = momenta(s)
+    for k in range(len(uz)):
+        ref = np.array(oracle.push_vay(u0[k].copy(), np.zeros(3), np.array([Bm, 0.0, 0.0]), -1.0, 0.5))
+        assert np.abs(got[k] - ref).max() <= 2e-6 * np.linalg.norm(ref), (k, got[k], ref)
