@@ -9,8 +9,12 @@ ABI with host buffers.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank advances its own replica of the workload (the step
-has no exchange in this build); rank 0 prints the aggregate over ranks.
+Under torchrun (N > 1) the one 128 x 128 x 1024 instance is split along z into N slabs,
+one per rank (paper_0909_5603_gb300.slab: ghost planes of J, E and B exchanged every
+step, particles moved every MIGRATE_EVERY steps, all staged through host memory over a
+gloo group); rank 0 prints particle-steps/s of the whole instance over the slowest
+rank's time (strong scaling).  --replicas instead runs N independent copies (weak
+scaling, no exchange).
 """
 from __future__ import annotations
 
@@ -384,6 +388,81 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+MIGRATE_EVERY = 8
+
+
+def run_slabs(args, rank, world):
+    """The instance split into `world` z slabs (one per rank); every rank loads the whole
+    instance once, keeps its slab and frees the rest."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_0909_5603_gb300 as pic
+    from paper_0909_5603_gb300 import slab as S
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    pic.build()
+    w = workload(args.nz)
+    n = w["n"]
+    kw = dict(bc=(1, 1, 1), dx=w["dx"], dt=w["dt"], gamma_boost=GAMMA_B, order=2, precision=pic.PIC_PREC_FP32,
+              pusher=pic.PIC_PUSHER_VAY, filter_passes=3, tile=(8, 8, 8), track_ids=False)
+    whole = pic.Simulation(3, n, **kw)
+    whole.load_lab_frame(laser=w["laser"], plasma=w["plasma"])
+    n_whole = whole.num_particles()
+    slabs = S.plan(n[2], world, False, ghost=S.ghost_planes(3, MIGRATE_EVERY))
+    sim = S.split_gpu(whole, slabs, [rank], **kw)[rank]
+    del whole
+    torch.cuda.empty_cache()
+    group = dist.new_group(backend="gloo")
+    run = S.SlabRun(slabs, {rank: S.GpuShard(sim)}, S.Distributed(slabs[rank], group), n[0], n[1],
+                    migrate_every=MIGRATE_EVERY)
+    shard = run.shards[rank]
+    run.step(args.warmup)
+    sim.synchronize()
+    nb = sim.num_particles()
+    calls0 = shard.plane_calls
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(sim.stream)
+        run.step(args.steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    psteps = 0.5 * (nb + sim.num_particles()) * args.steps
+    ms_max = allreduce_max(ms, world)
+    value = allreduce_sum(psteps, world) / (ms_max * 1e-3)
+    plane_launches = shard.plane_calls - calls0
+    # the step's own launches, counted by the library over one more (profiled) step
+    sim.set_profiling(True, reset=True)
+    run.step(1)
+    sim.synchronize()
+    step_launches = sim.timings()["launches"]
+    sim.set_profiling(False)
+    if rank != 0:
+        return
+    ncell = n[0] * n[1] * n[2]
+    line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args.nz), "precision": "FP32 storage + FP64 gamma solve",
+                       "particles": n_whole, "cells": ncell,
+                       "l2": f"inputs larger than L2 ({n_whole * 32 / world / 1e9:.2f} GB of particles per slab)",
+                       "parallelism": f"z slabs x{world}, {slabs[0].ghost} ghost planes, particles moved every "
+                                      f"{MIGRATE_EVERY} steps, exchange through host memory (gloo)"},
+            "cell_updates_per_s": ncell * args.steps / (ms_max * 1e-3),
+            "roofline": None, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": int(step_launches * args.steps + plane_launches),
+            "note": "per-kernel roofline, CPU baseline and end-to-end figures come from the 1-GPU run; "
+                    "gpu_launches counts rank 0's phase and plane pack/unpack launches (not the relayouts "
+                    "of moved particles)",
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def end_to_end(pic, w, args, torch):
     """Same metric through the public API with host buffers: the particle state is
     uploaded from pinned host memory, K steps run, each step's diagnostics are read back
@@ -577,6 +656,8 @@ def main():
     ap.add_argument("--instability-study", action="store_true",
                     help="instead of the benchmark: field growth per boost, solver and filter passes")
     ap.add_argument("--study-steps", type=int, default=400)
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1: N independent copies of the instance instead of N z slabs of one")
     ap.add_argument("--nz", type=int, default=N_GRID[2],
                     help="cells along z (a shorter slab of the same workload, for profiling captures)")
     args = ap.parse_args()
@@ -597,6 +678,8 @@ def main():
         print(json.dumps({"precision_sweep": precision_sweep(pic, torch, args)}))
     elif args.impl == "reference":
         run_reference(args, rank, world)
+    elif world > 1 and not args.replicas:
+        run_slabs(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -114,6 +114,11 @@ typedef struct {
                                neighbours (3/4, 1/8 in 2D3V); dispersion-free along the axis
                                of the smallest cell at dt equal to it, Courant limit
                                min_a dx_a.  Ampere's law keeps the Yee differences. */
+    int absorb_faces;       /* which faces of absorbing axes carry the damping layer: bit 2a
+                               the lower face of axis a, bit 2a+1 the upper one (default
+                               0x3F, all).  A face without its bit stays absorbing for
+                               particles and zero beyond, undamped: the inner face of a slab
+                               whose neighbour slab supplies the field (pic_put_planes). */
 } pic_options;
 
 typedef struct {
@@ -379,6 +384,49 @@ pic_status pic_set_injection(pic_ctx *ctx, int enable, double z_lab, int32_t fir
 pic_status pic_autotune(const pic_grid *grid, const double dx[3], double dt, double gamma_boost, int shape_order,
                         const pic_options *base, const pic_laser_lab *laser, const pic_plasma_lab *plasma,
                         const pic_beam_lab *beam, int steps, pic_options *best, double *ms_per_step);
+
+/* Domain decomposition along z (the paper needs no change of the PIC code's parallelism
+ * in the boosted frame, Sec. 3.2): a slab of a larger grid runs as its own context whose
+ * inner z faces are absorbing without a damping layer (pic_options.absorb_faces), carrying
+ * ghost planes that a neighbour slab owns.  These calls move z planes of the fields and
+ * the particles that left a slab; the exchange schedule is the caller's (the Python
+ * module paper_0909_5603_gb300.slab).  The paper has no counterpart for the calls
+ * themselves; they are how its unchanged parallel PIC loop maps onto several GPUs.
+ *
+ * pic_get_planes copies the nk z planes k0 .. k0 + nk - 1 of component comp (PIC_EX ..
+ * PIC_BZ, or PIC_JX .. PIC_JZ: the current the last particle phase deposited, before any
+ * filter sweep) into host_out[nk][n1][n0] (count >= nk n0 n1), FP64.  pic_put_planes
+ * overwrites (add = 0) or adds to (add = 1) those planes from host_in.  0 <= k0,
+ * k0 + nk <= n2, nk >= 1 (else PIC_ERR_ARG).  Both synchronise ctx's stream; device
+ * memory: none beyond the context's. */
+pic_status pic_get_planes(pic_ctx *ctx, int comp, int k0, int nk, double *host_out, size_t count);
+pic_status pic_put_planes(pic_ctx *ctx, int comp, int k0, int nk, const double *host_in, size_t count, int add);
+
+/* pic_extract_particles removes the live particles whose z cell index lies outside
+ * [k_lo, k_hi) and copies them, in canonical order, into the caller's arrays (layout as
+ * pic_get_particles; id may be NULL; room for cap particles, else PIC_ERR_ARG with *n_out
+ * set and nothing removed).  pic_add_particles appends n particles (layout as
+ * pic_load_particles; id may be NULL when ids are not tracked).  Unlike a load, both keep
+ * the step count, the ion background, the antenna, the injection plane and the stations:
+ * the particle set changes, the state of the run does not.  Both read the particles back
+ * and lay the set out again on the host (O(particles) host work and copies per call). */
+pic_status pic_extract_particles(pic_ctx *ctx, int k_lo, int k_hi, int32_t *cell, double *off3, double *u3, double *w,
+                                 int32_t *id, int64_t cap, int64_t *n_out);
+pic_status pic_add_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3, const double *u3,
+                             const double *w, const int32_t *id);
+
+/* pic_adopt_slab makes slab (loaded with its particles) continue the run of whole as the z
+ * slab whose plane 0 is plane k_origin of whole (k_origin may be negative or run past
+ * whole's planes: positions there are taken in whole's box, wrapped when its z is
+ * periodic) and which owns its planes k_lo .. k_hi - 1 (0 <= k_lo < k_hi <= n2; the
+ * others are ghosts): it takes over the ion background of whole's lab-frame plasma, in
+ * whole's box, with the ions' current deposited on the owned planes only (a ghost plane
+ * receives it from its owner), the step count and the phase counter.  Both are 3D
+ * members of the same x-y grid, cell size, time step, boost, shape order and precision
+ * (else PIC_ERR_ARG); neither carries an antenna, an injection plane or stations
+ * (PIC_ERR_STATE).  Fields and particles are moved with the calls above.  Synchronises
+ * both streams. */
+pic_status pic_adopt_slab(pic_ctx *slab, pic_ctx *whole, int k_origin, int k_lo, int k_hi);
 
 /* Charge density read-out that allocates no device memory.  The paper has no counterpart:
  * this is a service of the library, not a step of the method.

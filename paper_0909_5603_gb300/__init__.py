@@ -35,7 +35,8 @@ EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error"
             "pic_num_particles", "pic_get_particles", "pic_get_diagnostics", "pic_set_profiling",
             "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc", "pic_autotune",
             "pic_set_stations", "pic_get_station", "pic_set_injection", "pic_set_laser_antenna",
-            "pic_get_fields", "pic_get_gauss_residual"]
+            "pic_get_fields", "pic_get_gauss_residual", "pic_get_planes", "pic_put_planes",
+            "pic_extract_particles", "pic_add_particles", "pic_adopt_slab"]
 PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
@@ -58,7 +59,8 @@ class pic_options(ctypes.Structure):
                 ("tile", ctypes.c_int * 3), ("threads", ctypes.c_int), ("absorb_cells", ctypes.c_int),
                 ("absorb_strength", ctypes.c_double), ("charge", ctypes.c_double), ("mass", ctypes.c_double),
                 ("track_ids", ctypes.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
-                ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("solver", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("solver", ctypes.c_int),
+                ("absorb_faces", ctypes.c_int)]
 
 
 class pic_diag(ctypes.Structure):
@@ -156,6 +158,17 @@ def lib():
         L.pic_set_laser_antenna.argtypes = [vp, P(pic_laser_lab), ctypes.c_double]
         L.pic_set_injection.restype = st
         L.pic_set_injection.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int32]
+        L.pic_get_planes.restype = st
+        L.pic_get_planes.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t]
+        L.pic_put_planes.restype = st
+        L.pic_put_planes.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int]
+        L.pic_extract_particles.restype = st
+        L.pic_extract_particles.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_int64,
+                                            P(ctypes.c_int64)]
+        L.pic_add_particles.restype = st
+        L.pic_add_particles.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.pic_adopt_slab.restype = st
+        L.pic_adopt_slab.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.pic_autotune.restype = st
         L.pic_autotune.argtypes = [P(pic_grid), P(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    P(pic_options), P(pic_laser_lab), P(pic_plasma_lab), P(pic_beam_lab), ctypes.c_int,
@@ -263,7 +276,7 @@ class Simulation:
     def __init__(self, ndim, n, bc, dx, dt, gamma_boost=1.0, order=1, precision=PIC_PREC_FP32,
                  pusher=PIC_PUSHER_VAY, filter_passes=0, tile=(0, 0, 0), absorb_cells=16,
                  absorb_strength=0.1, charge=-1.0, mass=1.0, track_ids=True, stream=None, device=None,
-                 use_torch_allocator=True, solver=PIC_SOLVER_YEE):
+                 use_torch_allocator=True, solver=PIC_SOLVER_YEE, absorb_faces=0x3F):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required: the PIC step runs only in the sm_103a kernels")
@@ -289,6 +302,7 @@ class Simulation:
         opt.mass = mass
         opt.track_ids = 1 if track_ids else 0
         opt.solver = solver
+        opt.absorb_faces = int(absorb_faces)
         opt.stream = self.stream.cuda_stream
         opt.device = self.device
         self._live = {}
@@ -412,6 +426,45 @@ class Simulation:
         _check(lib().pic_get_particles(self.h, _ptr(cell), _ptr(off), _ptr(u), _ptr(w), _ptr(ids), n,
                                        ctypes.byref(got)), self.h)
         return dict(cell=cell, off=off, u=u, w=w, id=ids)
+
+    # -- z-slab exchange
+    def get_planes(self, comp, k0, nk):
+        out = np.empty((nk, self.n[1], self.n[0]))
+        _check(lib().pic_get_planes(self.h, comp, int(k0), int(nk), _ptr(out), out.size), self.h)
+        return out
+
+    def put_planes(self, comp, k0, values, add=False):
+        v = np.ascontiguousarray(np.asarray(values, np.float64).reshape(-1, self.n[1], self.n[0]))
+        _check(lib().pic_put_planes(self.h, comp, int(k0), v.shape[0], _ptr(v), v.size, 1 if add else 0), self.h)
+
+    def extract_particles(self, k_lo, k_hi):
+        """Removes and returns the particles whose z cell index is outside [k_lo, k_hi)."""
+        cap = self.num_particles()
+        cell = np.empty(cap, np.int32)
+        off = np.empty((cap, 3))
+        u = np.empty((cap, 3))
+        w = np.empty(cap)
+        ids = np.empty(cap, np.int32)
+        got = ctypes.c_int64()
+        _check(lib().pic_extract_particles(self.h, int(k_lo), int(k_hi), _ptr(cell), _ptr(off), _ptr(u), _ptr(w),
+                                           _ptr(ids), cap, ctypes.byref(got)), self.h)
+        m = int(got.value)
+        return dict(cell=cell[:m], off=off[:m], u=u[:m], w=w[:m], id=ids[:m])
+
+    def add_particles(self, cell, off, u, w, ids=None):
+        cell = np.ascontiguousarray(cell, dtype=np.int32)
+        npart = cell.size
+        off = np.ascontiguousarray(np.asarray(off, np.float64).reshape(npart, 3))
+        u = np.ascontiguousarray(np.asarray(u, np.float64).reshape(npart, 3))
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        idp = None if ids is None else np.ascontiguousarray(ids, dtype=np.int32)
+        _check(lib().pic_add_particles(self.h, npart, _ptr(cell), _ptr(off), _ptr(u), _ptr(w),
+                                       None if idp is None else _ptr(idp)), self.h)
+
+    def adopt_slab(self, whole, k_origin, k_lo, k_hi):
+        """Continue the run of `whole` as its z slab starting at plane k_origin and owning
+        local planes k_lo .. k_hi - 1."""
+        _check(lib().pic_adopt_slab(self.h, whole.h, int(k_origin), int(k_lo), int(k_hi)), self.h)
 
     def diagnostics(self):
         d = pic_diag()

@@ -558,14 +558,16 @@ __global__ void __launch_bounds__(256) k_field_energy(Launch L, double *sums)
     }
 }
 
+// Interior values of one component as dense FP64 (x fastest), for the z planes k0 ..
+// k0 + ncell / (n0 n1) - 1 (k0 = 0 and ncell = every cell for a whole field)
 template <typename R>
-__global__ void k_pack(InstDev I, int comp, int filtered, double *dense, long long ncell)
+__global__ void k_pack(InstDev I, int comp, int filtered, double *dense, long long ncell, int k0)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ncell) return;
     const int i = (int)(g % I.n[0]);
     const int j = (int)((g / I.n[0]) % I.n[1]);
-    const int k = (int)(g / ((long long)I.n[0] * I.n[1]));
+    const int k = k0 + (int)(g / ((long long)I.n[0] * I.n[1]));
     const long long p = (i + I.gh[0]) + I.sy * (j + I.gh[1]) + I.sz * (k + I.gh[2]);
     const void *src;
     if (comp < 3) src = I.E[comp];
@@ -577,17 +579,18 @@ __global__ void k_pack(InstDev I, int comp, int filtered, double *dense, long lo
     dense[g] = (double)((const R *)src)[p];
 }
 
+// The inverse of k_pack: writes (add = 0) or adds (add = 1) dense FP64 values
 template <typename R>
-__global__ void k_unpack(InstDev I, int comp, const double *dense, long long ncell)
+__global__ void k_unpack(InstDev I, int comp, const double *dense, long long ncell, int k0, int add)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ncell) return;
     const int i = (int)(g % I.n[0]);
     const int j = (int)((g / I.n[0]) % I.n[1]);
-    const int k = (int)(g / ((long long)I.n[0] * I.n[1]));
+    const int k = k0 + (int)(g / ((long long)I.n[0] * I.n[1]));
     const long long p = (i + I.gh[0]) + I.sy * (j + I.gh[1]) + I.sz * (k + I.gh[2]);
-    void *dst = comp < 3 ? I.E[comp] : (comp < 6 ? I.B[comp - 3] : I.J[comp - 6]);
-    ((R *)dst)[p] = (R)dense[g];
+    R *dst = (R *)(comp < 3 ? I.E[comp] : (comp < 6 ? I.B[comp - 3] : I.J[comp - 6]));
+    dst[p] = add ? (R)((double)dst[p] + dense[g]) : (R)dense[g];
 }
 
 // div E on nodes: sum_a (E_a[i] - E_a[i - e_a]) / dx_a
@@ -717,15 +720,31 @@ cudaError_t launch_field_energy(int fp64, const Launch &L, double *sums, cudaStr
 
 cudaError_t launch_pack(int fp64, const InstDev &I, int comp, int filtered, double *dense, long long ncell, cudaStream_t s)
 {
-    if (fp64) k_pack<double><<<blocks_for(ncell, 256), 256, 0, s>>>(I, comp, filtered, dense, ncell);
-    else k_pack<float><<<blocks_for(ncell, 256), 256, 0, s>>>(I, comp, filtered, dense, ncell);
-    return cudaGetLastError();
+    return launch_pack_planes(fp64, I, comp, filtered, dense, 0, (int)(ncell / ((long long)I.n[0] * I.n[1])), s);
 }
 
 cudaError_t launch_unpack(int fp64, const InstDev &I, int comp, const double *dense, long long ncell, cudaStream_t s)
 {
-    if (fp64) k_unpack<double><<<blocks_for(ncell, 256), 256, 0, s>>>(I, comp, dense, ncell);
-    else k_unpack<float><<<blocks_for(ncell, 256), 256, 0, s>>>(I, comp, dense, ncell);
+    return launch_unpack_planes(fp64, I, comp, dense, 0, (int)(ncell / ((long long)I.n[0] * I.n[1])), 0, s);
+}
+
+cudaError_t launch_pack_planes(int fp64, const InstDev &I, int comp, int filtered, double *dense, int k0, int nk,
+                               cudaStream_t s)
+{
+    const long long n = (long long)nk * I.n[0] * I.n[1];
+    if (n <= 0) return cudaSuccess;
+    if (fp64) k_pack<double><<<blocks_for(n, 256), 256, 0, s>>>(I, comp, filtered, dense, n, k0);
+    else k_pack<float><<<blocks_for(n, 256), 256, 0, s>>>(I, comp, filtered, dense, n, k0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_planes(int fp64, const InstDev &I, int comp, const double *dense, int k0, int nk, int add,
+                                 cudaStream_t s)
+{
+    const long long n = (long long)nk * I.n[0] * I.n[1];
+    if (n <= 0) return cudaSuccess;
+    if (fp64) k_unpack<double><<<blocks_for(n, 256), 256, 0, s>>>(I, comp, dense, n, k0, add);
+    else k_unpack<float><<<blocks_for(n, 256), 256, 0, s>>>(I, comp, dense, n, k0, add);
     return cudaGetLastError();
 }
 

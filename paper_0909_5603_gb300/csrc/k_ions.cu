@@ -31,13 +31,16 @@ __device__ double ion_charge_in_box(const InstDev &I, double lo, double hi)
     return charge;
 }
 
-// Ion charge between box coordinates a < b at t = 0 (b - a below the box length):
-// clipped to the box when z is absorbing (only the loaded volume carries ions), wrapped
-// into it when periodic.
+// Ion charge between coordinates a < b of this grid at t = 0 (b - a below the box
+// length), taken in the box the profile fills (this grid's, or the whole grid of which
+// this one is a z slab): clipped to the box when its z is absorbing (only the loaded
+// volume carries ions), wrapped into it when periodic.
 __device__ double ion_charge(const InstDev &I, double a, double b)
 {
-    const double Lz = I.n[2] * I.dx[2];
-    if (I.bc[2] != 0) {
+    const double Lz = I.ion_lz;
+    a += I.ion_z0;
+    b += I.ion_z0;
+    if (!I.ion_periodic) {
         a = fmax(a, 0.0);
         b = fmin(b, Lz);
         return b > a ? ion_charge_in_box(I, a, b) : 0.0;
@@ -62,7 +65,7 @@ __global__ void __launch_bounds__(256) k_ion_faces(Launch L)
     for (int k = threadIdx.x; k < I.n[2]; k += blockDim.x) {
         const double z = (k + 0.5) * I.dx[2];
         const double crossing = ion_charge(I, z + I.ion_beta * t0, z + I.ion_beta * t1);
-        ((R *)I.ion_face)[k] = R(-crossing / I.dt);
+        ((R *)I.ion_face)[k] = (k >= I.ion_k0 && k < I.ion_k1) ? R(-crossing / I.dt) : R(0);
     }
 }
 

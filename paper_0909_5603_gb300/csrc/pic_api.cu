@@ -208,6 +208,7 @@ extern "C" void pic_default_options(pic_options *o)
     o->mass = 1.0;
     o->track_ids = 1;
     o->device = -1;
+    o->absorb_faces = 0x3F;
 }
 
 extern "C" const char *pic_last_error(const pic_ctx *ctx)
@@ -493,10 +494,11 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
         if (!activeaxis(c->ndim, a) || c->bc[a] != PIC_ABSORBING || o.absorb_cells <= 0) continue;
         std::vector<double> f(c->n[a]);
         const int L = o.absorb_cells;
+        const bool lo = (o.absorb_faces >> (2 * a)) & 1, hi = (o.absorb_faces >> (2 * a + 1)) & 1;
         for (int i = 0; i < c->n[a]; ++i) {
             int d = 0;
-            if (L - i > d) d = L - i;
-            if (i - (c->n[a] - 1 - L) > d) d = i - (c->n[a] - 1 - L);
+            if (lo && L - i > d) d = L - i;
+            if (hi && i - (c->n[a] - 1 - L) > d) d = i - (c->n[a] - 1 - L);
             const double r = (double)d / (double)L;
             f[i] = 1.0 - o.absorb_strength * r * r;
         }
@@ -722,9 +724,8 @@ static pic_status place_from_host(pic_ctx *c, int64_t n, const int32_t *cell, co
 }
 
 // After the particles are in place: the initial tile layout (every tile's particles in
-// its own segment, all in the "stays" bucket), the FP32 current scale, and a reset of
-// the step state.
-static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg)
+// its own segment, all in the "stays" bucket) in layout 0.
+static pic_status upload_layout(pic_ctx *c, const std::vector<int> &seg)
 {
     InstDev &h = c->h;
     const int R = h.R;
@@ -756,6 +757,16 @@ static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg)
     CUDA_OR_FAIL(c, cudaMemcpyAsync(h.pop, pop.data(), sizeof(int) * pop.size(), cudaMemcpyHostToDevice, s));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(h.chunk_pre[0], pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, s));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(h.chunk_cb[0], cbv.data(), sizeof(int) * cbv.size(), cudaMemcpyHostToDevice, s));
+    return PIC_OK;
+}
+
+// A load: the layout and a reset of the step state.
+static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg)
+{
+    InstDev &h = c->h;
+    cudaStream_t s = c->stream;
+    pic_status st0 = upload_layout(c, seg);
+    if (st0 != PIC_OK) return st0;
     fill_step_coef(h);
     apply_injection(c);
     antenna_off(c);  // a load removes the antenna
@@ -784,8 +795,23 @@ static pic_status finish_load(pic_ctx *c, const std::vector<int> &seg)
 
 // Host particles (FP64, any order): validated, laid out in the canonical order with a
 // stable counting sort by tile on the host, then converted and placed on the device.
+// A new particle set that continues the run (pic_extract_particles, pic_add_particles):
+// the layout, the parity word pointing at it; the step count, phase counter, lost count,
+// ion background, antenna, injection plane and stations are kept.
+static pic_status finish_relayout(pic_ctx *c, const std::vector<int> &seg)
+{
+    pic_status st = upload_layout(c, seg);
+    if (st != PIC_OK) return st;
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->h.cur, 0, sizeof(int), c->stream));
+    c->version++;  // a batch holding this instance re-reads its parameters
+    destroy_graph(c);
+    if ((st = upload_inst(c)) != PIC_OK) return st;
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
 static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, const double *off, const double *u,
-                                const double *w, const int32_t *id)
+                                const double *w, const int32_t *id, bool keep_state = false)
 {
     InstDev &h = c->h;
     if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", (long long)n);
@@ -857,7 +883,7 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
     pic_status st = ensure_particle_capacity(c, n);
     if (st != PIC_OK) return st;
     if ((st = place_from_host(c, n, cell, off, u, w, id, 0, slot)) != PIC_OK) return st;
-    return finish_load(c, seg);
+    return keep_state ? finish_relayout(c, seg) : finish_load(c, seg);
 }
 
 extern "C" pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3, const double *u3,
@@ -1014,6 +1040,11 @@ extern "C" pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *lase
     h.ion_ramp = plasma ? plasma->ramp_len : 0.0;
     h.ion_gb = ctx->gamma_b;
     h.ion_beta = std::sqrt(1.0 - 1.0 / (ctx->gamma_b * ctx->gamma_b));
+    h.ion_z0 = 0.0;
+    h.ion_lz = ctx->n[2] * ctx->dx[2];
+    h.ion_periodic = ctx->bc[2] == PIC_PERIODIC;
+    h.ion_k0 = 0;
+    h.ion_k1 = ctx->n[2];
     // the plasma is drawn on the device (k_load.cu); laser, beam and the beam's field on
     // the host.  Plasma ids come first, as in the host transform.
     std::vector<int> counts;
@@ -1474,6 +1505,187 @@ extern "C" pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off
         if (w) widen_in_place(w, n);
     }
     return check_device_error(ctx);
+}
+
+// ---- z-slab exchange (domain decomposition along z) -----------------------------------
+static pic_status check_planes(pic_ctx *c, int comp, int k0, int nk, size_t count)
+{
+    if (c->is_batch) return fail(c, PIC_ERR_ARG, "plane exchange takes a member, not a batch");
+    if (comp < PIC_EX || comp > PIC_JZ) return fail(c, PIC_ERR_ARG, "component %d invalid for planes", comp);
+    if (nk < 1 || k0 < 0 || k0 + nk > c->n[2]) return fail(c, PIC_ERR_ARG, "planes %d .. %d outside 0 .. %d", k0, k0 + nk - 1, c->n[2] - 1);
+    if (count < (size_t)nk * c->n[0] * c->n[1]) return fail(c, PIC_ERR_ARG, "need room for %zu values", (size_t)nk * c->n[0] * c->n[1]);
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_planes(pic_ctx *ctx, int comp, int k0, int nk, double *host_out, size_t count)
+{
+    if (!ctx || !host_out) return PIC_ERR_ARG;
+    pic_status st = check_planes(ctx, comp, k0, nk, count);
+    if (st != PIC_OK) return st;
+    if ((st = pic_synchronize(ctx)) != PIC_OK) return st;
+    const size_t n = (size_t)nk * ctx->n[0] * ctx->n[1];
+    CUDA_OR_FAIL(ctx, launch_pack_planes(ctx->fp64, ctx->h, comp, 0, ctx->d_dense, k0, nk, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(host_out, ctx->d_dense, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
+}
+
+extern "C" pic_status pic_put_planes(pic_ctx *ctx, int comp, int k0, int nk, const double *host_in, size_t count, int add)
+{
+    if (!ctx || !host_in) return PIC_ERR_ARG;
+    pic_status st = check_planes(ctx, comp, k0, nk, count);
+    if (st != PIC_OK) return st;
+    if ((st = pic_synchronize(ctx)) != PIC_OK) return st;
+    const size_t n = (size_t)nk * ctx->n[0] * ctx->n[1];
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(ctx->d_dense, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_OR_FAIL(ctx, launch_unpack_planes(ctx->fp64, ctx->h, comp, ctx->d_dense, k0, nk, add ? 1 : 0, ctx->stream));
+    // E and B carry copies of the periodic faces that the gather reads (the current does not)
+    if (comp < PIC_JX && (st = ghost_fill_now(ctx)) != PIC_OK) return st;
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
+}
+
+// All live particles on the host in canonical order (ids only when tracked).
+struct HostParticles {
+    std::vector<int32_t> cell, id;
+    std::vector<double> off, u, w;
+    int64_t n = 0;
+};
+
+static pic_status read_particles(pic_ctx *c, HostParticles &P)
+{
+    int64_t n = 0;
+    pic_status st = pic_num_particles(c, &n);
+    if (st != PIC_OK) return st;
+    P.cell.resize((size_t)std::max<int64_t>(n, 1));
+    P.off.resize(3 * P.cell.size());
+    P.u.resize(3 * P.cell.size());
+    P.w.resize(P.cell.size());
+    if (c->opt.track_ids) P.id.resize(P.cell.size());
+    st = pic_get_particles(c, P.cell.data(), P.off.data(), P.u.data(), P.w.data(),
+                           c->opt.track_ids ? P.id.data() : nullptr, (int64_t)P.cell.size(), &P.n);
+    return st;
+}
+
+extern "C" pic_status pic_extract_particles(pic_ctx *ctx, int k_lo, int k_hi, int32_t *cell, double *off3, double *u3,
+                                            double *w, int32_t *id, int64_t cap, int64_t *n_out)
+{
+    if (!ctx || !n_out) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_extract_particles takes a member, not a batch");
+    if (!ctx->loaded) return fail(ctx, PIC_ERR_STATE, "pic_extract_particles before any load");
+    if (k_lo > k_hi) return fail(ctx, PIC_ERR_ARG, "k_lo %d > k_hi %d", k_lo, k_hi);
+    cudaSetDevice(ctx->device);
+    HostParticles P;
+    pic_status st = read_particles(ctx, P);
+    if (st != PIC_OK) return st;
+    const long long plane = (long long)ctx->n[0] * ctx->n[1];
+    std::vector<int64_t> go, keep;
+    for (int64_t p = 0; p < P.n; ++p) {
+        const int k = (int)(P.cell[p] / plane);
+        (k < k_lo || k >= k_hi ? go : keep).push_back(p);
+    }
+    *n_out = (int64_t)go.size();
+    if ((int64_t)go.size() > cap) return fail(ctx, PIC_ERR_ARG, "cap %lld < %zu particles to extract", (long long)cap, go.size());
+    if (go.empty()) return PIC_OK;
+    for (size_t q = 0; q < go.size(); ++q) {
+        const int64_t p = go[q];
+        if (cell) cell[q] = P.cell[p];
+        if (id) id[q] = P.id.empty() ? 0 : P.id[p];
+        for (int a = 0; a < 3; ++a) {
+            if (off3) off3[3 * q + a] = P.off[3 * p + a];
+            if (u3) u3[3 * q + a] = P.u[3 * p + a];
+        }
+        if (w) w[q] = P.w[p];
+    }
+    HostParticles K;
+    K.n = (int64_t)keep.size();
+    K.cell.resize(keep.size());
+    K.off.resize(3 * keep.size());
+    K.u.resize(3 * keep.size());
+    K.w.resize(keep.size());
+    if (!P.id.empty()) K.id.resize(keep.size());
+    for (size_t q = 0; q < keep.size(); ++q) {
+        const int64_t p = keep[q];
+        K.cell[q] = P.cell[p];
+        if (!P.id.empty()) K.id[q] = P.id[p];
+        for (int a = 0; a < 3; ++a) {
+            K.off[3 * q + a] = P.off[3 * p + a];
+            K.u[3 * q + a] = P.u[3 * p + a];
+        }
+        K.w[q] = P.w[p];
+    }
+    return load_internal(ctx, K.n, K.cell.data(), K.off.data(), K.u.data(), K.w.data(), K.id.empty() ? nullptr : K.id.data(),
+                         true);
+}
+
+extern "C" pic_status pic_add_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3, const double *u3,
+                                        const double *w, const int32_t *id)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_add_particles takes a member, not a batch");
+    if (!ctx->loaded) return fail(ctx, PIC_ERR_STATE, "pic_add_particles before any load");
+    if (n < 0 || (n > 0 && (!cell || !off3 || !u3 || !w))) return fail(ctx, PIC_ERR_ARG, "particle arrays invalid");
+    if (n == 0) return PIC_OK;
+    cudaSetDevice(ctx->device);
+    HostParticles P;
+    pic_status st = read_particles(ctx, P);
+    if (st != PIC_OK) return st;
+    P.cell.resize((size_t)P.n);
+    P.off.resize(3 * (size_t)P.n);
+    P.u.resize(3 * (size_t)P.n);
+    P.w.resize((size_t)P.n);
+    P.cell.insert(P.cell.end(), cell, cell + n);
+    P.off.insert(P.off.end(), off3, off3 + 3 * n);
+    P.u.insert(P.u.end(), u3, u3 + 3 * n);
+    P.w.insert(P.w.end(), w, w + n);
+    if (ctx->opt.track_ids) {
+        P.id.resize((size_t)P.n);
+        for (int64_t p = 0; p < n; ++p) P.id.push_back(id ? id[p] : 0);
+    }
+    return load_internal(ctx, P.n + n, P.cell.data(), P.off.data(), P.u.data(), P.w.data(),
+                         ctx->opt.track_ids ? P.id.data() : nullptr, true);
+}
+
+extern "C" pic_status pic_adopt_slab(pic_ctx *slab, pic_ctx *whole, int k_origin, int k_lo, int k_hi)
+{
+    if (!slab || !whole) return PIC_ERR_ARG;
+    if (k_lo < 0 || k_lo >= k_hi || k_hi > slab->n[2]) return fail(slab, PIC_ERR_ARG, "owned planes %d .. %d invalid", k_lo, k_hi);
+    if (slab->is_batch || whole->is_batch) return fail(slab, PIC_ERR_ARG, "pic_adopt_slab takes members, not batches");
+    if (slab == whole) return fail(slab, PIC_ERR_ARG, "a context cannot be its own slab");
+    if (!slab->loaded || !whole->loaded) return fail(slab, PIC_ERR_STATE, "pic_adopt_slab needs both contexts loaded");
+    bool same = slab->ndim == whole->ndim && slab->ndim == 3 && slab->order == whole->order && slab->dt == whole->dt &&
+                slab->gamma_b == whole->gamma_b && slab->fp64 == whole->fp64;
+    for (int a = 0; a < 3; ++a) same = same && slab->dx[a] == whole->dx[a];
+    for (int a = 0; a < 2; ++a) same = same && slab->n[a] == whole->n[a] && slab->bc[a] == whole->bc[a];
+    if (!same) return fail(slab, PIC_ERR_ARG, "slab and whole differ in dimension, x-y grid, steps, boost, shape or precision");
+    if (whole->ant_on || whole->inj_on || whole->nst > 0 || slab->ant_on || slab->inj_on || slab->nst > 0)
+        return fail(slab, PIC_ERR_STATE, "antenna, injection plane and stations are not carried over to a slab");
+    pic_status st = pic_synchronize(whole);
+    if (st != PIC_OK) return fail(slab, st, "whole: %s", whole->err.c_str());
+    if ((st = pic_synchronize(slab)) != PIC_OK) return st;
+    int phase = 0;
+    cudaSetDevice(whole->device);
+    CUDA_OR_FAIL(slab, cudaMemcpy(&phase, whole->h.phase, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaSetDevice(slab->device);
+    InstDev &h = slab->h;
+    const InstDev &w = whole->h;
+    h.ion = w.ion;
+    h.ion_n0 = w.ion_n0;
+    h.ion_zs = w.ion_zs;
+    h.ion_ramp = w.ion_ramp;
+    h.ion_gb = w.ion_gb;
+    h.ion_beta = w.ion_beta;
+    h.ion_z0 = w.ion_z0 + k_origin * slab->dx[2];
+    h.ion_lz = w.ion_lz;
+    h.ion_periodic = w.ion_periodic;
+    h.ion_k0 = k_lo;
+    h.ion_k1 = k_hi;
+    slab->step = whole->step;
+    slab->mx_phases = whole->mx_phases;
+    CUDA_OR_FAIL(slab, cudaMemcpyAsync(h.phase, &phase, sizeof(int), cudaMemcpyHostToDevice, slab->stream));
+    slab->version++;
+    destroy_graph(slab);
+    return upload_inst(slab);
 }
 
 extern "C" pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out)

@@ -125,6 +125,12 @@ struct InstDev {
     // a rigid density gamma_b n0 p(gamma_b (z + beta_b t)) of charge -q on [0, Lz) at t = 0
     int ion;            // 0: none
     double ion_n0, ion_zs, ion_ramp, ion_gb, ion_beta;
+    // the box the ion profile fills: this grid's own ([0, n2 dz), its own z boundary), or,
+    // for a z slab of a larger grid, that grid's, with ion_z0 the coordinate there of this
+    // grid's z = 0
+    double ion_z0, ion_lz;
+    int ion_periodic;
+    int ion_k0, ion_k1; // z planes whose Jz faces carry the ion current (a slab: its own)
     void *ion_face;     // [n[2]] this step's ion current on the Jz faces (working precision)
     int *phase;         // particle phases run since the last load (device counter)
     double gb, beta_b;  // the frame's boost: Lorentz factor and velocity

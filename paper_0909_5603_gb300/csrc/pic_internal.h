@@ -106,6 +106,11 @@ cudaError_t preload_rho_ion();
 cudaError_t launch_field_energy(int fp64, const Launch &L, double *sums, cudaStream_t s);
 cudaError_t launch_pack(int fp64, const InstDev &I, int comp, int filtered, double *dense, long long ncell, cudaStream_t s);
 cudaError_t launch_unpack(int fp64, const InstDev &I, int comp, const double *dense, long long ncell, cudaStream_t s);
+// the same for the z planes k0 .. k0 + nk - 1 (unpack: add = 1 adds instead of writing)
+cudaError_t launch_pack_planes(int fp64, const InstDev &I, int comp, int filtered, double *dense, int k0, int nk,
+                               cudaStream_t s);
+cudaError_t launch_unpack_planes(int fp64, const InstDev &I, int comp, const double *dense, int k0, int nk, int add,
+                                 cudaStream_t s);
 cudaError_t launch_dive(int fp64, const InstDev &I, double *dense, long long ncell, cudaStream_t s);
 // max |a - b| (as the bits of a non-negative double, atomicMax) and sum (a - b)^2
 cudaError_t launch_residual(const double *a, const double *b, long long n, unsigned long long *max_bits, double *sumsq,

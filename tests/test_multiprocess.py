@@ -1,10 +1,11 @@
 """The multi-process paths of bench.py, on the CPU with gloo (world size 2).
 
-The boosted-frame step does not shard in this build (replicas only): each rank runs its
-own instance and the job reports the particle-steps of all ranks over the slowest rank's
-time.  These tests cover the reduction helpers that implement that, and the reference
-arm under torchrun (rank 0 times the oracle and prints the one JSON line, the other ranks
-exit without work).
+Under torchrun the benchmark splits its instance into z slabs (the exchange itself is
+covered by tests/test_slab.py, on gloo ranks with oracle slabs) or, with --replicas,
+runs independent copies; either way the job reports the particle-steps of all ranks over
+the slowest rank's time.  These tests cover the reduction helpers that implement that,
+and the reference arm under torchrun (rank 0 times the oracle and prints the one JSON
+line, the other ranks exit without work).
 """
 import json
 import os
