@@ -394,9 +394,12 @@ pic_status pic_autotune(const pic_grid *grid, const double dx[3], double dt, dou
  * themselves; they are how its unchanged parallel PIC loop maps onto several GPUs.
  *
  * pic_get_planes copies the nk z planes k0 .. k0 + nk - 1 of component comp (PIC_EX ..
- * PIC_BZ, or PIC_JX .. PIC_JZ: the current the last particle phase deposited, before any
- * filter sweep) into host_out[nk][n1][n0] (count >= nk n0 n1), FP64.  pic_put_planes
- * overwrites (add = 0) or adds to (add = 1) those planes from host_in.  0 <= k0,
+ * PIC_BZ, or PIC_JX .. PIC_JZ: the current as pic_get_field reads it, i.e. the deposit
+ * after a particle phase, the filtered current once the filter has run) into
+ * host_out[nk][n1][n0] (count >= nk n0 n1), FP64.  pic_put_planes overwrites (add = 0) or
+ * adds to (add = 1) those planes from host_in; for J it writes the deposit the coming
+ * filter phase reads (meaningful between pic_run_phases(PIC_PHASE_PARTICLES) and the
+ * filter).  0 <= k0,
  * k0 + nk <= n2, nk >= 1 (else PIC_ERR_ARG).  Both synchronise ctx's stream; device
  * memory: none beyond the context's. */
 pic_status pic_get_planes(pic_ctx *ctx, int comp, int k0, int nk, double *host_out, size_t count);

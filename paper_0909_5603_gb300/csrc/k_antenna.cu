@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_ant_add(const InstDev *Ip, AntDev A, in
     const int k0 = lo < 0.0 ? 0 : (int)fmin(floor(lo), (double)I.n[2]);
     const int k1 = hi >= I.n[2] - 1 ? I.n[2] - 1 : (int)floor(hi);
     const double T = ant_profile(A, I, i, j);
-    R *Ex = (R *)I.E[0], *By = (R *)I.B[1];
+    R *Ex = (R *)eb_field(I, 0), *By = (R *)eb_field(I, 4);
     for (int k = k0; k <= k1; ++k) {
         const long long p = padded(I, i, j, k);
         if (k > lo && k <= hi) Ex[p] += (R)(T * ant_ge(A, k));
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) k_ant_bterm(const InstDev *Ip, AntDev A, 
         // B_z at (i + 1/2, j + 1/2, kz): its averaged dE_x/dy reads E_x at kz - 1, kz,
         // kz + 1; the node below the plane (kz = k) reads the incident E_x of row k + 1
         // above it and subtracts it, the node above (kz = k + 1) adds that of row k
-        R *Bz = (R *)I.B[2];
+        R *Bz = (R *)eb_field(I, 5);
         for (int side = 0; side < 2; ++side) {
             const int kz = k + side;
             if (kz >= I.n[2]) continue;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256) k_ant_bterm(const InstDev *Ip, AntDev A, 
         T = ant_profile(A, I, i, j);
     }
     const double f = damp ? damp_at<R>(I, i, j, k) : 1.0;
-    R *By = (R *)I.B[1];
+    R *By = (R *)eb_field(I, 4);
     By[padded(I, i, j, k)] += (R)(f * h * (T * g / I.dx[2]));
 }
 
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_ant_eterm(const InstDev *Ip, AntDev A)
         g = ant_gb(A, m);
     }
     const double f = damp_at<R>(I, i, j, m);
-    R *Ex = (R *)I.E[0];
+    R *Ex = (R *)eb_field(I, 0);
     Ex[padded(I, i, j, m)] += (R)(f * I.dt * (ant_profile(A, I, i, j) * g / I.dx[2]));
 }
 

@@ -97,8 +97,9 @@ __global__ void __launch_bounds__(256) k_bhalf(Launch L, int damp)
     const InstDev &I = *Ip;
     long long up[3], dn[3];
     neighbour_offsets(I, c, up, dn);
-    const R *Ex = (const R *)I.E[0], *Ey = (const R *)I.E[1], *Ez = (const R *)I.E[2];
-    R *Bx = (R *)I.B[0], *By = (R *)I.B[1], *Bz = (R *)I.B[2];
+    const EBPtr F = cur_eb(I);
+    const R *Ex = (const R *)F.E[0], *Ey = (const R *)F.E[1], *Ez = (const R *)F.E[2];
+    R *Bx = (R *)F.B[0], *By = (R *)F.B[1], *Bz = (R *)F.B[2];
     const StepCoef<R> &K = coef<R>(I);
     const R h = K.half_dt;
     const R ix = K.inv_dx[0], iy = K.inv_dx[1], iz = K.inv_dx[2];
@@ -141,6 +142,302 @@ __global__ void __launch_bounds__(256) k_bhalf(Launch L, int damp)
     Bz[p] = bz;
 }
 
+// The whole Yee update of a step in one kernel (Yee solver, no antenna): B half step, E
+// step, damped B half step.  It reads E^n, B^n and J once and writes E^{n+1}, B^{n+1}
+// once (60 bytes per cell in FP32 instead of 120 for the three-kernel sequence).  The
+// inputs are the current E / B buffer pair and the outputs go to the other one (*fpar
+// flips after the kernel), so no CTA overwrites a value that a neighbouring CTA still
+// reads.  A CTA takes an x-y tile of TX x TY columns (one thread each) and marches
+// along z through a chunk of TZ planes, keeping in shared memory E^n of three planes on
+// the tile widened by [-1, +2] in x and y, B^{n+1/2} of three planes on [-1, +1] and
+// E^{n+1} of two planes on [0, +1].  For the output plane k, between two barriers:
+//   B^{n+1/2}(k+2) = B^n - dt/2 curl E^n        (E^n of planes k+2, k+3)
+//   E^{n+1}(k+1)  = f (E^n + dt (curl B^{n+1/2} - J))   (B^{n+1/2} of planes k, k+1)
+// and after the second:
+//   B^{n+1}(k)    = f (B^{n+1/2} - dt/2 curl E^{n+1})   (E^{n+1} of planes k, k+1)
+// with the loads of the next plane issued one plane ahead.  Outside an absorbing box
+// every field is zero; periodic axes wrap.  Each value is formed by the same expression
+// as in k_bhalf / k_efull; the in-plane offsets of a thread's cells are computed once.
+template <int ND>
+struct MxTile;
+template <>
+struct MxTile<3> {
+    static constexpr int X = 32, Y = 8, Z = 32;
+};
+template <>
+struct MxTile<2> {
+    static constexpr int X = 256, Y = 1, Z = 32;
+};
+
+template <typename R, int ND>
+constexpr size_t maxwell_fused_smem()
+{
+    constexpr int HY = ND == 3 ? 1 : 0;
+    constexpr int X = MxTile<ND>::X, Y = MxTile<ND>::Y;
+    constexpr size_t NE = (size_t)(X + 3) * (Y + 3 * HY), NB = (size_t)(X + 2) * (Y + 2 * HY), NQ = (size_t)(X + 1) * (Y + HY);
+    return sizeof(R) * 3 * (3 * NE + 3 * NB + 2 * NQ);
+}
+
+// index along one axis of the cell at q: false outside an absorbing box; wrapped on a
+// periodic axis
+__device__ __forceinline__ bool mx_axis(int q, int n, int bc, int &w)
+{
+    if (q >= 0 && q < n) {
+        w = q;
+        return true;
+    }
+    if (bc != 0) return false;
+    w = ((q % n) + n) % n;
+    return true;
+}
+
+template <typename R, int ND>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_maxwell_fused(Launch L, const long long *tile_start,
+                                                                              int filtered)
+{
+    constexpr int TX = MxTile<ND>::X, TY = MxTile<ND>::Y, TZ = MxTile<ND>::Z;
+    constexpr int HY = ND == 3 ? 1 : 0;
+    constexpr int EX = TX + 3, NE = EX * (TY + 3 * HY);  // E^n region: [-1, +2]
+    constexpr int BX = TX + 2, NB = BX * (TY + 2 * HY);  // B^{n+1/2} region: [-1, +1]
+    constexpr int QX = TX + 1, NQ = QX * (TY + HY);      // E^{n+1} region: [0, +1]
+    static_assert(TX * TY == 256 && NE <= 512 && NB <= 512 && NQ <= 512, "two region cells per thread");
+    extern __shared__ __align__(16) unsigned char msm[];
+    R *sE = (R *)msm;     // [3 planes][3 comps][NE]
+    R *sH = sE + 9 * NE;  // [3][3][NB]
+    R *sQ = sH + 9 * NB;  // [2][3][NQ]
+    const long long g = blockIdx.x;
+    if (g >= tile_start[L.ninst]) return;
+    const int ii = find_instance_ll(tile_start, L.ninst, g);
+    const InstDev &I = L.inst[ii];
+    const int n0 = I.n[0], n1 = I.n[1], n2 = I.n[2];
+    const int ntx = (n0 + TX - 1) / TX, nty = (n1 + TY - 1) / TY;
+    long long r = g - tile_start[ii];
+    const int x0 = (int)(r % ntx) * TX;
+    r /= ntx;
+    const int y0 = (int)(r % nty) * TY;
+    const int z0 = (int)(r / nty) * TZ;
+    const int z1 = min(z0 + TZ, n2);
+    const int par = *(volatile const int *)I.fpar;
+    // the components of each field are cstride elements apart
+    const long long cs = I.cstride;
+    const int nsweeps = I.filter_passes > 0 ? (I.ndim == 3 ? 3 : 2) : 0;
+    const R *Ein = (const R *)(par ? I.E2[0] : I.E[0]), *Bin = (const R *)(par ? I.B2[0] : I.B[0]);
+    R *Eout = (R *)(par ? I.E[0] : I.E2[0]), *Bout = (R *)(par ? I.B[0] : I.B2[0]);
+    const R *Jin = (const R *)((filtered && (nsweeps & 1)) ? I.Jt[0] : I.J[0]);
+    const StepCoef<R> &K = coef<R>(I);
+    const R h = K.half_dt, dt = K.dt;
+    const R ix = K.inv_dx[0], iy = K.inv_dx[1], iz = K.inv_dx[2];
+    const R *dampx = (const R *)I.damp[0], *dampy = (const R *)I.damp[1], *dampz = (const R *)I.damp[2];
+    const int tid = threadIdx.x;
+    // in-plane padded offset of the cell at (x0 + dx, y0 + dy), false outside the box;
+    // fxy: its x and y damping factors multiplied in the order of damp_factor
+    auto inplane = [&](int dx_, int dy_, int &off, R &fxy) -> bool {
+        int x, y = 0;
+        bool ok = mx_axis(x0 + dx_, n0, I.bc[0], x);
+        if (ND == 3) ok = ok && mx_axis(y0 + dy_, n1, I.bc[1], y);
+        off = (x + I.gh[0]) + I.sy * (y + I.gh[1]);  // < 2^31: one plane
+        fxy = R(1);
+        if (ok && dampx) fxy *= dampx[x];
+        if (ok && ND == 3 && dampy) fxy *= dampy[y];
+        return ok;
+    };
+    int eoff[2], boff[2], qoff[2], toff;
+    bool eok[2], bok[2], qok[2], tok;
+    R qf[2], tf, unused;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int e = tid + 256 * j, b = tid + 256 * j, q = tid + 256 * j;
+        eok[j] = e < NE && inplane(e % EX - 1, e / EX - HY, eoff[j], unused);
+        bok[j] = b < NB && inplane(b % BX - 1, b / BX - HY, boff[j], unused);
+        qok[j] = q < NQ && inplane(q % QX, q / QX, qoff[j], qf[j]);
+    }
+    const int tx = tid % TX, ty = tid / TX;
+    tok = x0 + tx < n0 && y0 + ty < n1 && inplane(tx, ty, toff, tf);
+    // z: padded plane offset of plane k, false outside an absorbing box
+    auto zplane = [&](int k, long long &zo, R &fz) -> bool {
+        int z;
+        const bool ok = mx_axis(k, n2, I.bc[2], z);
+        zo = I.sz * (long long)(z + I.gh[2]);
+        fz = (ok && dampz) ? dampz[z] : R(1);
+        return ok;
+    };
+    auto slot3 = [](int k) { return ((k % 3) + 3) % 3; };
+    // global loads of one plane for this thread's cells of a region
+    auto load3 = [&](const R *F, const int *off, const bool *ok, int k, R (&v)[2][3]) {
+        long long zo;
+        R fz;
+        const bool zk = zplane(k, zo, fz);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[j][c] = (zk && ok[j]) ? F[c * cs + off[j] + zo] : R(0);
+    };
+    auto storeE = [&](int k, const R (&v)[2][3]) {
+        R *d = sE + slot3(k) * 3 * NE;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            if (tid + 256 * j < NE)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) d[c * NE + tid + 256 * j] = v[j][c];
+    };
+    // B^{n+1/2}(k) from E^n of planes k, k+1 and B^n(k) (bv)
+    auto makeH = [&](int k, const R (&bv)[2][3]) {
+        long long zo;
+        R fz;
+        const bool zk = zplane(k, zo, fz);
+        const R *E0 = sE + slot3(k) * 3 * NE, *E1 = sE + slot3(k + 1) * 3 * NE;
+        R *H = sH + slot3(k) * 3 * NB;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int b = tid + 256 * j;
+            if (b >= NB) continue;
+            R hb[3] = {R(0), R(0), R(0)};
+            if (zk && bok[j]) {
+                const int e = b % BX + EX * (b / BX);
+                const R ex = E0[e], ey = E0[NE + e], ez = E0[2 * NE + e];
+                R dEz_dy = R(0), dEx_dy = R(0);
+                const R dEy_dz = (E1[NE + e] - ey) * iz;
+                const R dEx_dz = (E1[e] - ex) * iz;
+                const R dEz_dx = (E0[2 * NE + e + 1] - ez) * ix;
+                const R dEy_dx = (E0[NE + e + 1] - ey) * ix;
+                if (ND == 3) {
+                    dEz_dy = (E0[2 * NE + e + EX] - ez) * iy;
+                    dEx_dy = (E0[e + EX] - ex) * iy;
+                }
+                hb[0] = bv[j][0] - h * (dEz_dy - dEy_dz);
+                hb[1] = bv[j][1] - h * (dEx_dz - dEz_dx);
+                hb[2] = bv[j][2] - h * (dEy_dx - dEx_dy);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) H[c * NB + b] = hb[c];
+        }
+    };
+    // E^{n+1}(k) from B^{n+1/2} of planes k-1, k, E^n(k) and J(k) (jv)
+    auto makeQ = [&](int k, const R (&jv)[2][3]) {
+        long long zo;
+        R fz;
+        const bool zk = zplane(k, zo, fz);
+        const R *H1 = sH + slot3(k) * 3 * NB, *H0 = sH + slot3(k - 1) * 3 * NB;
+        const R *E0 = sE + slot3(k) * 3 * NE;
+        R *Q = sQ + (k & 1) * 3 * NQ;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int q = tid + 256 * j;
+            if (q >= NQ) continue;
+            R en[3] = {R(0), R(0), R(0)};
+            if (zk && qok[j]) {
+                const int qx = q % QX, qy = q / QX;
+                const int b = (qx + 1) + BX * (qy + HY), e = (qx + 1) + EX * (qy + HY);
+                const R bx = H1[b], by = H1[NB + b], bz = H1[2 * NB + b];
+                R dBz_dy = R(0), dBx_dy = R(0);
+                const R dBy_dz = (by - H0[NB + b]) * iz, dBx_dz = (bx - H0[b]) * iz;
+                const R dBz_dx = (bz - H1[2 * NB + b - 1]) * ix, dBy_dx = (by - H1[NB + b - 1]) * ix;
+                if (ND == 3) {
+                    dBz_dy = (bz - H1[2 * NB + b - BX]) * iy;
+                    dBx_dy = (bx - H1[b - BX]) * iy;
+                }
+                const R f = dampz ? qf[j] * fz : qf[j];
+                en[0] = f * (E0[e] + dt * ((dBz_dy - dBy_dz) - jv[j][0]));
+                en[1] = f * (E0[NE + e] + dt * ((dBx_dz - dBz_dx) - jv[j][1]));
+                en[2] = f * (E0[2 * NE + e] + dt * ((dBy_dx - dBx_dy) - jv[j][2]));
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Q[c * NQ + q] = en[c];
+        }
+    };
+    // B^{n+1}(k) on the tile from B^{n+1/2}(k), E^{n+1} of planes k, k+1; stores both
+    auto emit = [&](int k) {
+        if (!tok) return;
+        long long zo;
+        R fz;
+        zplane(k, zo, fz);
+        const R *Q0 = sQ + (k & 1) * 3 * NQ, *Q1 = sQ + ((k + 1) & 1) * 3 * NQ;
+        const R *H = sH + slot3(k) * 3 * NB;
+        const int q = tx + QX * ty, b = (tx + 1) + BX * (ty + HY);
+        const R ex = Q0[q], ey = Q0[NQ + q], ez = Q0[2 * NQ + q];
+        R dEz_dy = R(0), dEx_dy = R(0);
+        const R dEy_dz = (Q1[NQ + q] - ey) * iz;
+        const R dEx_dz = (Q1[q] - ex) * iz;
+        const R dEz_dx = (Q0[2 * NQ + q + 1] - ez) * ix;
+        const R dEy_dx = (Q0[NQ + q + 1] - ey) * ix;
+        if (ND == 3) {
+            dEz_dy = (Q0[2 * NQ + q + QX] - ez) * iy;
+            dEx_dy = (Q0[q + QX] - ex) * iy;
+        }
+        R bx = H[b] - h * (dEz_dy - dEy_dz);
+        R by = H[NB + b] - h * (dEx_dz - dEz_dx);
+        R bz = H[2 * NB + b] - h * (dEy_dx - dEx_dy);
+        const R f = dampz ? tf * fz : tf;
+        bx *= f;
+        by *= f;
+        bz *= f;
+        const long long p = toff + zo;
+        Bout[p] = bx;
+        Bout[cs + p] = by;
+        Bout[2 * cs + p] = bz;
+        Eout[p] = ex;
+        Eout[cs + p] = ey;
+        Eout[2 * cs + p] = ez;
+    };
+
+    R vE[2][3], cB[2][3], cJ[2][3], nB[2][3], nJ[2][3];
+    // prologue: E^n of planes z0-1 .. z0+2, B^{n+1/2} of z0-1 .. z0+1, E^{n+1} of z0
+    load3(Ein, eoff, eok, z0 - 1, vE);
+    storeE(z0 - 1, vE);
+    load3(Ein, eoff, eok, z0, vE);
+    storeE(z0, vE);
+    load3(Ein, eoff, eok, z0 + 1, vE);
+    storeE(z0 + 1, vE);
+    load3(Bin, boff, bok, z0 - 1, cB);
+    load3(Bin, boff, bok, z0, nB);
+    load3(Jin, qoff, qok, z0, cJ);
+    __syncthreads();
+    makeH(z0 - 1, cB);
+    makeH(z0, nB);
+    __syncthreads();
+    makeQ(z0, cJ);
+    __syncthreads();
+    load3(Ein, eoff, eok, z0 + 2, vE);
+    storeE(z0 + 2, vE);  // in the slot of plane z0 - 1
+    load3(Bin, boff, bok, z0 + 1, cB);
+    __syncthreads();
+    makeH(z0 + 1, cB);   // the third slot
+    // one plane ahead: E^n(z0+3), B^n(z0+2), J(z0+1)
+    load3(Ein, eoff, eok, z0 + 3, vE);
+    load3(Bin, boff, bok, z0 + 2, cB);
+    load3(Jin, qoff, qok, z0 + 1, cJ);
+#pragma unroll 1
+    for (int k = z0; k < z1; ++k) {
+        storeE(k + 3, vE);  // in the slot of plane k
+        // the next plane's loads, in flight through this plane's arithmetic
+        load3(Ein, eoff, eok, k + 4, vE);
+        load3(Bin, boff, bok, k + 3, nB);
+        load3(Jin, qoff, qok, k + 2, nJ);
+        __syncthreads();
+        makeH(k + 2, cB);  // in the slot of plane k - 1
+        makeQ(k + 1, cJ);  // in the slot of plane k - 1
+        __syncthreads();
+        emit(k);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cB[j][c] = nB[j][c];
+                cJ[j][c] = nJ[j][c];
+            }
+    }
+}
+
+// After the fused update: every instance of the launch switches to the buffer pair it
+// wrote.
+__global__ void k_flip_fields(Launch L)
+{
+    for (int i = threadIdx.x; i < L.ninst; i += blockDim.x) {
+        int *f = L.inst[i].fpar;
+        *f ^= 1;
+    }
+}
+
 // E <- damping x (E + dt (curl B - J)), J = the filtered current of this step.
 template <typename R>
 __global__ void __launch_bounds__(256) k_efull(Launch L, int filtered)
@@ -152,8 +449,9 @@ __global__ void __launch_bounds__(256) k_efull(Launch L, int filtered)
     const InstDev &I = *Ip;
     long long up[3], dn[3];
     neighbour_offsets(I, c, up, dn);
-    const R *Bx = (const R *)I.B[0], *By = (const R *)I.B[1], *Bz = (const R *)I.B[2];
-    R *Ex = (R *)I.E[0], *Ey = (R *)I.E[1], *Ez = (R *)I.E[2];
+    const EBPtr F = cur_eb(I);
+    const R *Bx = (const R *)F.B[0], *By = (const R *)F.B[1], *Bz = (const R *)F.B[2];
+    R *Ex = (R *)F.E[0], *Ey = (R *)F.E[1], *Ez = (R *)F.E[2];
     // one filter sweep per active axis alternates J -> Jt -> J ...
     const int nsweeps = I.filter_passes > 0 ? (I.ndim == 3 ? 3 : 2) : 0;
     void *const *Jsrc = (filtered && (nsweeps & 1)) ? I.Jt : I.J;
@@ -500,7 +798,7 @@ __global__ void __launch_bounds__(256) k_ghost(Launch L, int axis, long long per
     const int spos = layer < gh ? dpos + n : dpos - n;
     long long st[3] = {1, I.sy, I.sz};
     const long long base = a1 * st[o1] + a2 * st[o2];
-    R *f = (R *)(comp < 3 ? I.E[comp] : I.B[comp - 3]);
+    R *f = (R *)eb_field(I, comp);
     f[base + dpos * st[axis]] = f[base + spos * st[axis]];
 }
 
@@ -521,7 +819,7 @@ __global__ void __launch_bounds__(256) k_field_energy(Launch L, double *sums)
         R s2 = R(0);  // the cell's E^2 + B^2 in the storage precision, then FP64
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const R x = ((const R *)I.E[a])[c.p], y = ((const R *)I.B[a])[c.p];
+            const R x = ((const R *)eb_field(I, a))[c.p], y = ((const R *)eb_field(I, 3 + a))[c.p];
             s2 += x * x + y * y;
         }
         e = (double)s2 * (0.5 * I.dx[0] * I.dx[1] * I.dx[2]);
@@ -570,8 +868,7 @@ __global__ void k_pack(InstDev I, int comp, int filtered, double *dense, long lo
     const int k = k0 + (int)(g / ((long long)I.n[0] * I.n[1]));
     const long long p = (i + I.gh[0]) + I.sy * (j + I.gh[1]) + I.sz * (k + I.gh[2]);
     const void *src;
-    if (comp < 3) src = I.E[comp];
-    else if (comp < 6) src = I.B[comp - 3];
+    if (comp < 6) src = eb_field(I, comp);
     else {
         const int nsweeps = I.filter_passes > 0 ? (I.ndim == 3 ? 3 : 2) : 0;
         src = (filtered && (nsweeps & 1)) ? I.Jt[comp - 6] : I.J[comp - 6];
@@ -589,7 +886,7 @@ __global__ void k_unpack(InstDev I, int comp, const double *dense, long long nce
     const int j = (int)((g / I.n[0]) % I.n[1]);
     const int k = k0 + (int)(g / ((long long)I.n[0] * I.n[1]));
     const long long p = (i + I.gh[0]) + I.sy * (j + I.gh[1]) + I.sz * (k + I.gh[2]);
-    R *dst = (R *)(comp < 3 ? I.E[comp] : (comp < 6 ? I.B[comp - 3] : I.J[comp - 6]));
+    R *dst = (R *)(comp < 6 ? eb_field(I, comp) : I.J[comp - 6]);
     dst[p] = add ? (R)((double)dst[p] + dense[g]) : (R)dense[g];
 }
 
@@ -609,7 +906,7 @@ __global__ void k_dive(InstDev I, double *dense, long long ncell)
     double d = 0.0;
     for (int a = 0; a < 3; ++a) {
         if (I.ndim == 2 && a == 1) continue;
-        const R *E = (const R *)I.E[a];
+        const R *E = (const R *)eb_field(I, a);
         d += ((double)E[c.p] - (double)E[c.p + dn[a]]) / I.dx[a];
     }
     dense[g] = d;
@@ -638,6 +935,36 @@ static void filter_axis(const Launch &L, int axis, int passes, unsigned nb, cons
     case 4: filter_fixed<R, 4>(L, axis, nb, start, src_is_jt, s); break;
     default: k_filter_axis<R><<<nb, 256, 0, s>>>(L, axis, start, src_is_jt); break;
     }
+}
+
+template <typename R, int ND>
+static cudaError_t maxwell_fused_attr()
+{
+    return cudaFuncSetAttribute(k_maxwell_fused<R, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)maxwell_fused_smem<R, ND>());
+}
+
+cudaError_t launch_maxwell_fused(int fp64, int ndim, const Launch &L, const long long *tile_start, long long ntiles,
+                                 int filtered, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    const unsigned nb = (unsigned)ntiles;
+    if (fp64) {
+        if (ndim == 3) k_maxwell_fused<double, 3><<<nb, 256, maxwell_fused_smem<double, 3>(), s>>>(L, tile_start, filtered);
+        else k_maxwell_fused<double, 2><<<nb, 256, maxwell_fused_smem<double, 2>(), s>>>(L, tile_start, filtered);
+    } else {
+        if (ndim == 3) k_maxwell_fused<float, 3><<<nb, 256, maxwell_fused_smem<float, 3>(), s>>>(L, tile_start, filtered);
+        else k_maxwell_fused<float, 2><<<nb, 256, maxwell_fused_smem<float, 2>(), s>>>(L, tile_start, filtered);
+    }
+    k_flip_fields<<<1, 128, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_fields(int fp64)
+{
+    cudaError_t e = fp64 ? maxwell_fused_attr<double, 3>() : maxwell_fused_attr<float, 3>();
+    if (e == cudaSuccess) e = fp64 ? maxwell_fused_attr<double, 2>() : maxwell_fused_attr<float, 2>();
+    return e;
 }
 
 cudaError_t launch_filter(int fp64, const Launch &L, const long long *const pencil_start[3],

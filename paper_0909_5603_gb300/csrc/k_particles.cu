@@ -5,169 +5,20 @@
 
 namespace pic {
 
-// -------------------------------------------------------------------------------------
-// Tile population scan: one CTA per instance.  mode 0 (step): lays out the output
-// layout (segment starts and chunk bases) from the populations, zeroes them, flips the
-// parity and counts the particle phase.  mode 1 (read-out): writes the exclusive scan of the populations into
-// `dst` (one int per tile + total) and the total into *live, changing nothing else.
-// -------------------------------------------------------------------------------------
-// The same table computed by one warp per tile ahead of the particle kernel (no block
-// barriers, at full occupancy), stored as the tile's source record: the particle count,
-// the number of non-empty sub-ranges (-1 when more than kSubCache) and their first slots
-// and positions.  The particle kernel loads it in one coalesced read and builds the table
-// itself only for a tile whose record overflowed.
-struct SrcScratch {
-    int n;
-    int dir[kDirs], seg[kDirs], c0[kDirs];
-    int chpre[kDirs + 1];
-};
-
+// Source records of every tile, one warp per tile (tile_sources_warp).
 __global__ void __launch_bounds__(256) k_tile_sources(Launch L)
 {
     __shared__ SrcScratch W[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x * 8 + warp;
     if (g >= L.total_tiles) return;  // the whole warp
-    const int ii = find_instance(L.tile_start, L.ninst, g);
-    const InstDev &I = L.inst[ii];
-    const int t = g - L.tile_start[ii];
-    const int lay = 1 - *I.cur;  // the input layout of the coming phase (the scan flipped it)
-    const int tx = t % I.nt[0], ty = (t / I.nt[0]) % I.nt[1], tz = t / (I.nt[0] * I.nt[1]);
-    SrcScratch &S = W[warp];
-    const int *pre = I.chunk_pre[lay];
-    int dx[3], sx[3], dy[3], sy[3], dz[3], sz[3];
-    const int mx = axis_sources(tx, I.nt[0], I.bc[0], dx, sx);
-    const int my = I.ndim == 3 ? axis_sources(ty, I.nt[1], I.bc[1], dy, sy) : 1;
-    if (I.ndim != 3) { dy[0] = 0; sy[0] = 0; }
-    const int mz = axis_sources(tz, I.nt[2], I.bc[2], dz, sz);
-    const int n = mx * my * mz;
-    int nch = 0;
-    if (lane < n) {
-        const int c = lane % mx, b = (lane / mx) % my, a = lane / (mx * my);
-        const int st = sx[c] + I.nt[0] * (sy[b] + I.nt[1] * sz[a]);
-        const int d = (dz[a] + 1) * 9 + (dy[b] + 1) * 3 + (dx[c] + 1);
-        const int c0 = I.chunk_base[lay][st];
-        nch = I.chunk_base[lay][st + 1] - c0;
-        S.dir[lane] = d;
-        S.seg[lane] = I.seg[lay][st];
-        S.c0[lane] = c0;
-    }
-    int pn = nch;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int yn = __shfl_up_sync(0xffffffffu, pn, o);
-        if (lane >= o) pn += yn;
-    }
-    if (lane < n) S.chpre[lane] = pn - nch;
-    if (lane == n - 1) S.chpre[n] = pn;
-    __syncwarp();
-    const int npairs = S.chpre[n];
-    int *rec = I.srcrec + (size_t)t * kSrcRec;
-    int written = 0, slot_run = 0;
-    bool fits = true;
-    for (int q0 = 0; q0 < npairs; q0 += 32) {
-        const int q = q0 + lane;
-        int cntq = 0, posq = 0;
-        if (q < npairs) {
-            int s = 0, top = n - 1;
-            while (s < top) {
-                const int mid = (s + top + 1) >> 1;
-                if (S.chpre[mid] <= q) s = mid; else top = mid - 1;
-            }
-            const int k = q - S.chpre[s];
-            const long long c = S.c0[s] + k;
-            const int d = S.dir[s];
-            const int p0 = pre[c * kPre + d];
-            cntq = pre[c * kPre + d + 1] - p0;
-            posq = S.seg[s] + k * I.R + p0;
-        }
-        const int ne = cntq > 0 ? 1 : 0;
-        int ic = cntq, in_ = ne;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y1 = __shfl_up_sync(0xffffffffu, ic, o);
-            const int y2 = __shfl_up_sync(0xffffffffu, in_, o);
-            if (lane >= o) { ic += y1; in_ += y2; }
-        }
-        const int tot_cnt = __shfl_sync(0xffffffffu, ic, 31), tot_ne = __shfl_sync(0xffffffffu, in_, 31);
-        if (written + tot_ne > kSubCache) fits = false;
-        if (fits && ne) {
-            rec[kRecSlot + written + in_ - 1] = slot_run + ic - cntq;
-            rec[kRecPos + written + in_ - 1] = posq;
-        }
-        written += tot_ne;
-        slot_run += tot_cnt;
-    }
-    if (lane == 0) {
-        rec[0] = slot_run;
-        rec[1] = fits ? written : -1;
-        if (fits) rec[kRecSlot + written] = slot_run;
-    }
+    tile_sources_warp(L, g, W[warp], lane);
 }
 
+// Tile population scan, one CTA per instance (scan_instance).
 __global__ void __launch_bounds__(1024) k_scan(Launch L, int mode, int *const *dst)
 {
-    const InstDev &I = L.inst[blockIdx.x];
-    __shared__ int s_warp[32], s_warp2[32];
-    __shared__ int s_carry, s_carry2;
-    const int cur = *I.cur;
-    const int out = 1 - cur;
-    const int nt = I.ntiles;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) { s_carry = 0; s_carry2 = 0; }
-    __syncthreads();
-    for (int base = 0; base < nt; base += 1024) {
-        const int t = base + tid;
-        const int p = t < nt ? I.pop[t] : 0;
-        const int ch = (p + I.R - 1) / I.R;
-        int a = p, b = ch;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int x = __shfl_up_sync(0xffffffffu, a, o);
-            const int y = __shfl_up_sync(0xffffffffu, b, o);
-            if (lane >= o) { a += x; b += y; }
-        }
-        if (lane == 31) { s_warp[warp] = a; s_warp2[warp] = b; }
-        __syncthreads();
-        if (warp == 0) {
-            int x = s_warp[lane], y = s_warp2[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int xx = __shfl_up_sync(0xffffffffu, x, o);
-                const int yy = __shfl_up_sync(0xffffffffu, y, o);
-                if (lane >= o) { x += xx; y += yy; }
-            }
-            s_warp[lane] = x;
-            s_warp2[lane] = y;
-        }
-        __syncthreads();
-        const int ex = s_carry + (warp ? s_warp[warp - 1] : 0) + a - p;
-        const int ex2 = s_carry2 + (warp ? s_warp2[warp - 1] : 0) + b - ch;
-        if (t < nt) {
-            if (mode == 0) {
-                I.seg[out][t] = ex;
-                I.chunk_base[out][t] = ex2;
-                I.pop[t] = 0;
-            } else {
-                dst[blockIdx.x][t] = ex;
-            }
-        }
-        __syncthreads();
-        if (tid == 0) { s_carry += s_warp[31]; s_carry2 += s_warp2[31]; }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        if (mode == 0) {
-            I.seg[out][nt] = s_carry;
-            I.chunk_base[out][nt] = s_carry2;
-            if (s_carry > I.cap || s_carry2 > I.chunk_cap) atomicOr(I.err, kErrCapacity);
-            *I.cur = out;
-            *I.phase += 1;  // one more particle phase (the ion current read the old count)
-        } else {
-            dst[blockIdx.x][nt] = s_carry;
-        }
-        *I.live = s_carry;
-    }
+    scan_instance(L, blockIdx.x, mode, dst);
 }
 
 // -------------------------------------------------------------------------------------

@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(256) k_station_record(const InstDev *Ip, Stati
     double zp, tp;
     if (!station_plane(I, S.z_lab[st], zp, tp)) return;
     const int i = e % I.n[0], j = e / I.n[0];
-    const void *F[6] = {I.E[0], I.E[1], I.E[2], I.B[0], I.B[1], I.B[2]};
+    const EBPtr cur = cur_eb(I);
+    const void *F[6] = {cur.E[0], cur.E[1], cur.E[2], cur.B[0], cur.B[1], cur.B[2]};
     const double zst[6] = {0.0, 0.0, 0.5, 0.5, 0.5, 0.0};  // z stagger: Ex Ey Ez Bx By Bz
     double f[6];
 #pragma unroll

@@ -54,7 +54,7 @@ struct pic_ctx {
     bool any_periodic[3] = {false, false, false};
     int max_sweeps = 0;
     long long *d_pencil = nullptr;       // per axis: [ninst + 1] filter pencil offsets (device)
-    long long pencil_total[3] = {0, 0, 0};
+    long long pencil_total[4] = {0, 0, 0, 0};  // [3]: tiles of the fused Yee update
     std::vector<Block> blocks;
     uint64_t version = 1;  // bumps when device pointers of the instance change
     // state
@@ -281,8 +281,9 @@ static pic_status encode_tmaps(pic_ctx *c, CUtensorMap *maps)
     const cuuint64_t strides[2] = {(cuuint64_t)c->h.sy * c->es, (cuuint64_t)c->h.sz * c->es};
     const cuuint32_t box[3] = {(cuuint32_t)c->h.box[0], (cuuint32_t)c->h.box[1], (cuuint32_t)c->h.box[2]};
     const cuuint32_t estr[3] = {1, 1, 1};
-    for (int comp = 0; comp < 6; ++comp) {
-        void *base = comp < 3 ? c->h.E[comp] : c->h.B[comp - 3];
+    for (int comp = 0; comp < 12; ++comp) {
+        const int f = comp % 6;
+        void *base = comp < 6 ? (f < 3 ? c->h.E[f] : c->h.B[f - 3]) : (f < 3 ? c->h.E2[f] : c->h.B2[f - 3]);
         CUresult r = enc(&maps[comp], c->fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
                          dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -443,13 +444,14 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     }
     c->max_sweeps = o.filter_passes * (c->ndim == 3 ? 3 : 2);
 
-    // device memory: 12 field components (E, B, J, J scratch), bookkeeping, scratch
-    const size_t fbytes = 12 * (size_t)h.cstride * c->es;
+    // device memory: 18 field components (E, B, J, J scratch, the second E and B),
+    // bookkeeping, scratch
+    const size_t fbytes = 18 * (size_t)h.cstride * c->es;
     unsigned char *F = (unsigned char *)dalloc(c, fbytes);
     int *small = (int *)dalloc(c, 4096);
     int nt1 = h.ntiles + 1;
     int *tiles = (int *)dalloc(c, sizeof(int) * (size_t)(4 * nt1 + 2 * h.ntiles * kBuckets + h.ntiles + 64));
-    CUtensorMap *tm = (CUtensorMap *)dalloc(c, 6 * sizeof(CUtensorMap));
+    CUtensorMap *tm = (CUtensorMap *)dalloc(c, 12 * sizeof(CUtensorMap));
     c->d_inst = (InstDev *)dalloc(c, sizeof(InstDev));
     c->d_tile_start = (int *)dalloc(c, 2 * sizeof(int));
     c->d_cell_start = (long long *)dalloc(c, 2 * sizeof(long long));
@@ -457,7 +459,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     c->d_sums = (double *)dalloc(c, 64 * sizeof(double));
     c->d_start = (int *)dalloc(c, sizeof(int) * (size_t)nt1);
     c->d_start_ptr = (int **)dalloc(c, sizeof(int *));
-    c->d_pencil = (long long *)dalloc(c, 6 * sizeof(long long));
+    c->d_pencil = (long long *)dalloc(c, 8 * sizeof(long long));
     h.ion_face = dalloc(c, sizeof(double) * (size_t)c->n[2]);
     h.srcrec = (int *)dalloc(c, sizeof(int) * (size_t)h.ntiles * kSrcRec);
     if (!F || !small || !tiles || !tm || !c->d_inst || !c->d_tile_start || !c->d_cell_start || !c->d_dense || !c->d_sums ||
@@ -471,6 +473,8 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
         h.B[a] = F + (size_t)(3 + a) * h.cstride * c->es;
         h.J[a] = F + (size_t)(6 + a) * h.cstride * c->es;
         h.Jt[a] = F + (size_t)(9 + a) * h.cstride * c->es;
+        h.E2[a] = F + (size_t)(12 + a) * h.cstride * c->es;
+        h.B2[a] = F + (size_t)(15 + a) * h.cstride * c->es;
     }
     h.cur = small;
     h.err = small + 1;
@@ -478,6 +482,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     h.jsel = small + 3;
     h.lost = (unsigned long long *)(small + 4);
     h.phase = small + 6;
+    h.fpar = small + 8;
     h.seg[0] = tiles;
     h.seg[1] = tiles + nt1;
     h.chunk_base[0] = tiles + 2 * nt1;
@@ -520,16 +525,16 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     }
 
     pic_status st = PIC_OK;
-    CUtensorMap maps[6];
+    CUtensorMap maps[12];
     if ((st = encode_tmaps(c, maps)) != PIC_OK) {
         std::string e = c->err;
         dfree_all(c);
         delete c;
         return fail(nullptr, st, "%s", e.c_str());
     }
-    long long pencils[6];
-    for (int a = 0; a < 3; ++a) {
-        c->pencil_total[a] = o.filter_passes > 0 ? filter_pencils(c->n, c->ndim, a) : 0;
+    long long pencils[8];
+    for (int a = 0; a < 4; ++a) {
+        c->pencil_total[a] = a == 3 ? maxwell_tiles(c->n, c->ndim) : o.filter_passes > 0 ? filter_pencils(c->n, c->ndim, a) : 0;
         pencils[2 * a] = 0;
         pencils[2 * a + 1] = c->pencil_total[a];
     }
@@ -544,6 +549,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
                cudaMemcpyAsync(c->d_start_ptr, &dptr_start, sizeof(int *), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
                cudaMemcpyAsync(c->d_pencil, pencils, sizeof(pencils), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
                prepare_particles(c->ndim, c->order, c->fp64, o.pusher, c->smem) == cudaSuccess &&
+               prepare_fields(c->fp64) == cudaSuccess &&
                noalloc_load_grid(c->order, c->fp64) == cudaSuccess;
     if (!okc || upload_inst(c) != PIC_OK) {
         cudaError_t e = cudaGetLastError();
@@ -1083,7 +1089,8 @@ extern "C" pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *lase
     LabFields F;
     transform_lab_inputs(G, ctx->gamma_b, laser, on_device ? nullptr : plasma, beam, P, F);
     // fields: zero except the laser and the beam's self-field
-    CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->h.E[0], 0, 12 * (size_t)ctx->h.cstride * ctx->es, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->h.E[0], 0, 18 * (size_t)ctx->h.cstride * ctx->es, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->h.fpar, 0, sizeof(int), ctx->stream));
     pic_status st;
     for (int c = 0; c < 6; ++c)
         if (!F.comp[c].empty() && (st = set_field_internal(ctx, PIC_EX + c, F.comp[c].data())) != PIC_OK) return st;
@@ -1217,7 +1224,13 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
         if (c->ant_on) ants.push_back(c);
         for (auto m : c->members)
             if (m->ant_on) ants.push_back(m);
-        if (ants.empty()) {
+        if (ants.empty() && c->opt.solver == PIC_SOLVER_YEE && c->pencil_total[3] > 0) {
+            // the fused update: one launch, then the buffer switch
+            const int nin = c->is_batch ? (int)c->members.size() : 1;
+            CUDA_OR_FAIL(c, launch_maxwell_fused(fp64, c->ndim, L, c->d_pencil + 3 * (nin + 1), c->pencil_total[3], filtered,
+                                                 c->stream));
+            launches += 2;
+        } else if (ants.empty()) {
             CUDA_OR_FAIL(c, launch_maxwell(fp64, c->opt.solver, L, filtered, c->stream));
             launches += 3;
         } else {
@@ -1254,6 +1267,12 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
         CUDA_OR_FAIL(c, launch_stations(fp64, c->d_inst, S, c->nst, c->n[0] * c->n[1], c->stream));
         tm.end(4);
         launches += 2;
+    }
+    if (mask & PIC_PHASE_PARTICLES) {
+        // J now holds this phase's deposit; a filtered copy from an earlier step is stale
+        c->last_filtered = 0;
+        if (c->is_batch)
+            for (auto m : c->members) m->last_filtered = 0;
     }
     if (mask & (PIC_PHASE_FILTER | PIC_PHASE_MAXWELL)) {
         c->last_filtered = filtered;
@@ -1524,7 +1543,7 @@ extern "C" pic_status pic_get_planes(pic_ctx *ctx, int comp, int k0, int nk, dou
     if (st != PIC_OK) return st;
     if ((st = pic_synchronize(ctx)) != PIC_OK) return st;
     const size_t n = (size_t)nk * ctx->n[0] * ctx->n[1];
-    CUDA_OR_FAIL(ctx, launch_pack_planes(ctx->fp64, ctx->h, comp, 0, ctx->d_dense, k0, nk, ctx->stream));
+    CUDA_OR_FAIL(ctx, launch_pack_planes(ctx->fp64, ctx->h, comp, ctx->last_filtered, ctx->d_dense, k0, nk, ctx->stream));
     CUDA_OR_FAIL(ctx, cudaMemcpyAsync(host_out, ctx->d_dense, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
     return check_device_error(ctx);
@@ -1875,8 +1894,8 @@ static pic_status refresh_batch(pic_ctx *c)
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_inst, insts.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, c->stream));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_tile_start, ts.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, c->stream));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_cell_start, cs.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, c->stream));
-    std::vector<long long> ps((size_t)3 * (n + 1), 0);
-    for (int a = 0; a < 3; ++a) {
+    std::vector<long long> ps((size_t)4 * (n + 1), 0);
+    for (int a = 0; a < 4; ++a) {
         for (int i = 0; i < n; ++i) ps[(size_t)a * (n + 1) + i + 1] = ps[(size_t)a * (n + 1) + i] + c->members[i]->pencil_total[a];
         c->pencil_total[a] = ps[(size_t)a * (n + 1) + n];
     }
@@ -1922,7 +1941,7 @@ extern "C" pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx
     c->d_inst = (InstDev *)dalloc(c, sizeof(InstDev) * n);
     c->d_tile_start = (int *)dalloc(c, sizeof(int) * (n + 1));
     c->d_cell_start = (long long *)dalloc(c, sizeof(long long) * (n + 1));
-    c->d_pencil = (long long *)dalloc(c, sizeof(long long) * 3 * (n + 1));
+    c->d_pencil = (long long *)dalloc(c, sizeof(long long) * 4 * (n + 1));
     if (!c->d_inst || !c->d_tile_start || !c->d_cell_start || !c->d_pencil) {
         dfree_all(c);
         delete c;

@@ -96,8 +96,12 @@ struct InstDev {
     double dt, dx[3], q, m;
     StepCoef<float> cf;   // FP32 instances
     StepCoef<double> cd;  // FP64 instances
-    // fields (element type set by the precision of the launch)
+    // fields (element type set by the precision of the launch).  E and B have two
+    // buffers: the fused Maxwell update reads one pair and writes the other, then flips
+    // *fpar; every reader takes the current pair through cur_eb / eb_field.
     void *E[3], *B[3], *J[3], *Jt[3];  // Jt: scratch for filter sweeps
+    void *E2[3], *B2[3];               // the second E / B buffer
+    int *fpar;                         // 0: E, B current; 1: E2, B2
     // particles, two buffers
     int *cell[2];
     void *off[2][3];
@@ -117,7 +121,8 @@ struct InstDev {
     int *err;           // sticky error word
     unsigned long long *lost; // particles removed so far
     int *live;          // live particles (written by the scan)
-    const CUtensorMap *tmap;  // 6 maps: Ex Ey Ez Bx By Bz boxes for the gather stage
+    const CUtensorMap *tmap;  // 12 maps: Ex Ey Ez Bx By Bz boxes for the gather stage, for
+                              // buffer 0 then buffer 1
     const void *damp[3];      // absorbing-layer factor per cell index along each axis
                               // (working precision; null on periodic / inactive axes)
     FastDiv div_n0, div_n1;   // cell index -> (i, j, k)
@@ -150,6 +155,30 @@ template <>
 __host__ __device__ __forceinline__ const StepCoef<float> &coef<float>(const InstDev &I) { return I.cf; }
 template <>
 __host__ __device__ __forceinline__ const StepCoef<double> &coef<double>(const InstDev &I) { return I.cd; }
+
+// The E / B buffer pair holding the current fields (read once per kernel).
+struct EBPtr {
+    void *E[3], *B[3];
+};
+
+__device__ __forceinline__ EBPtr cur_eb(const InstDev &I)
+{
+    const int par = *(volatile const int *)I.fpar;
+    EBPtr f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f.E[a] = par ? I.E2[a] : I.E[a];
+        f.B[a] = par ? I.B2[a] : I.B[a];
+    }
+    return f;
+}
+
+// Current buffer of field component comp (0..5: Ex Ey Ez Bx By Bz).
+__device__ __forceinline__ void *eb_field(const InstDev &I, int comp)
+{
+    const int par = *(volatile const int *)I.fpar;
+    return comp < 3 ? (par ? I.E2[comp] : I.E[comp]) : (par ? I.B2[comp - 3] : I.B[comp - 3]);
+}
 
 // launch-wide view of a set of instances stepped together
 struct Launch {

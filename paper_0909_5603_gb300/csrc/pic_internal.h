@@ -70,6 +70,18 @@ cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, i
                            void *w, int *id, cudaStream_t s);
 cudaError_t launch_particle_sums(int fp64, const Launch &L, double *sums, cudaStream_t s);
 cudaError_t launch_rho(int order, int fp64, const Launch &L, double *rho, cudaStream_t s);
+// opt-in to the shared memory of the fused Yee update (once per device and precision)
+cudaError_t prepare_fields(int fp64);
+// the whole Yee update of the step (Yee solver, no antenna) in one launch over
+// maxwell_tiles() tiles per instance, then the switch of every instance to the E / B
+// buffer pair it wrote
+cudaError_t launch_maxwell_fused(int fp64, int ndim, const Launch &L, const long long *tile_start, long long ntiles,
+                                 int filtered, cudaStream_t s);
+inline long long maxwell_tiles(const int n[3], int ndim)
+{
+    return ndim == 3 ? (long long)((n[0] + 31) / 32) * ((n[1] + 7) / 8) * ((n[2] + 31) / 32)
+                     : (long long)((n[0] + 255) / 256) * ((n[2] + 31) / 32);
+}
 // passes: the filter passes of every instance of the launch (0 when they differ)
 cudaError_t launch_filter(int fp64, const Launch &L, const long long *const pencil_start[3],
                           const long long pencil_total[3], int ndim, int passes, cudaStream_t s);
