@@ -537,7 +537,21 @@ def batched_scan(pic, torch, count=256, steps=10, steps64=3, warmup=3):
     out = {"instances": count, "particles": int(nb), "cells": int(cells), "steps": steps,
            "load_seconds": round(load_s, 2), "ms_per_step": ms,
            "particle_steps_per_s": 0.5 * (nb + na) / (ms * 1e-3),
-           "cell_updates_per_s": cells / (ms * 1e-3), "dtype": "f32"}
+           "cell_updates_per_s": cells / (ms * 1e-3), "dtype": "f32",
+           "launch": "per-phase kernels over all instances, one CUDA graph replay per step"}
+    # the same batch as one persistent launch per call (every step of the call)
+    batch.set_persistent(True)
+    batch.step(1)
+    batch.synchronize()
+    nbp = sum(s.num_particles() for s in sims)
+    e0.record(stream)
+    batch.step(steps)
+    e1.record(stream)
+    batch.synchronize()
+    msp = e0.elapsed_time(e1) / steps
+    nap = sum(s.num_particles() for s in sims)
+    out["persistent"] = {"ms_per_step": msp, "particle_steps_per_s": 0.5 * (nbp + nap) / (msp * 1e-3),
+                         "launch": f"one persistent launch for the {steps} steps"}
     batch.close()
     del sims, batch
     torch.cuda.empty_cache()

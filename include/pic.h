@@ -304,6 +304,20 @@ pic_status pic_synchronize(pic_ctx *ctx);
  * pic_set_profiling, pic_get_timings and pic_destroy accept a batch. */
 pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx **batch);
 
+/* Persistent batched step (the paper has no counterpart; it serves the batch above).
+ * With on = 1, every later pic_step(batch, n) runs its n steps in ONE launch of a
+ * persistent kernel: CTAs pull (step, phase, instance, item) work items from a device
+ * list and each item waits only until its own instance has completed its previous phase,
+ * so the instances of an uneven batch do not wait for one another at phase boundaries.
+ * Each wait is bounded by spin_limit polls (<= 0: 2^21, about a second); a wait that
+ * gives up sets PIC_ERR_TIMEOUT on its instance (reported by the next synchronising
+ * call) and ends the launch.  test_stall >= 0 makes that instance's J set-up wait for an
+ * item that never runs, to exercise the timeout (-1: off).  Members must be FP32, Vay,
+ * Yee, with one filter pass count <= 4 and no antenna, injection plane or stations (else
+ * PIC_ERR_UNSUPPORTED); pic_run_phases and profiled steps keep the per-phase launches.
+ * on = 0 returns to the per-phase CUDA graph.  Not valid on a member (PIC_ERR_ARG). */
+pic_status pic_batch_set_persistent(pic_ctx *batch, int on, long long spin_limit, int test_stall);
+
 /* Lab-frame stations (Sec. 2: the results are recorded at planes immobile in the
  * laboratory frame and transformed back to it).  Replaces the stations with `count`
  * planes z = z_lab[i] (lab coordinates; lab and boosted frames share their origin at

@@ -36,7 +36,7 @@ EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error"
             "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc", "pic_autotune",
             "pic_set_stations", "pic_get_station", "pic_set_injection", "pic_set_laser_antenna",
             "pic_get_fields", "pic_get_gauss_residual", "pic_get_planes", "pic_put_planes",
-            "pic_extract_particles", "pic_add_particles", "pic_adopt_slab"]
+            "pic_extract_particles", "pic_add_particles", "pic_adopt_slab", "pic_batch_set_persistent"]
 PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
@@ -167,6 +167,8 @@ def lib():
                                             P(ctypes.c_int64)]
         L.pic_add_particles.restype = st
         L.pic_add_particles.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.pic_batch_set_persistent.restype = st
+        L.pic_batch_set_persistent.argtypes = [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int]
         L.pic_adopt_slab.restype = st
         L.pic_adopt_slab.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.pic_autotune.restype = st
@@ -489,6 +491,10 @@ class Batch:
 
     def step(self, n=1):
         _check(lib().pic_step(self.h, n), self.h)
+
+    def set_persistent(self, on=True, spin_limit=0, test_stall=-1):
+        """pic_batch_set_persistent: each step() call as one persistent launch."""
+        _check(lib().pic_batch_set_persistent(self.h, 1 if on else 0, int(spin_limit), int(test_stall)), self.h)
 
     def synchronize(self):
         _check(lib().pic_synchronize(self.h), self.h)

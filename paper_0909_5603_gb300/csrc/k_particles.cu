@@ -18,7 +18,8 @@ __global__ void __launch_bounds__(256) k_tile_sources(Launch L)
 // Tile population scan, one CTA per instance (scan_instance).
 __global__ void __launch_bounds__(1024) k_scan(Launch L, int mode, int *const *dst)
 {
-    scan_instance(L, blockIdx.x, mode, dst);
+    __shared__ int sh[66];
+    scan_instance(L, blockIdx.x, mode, dst, sh);
 }
 
 // -------------------------------------------------------------------------------------

@@ -508,11 +508,12 @@ __device__ __forceinline__ void tile_sources_warp(const Launch &L, int g, SrcScr
 // the populations, zeroes them, flips the parity and counts the particle phase.  mode 1
 // (read-out): writes the exclusive scan of the populations into dst[ii] (one int per
 // tile + total) and the total into *live, changing nothing else.
-__device__ __forceinline__ void scan_instance(const Launch &L, int ii, int mode, int *const *dst)
+// sh: 66 ints of shared memory.
+__device__ __forceinline__ void scan_instance(const Launch &L, int ii, int mode, int *const *dst, int *sh)
 {
     const InstDev &I = L.inst[ii];
-    __shared__ int s_warp[32], s_warp2[32];
-    __shared__ int s_carry, s_carry2;
+    int *s_warp = sh, *s_warp2 = sh + 32;
+    int &s_carry = sh[64], &s_carry2 = sh[65];
     const int cur = *I.cur;
     const int out = 1 - cur;
     const int nt = I.ntiles;

@@ -85,6 +85,13 @@ struct pic_ctx {
     double *st_off = nullptr, *st_u = nullptr, *st_w = nullptr;
     // graph
     cudaGraphExec_t graph = nullptr;
+    // persistent batched step (pic_batch_set_persistent)
+    bool persistent = false;
+    long long spin_limit = 0;
+    int stall_inst = -1;
+    PersistPlan *plan = nullptr;
+    size_t persist_smem = 0;
+    int persist_grid = 0;
     // profiling
     bool profiling = false;
     std::vector<cudaEvent_t> events;
@@ -583,6 +590,7 @@ extern "C" void pic_destroy(pic_ctx *ctx)
     destroy_graph(ctx);
     for (auto e : ctx->events) cudaEventDestroy(e);
     dfree_all(ctx);
+    delete ctx->plan;
     delete ctx;
 }
 
@@ -1300,6 +1308,20 @@ extern "C" pic_status pic_step(pic_ctx *ctx, int n)
     } else if (!ctx->loaded) {
         return fail(ctx, PIC_ERR_STATE, "pic_step before any load");
     }
+    if (ctx->is_batch && ctx->persistent && !ctx->profiling && n > 0) {
+        // every step in one launch of the persistent kernel
+        const int nin = (int)ctx->members.size();
+        const pic_ctx *m0 = ctx->members[0];
+        const int filtered = ctx->max_sweeps > 0 ? 1 : 0;
+        CUDA_OR_FAIL(ctx, ctx->plan->launch(ctx->L, ctx->ndim, ctx->order, n, m0->opt.filter_passes, filtered, ctx->d_pencil,
+                                            ctx->d_pencil + 3 * (nin + 1), ctx->persist_smem, ctx->persist_grid,
+                                            ctx->spin_limit, ctx->stall_inst, ctx->stream));
+        ctx->step += n;
+        ctx->mx_phases += n;
+        for (auto m : ctx->members) m->step += n, m->mx_phases += n, m->last_filtered = filtered;
+        ctx->last_filtered = filtered;
+        return PIC_OK;
+    }
     for (int s = 0; s < n; ++s) {
         if (ctx->profiling || ctx->stream == nullptr) {
             pic_status st = enqueue_step(ctx, PIC_PHASE_ALL);
@@ -1906,6 +1928,64 @@ static pic_status refresh_batch(pic_ctx *c)
     c->member_versions.clear();
     for (auto m : c->members) c->member_versions.push_back(m->version);
     destroy_graph(c);
+    return PIC_OK;
+}
+
+static void *plan_alloc(void *user, size_t bytes) { return dalloc((pic_ctx *)user, bytes); }
+
+extern "C" pic_status pic_batch_set_persistent(pic_ctx *batch, int on, long long spin_limit, int test_stall)
+{
+    if (!batch) return PIC_ERR_ARG;
+    if (!batch->is_batch) return fail(batch, PIC_ERR_ARG, "pic_batch_set_persistent takes a batch");
+    cudaSetDevice(batch->device);
+    CUDA_OR_FAIL(batch, cudaStreamSynchronize(batch->stream));
+    if (!on) {
+        batch->persistent = false;
+        return PIC_OK;
+    }
+    const int n = (int)batch->members.size();
+    if (test_stall < -1 || test_stall >= n) return fail(batch, PIC_ERR_ARG, "test_stall %d outside -1 .. %d", test_stall, n - 1);
+    const int passes = batch->members[0]->opt.filter_passes;
+    for (auto m : batch->members) {
+        if (m->fp64) return fail(batch, PIC_ERR_UNSUPPORTED, "the persistent step runs FP32 instances");
+        if (m->opt.pusher != PIC_PUSHER_VAY) return fail(batch, PIC_ERR_UNSUPPORTED, "the persistent step runs the Vay pusher");
+        if (m->opt.solver != PIC_SOLVER_YEE) return fail(batch, PIC_ERR_UNSUPPORTED, "the persistent step runs the Yee solver");
+        if (m->ant_on || m->inj_on || m->nst > 0)
+            return fail(batch, PIC_ERR_UNSUPPORTED, "the persistent step runs without antenna, injection plane and stations");
+        if (m->opt.filter_passes != passes || passes > 4)
+            return fail(batch, PIC_ERR_UNSUPPORTED, "the persistent step needs one filter pass count of at most 4");
+    }
+    if (!batch->plan) {
+        std::vector<PersistCounts> counts(n);
+        for (int i = 0; i < n; ++i) {
+            const pic_ctx *m = batch->members[i];
+            PersistCounts &k = counts[i];
+            k.ncell = m->ncell;
+            k.ntiles = m->h.ntiles;
+            for (int a = 0; a < 3; ++a) {
+                k.pencils[a] = m->pencil_total[a];
+                const int o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
+                k.ghost[a] = m->any_periodic[a] ? 6LL * 2 * m->h.gh[a] * m->h.P[o1] * m->h.P[o2] : 0;
+            }
+            k.mx_tiles = m->pencil_total[3];
+        }
+        PersistPlan *plan = new PersistPlan;
+        cudaError_t e = plan->build(counts, plan_alloc, batch);
+        if (e != cudaSuccess) {
+            delete plan;
+            return fail(batch, e == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA, "work list: %s", cudaGetErrorString(e));
+        }
+        batch->plan = plan;
+        batch->persist_smem = persist_smem(batch->ndim, batch->smem);
+        int bps = 0, sms = 0;
+        CUDA_OR_FAIL(batch, persist_blocks_per_sm(batch->ndim, batch->order, batch->persist_smem, &bps));
+        CUDA_OR_FAIL(batch, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, batch->device));
+        if (bps < 1) return fail(batch, PIC_ERR_UNSUPPORTED, "the persistent kernel does not fit an SM");
+        batch->persist_grid = bps * sms;
+    }
+    batch->spin_limit = spin_limit > 0 ? spin_limit : (1LL << 21);
+    batch->stall_inst = test_stall;
+    batch->persistent = true;
     return PIC_OK;
 }
 

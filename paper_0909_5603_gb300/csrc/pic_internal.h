@@ -4,6 +4,8 @@
 
 #include "pic_instance.h"
 
+#include <vector>
+
 namespace pic {
 
 // FP64 particles to place in the canonical order (device arrays, 3 values per particle
@@ -70,6 +72,40 @@ cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, i
                            void *w, int *id, cudaStream_t s);
 cudaError_t launch_particle_sums(int fp64, const Launch &L, double *sums, cudaStream_t s);
 cudaError_t launch_rho(int order, int fp64, const Launch &L, double *rho, cudaStream_t s);
+// ---- persistent batched step (k_persist.cu)
+// sizes of one instance that set its work items per phase
+struct PersistCounts {
+    long long ncell;
+    int ntiles;
+    long long pencils[3];  // filter pencils per axis
+    long long mx_tiles;    // fused Yee tiles
+    long long ghost[3];    // periodic ghost-copy elements per axis (0: not periodic)
+};
+// The device work list of a batch (per-phase item offsets and the launch's counters).
+class PersistPlan {
+  public:
+    struct Impl;
+    PersistPlan();
+    ~PersistPlan();
+    PersistPlan(const PersistPlan &) = delete;
+    PersistPlan &operator=(const PersistPlan &) = delete;
+    // device memory from alloc(user, bytes), owned by the caller's context
+    cudaError_t build(const std::vector<PersistCounts> &inst, void *(*alloc)(void *, size_t), void *user);
+    long long items_per_step() const;
+    // nsteps steps of the batch in one launch of grid CTAs (kNT threads, smem bytes of
+    // dynamic shared memory); pencil_tables: the three per-axis pencil offset tables,
+    // mx_start: the fused Yee tile offsets
+    cudaError_t launch(const Launch &L, int ndim, int order, int nsteps, int passes, int filtered,
+                       const long long *pencil_tables, const long long *mx_start, size_t smem, int grid,
+                       long long spin_limit, int stall_inst, cudaStream_t s);
+
+  private:
+    Impl *impl;
+};
+// dynamic shared memory of the persistent kernel, and its resident CTAs per SM
+size_t persist_smem(int ndim, size_t particle_smem);
+cudaError_t persist_blocks_per_sm(int ndim, int order, size_t smem, int *bps);
+
 // opt-in to the shared memory of the fused Yee update (once per device and precision)
 cudaError_t prepare_fields(int fp64);
 // the whole Yee update of the step (Yee solver, no antenna) in one launch over
