@@ -53,8 +53,8 @@ struct PersistDesc {
     int stall_inst;                       // test: this instance's J set-up waits for an item that never runs
 };
 
-constexpr int kJInitCells = 256;  // cells per J set-up item
-constexpr int kGhostElems = 256;  // elements per ghost-copy item
+constexpr int kJInitCells = 4096;  // cells per J set-up item (16 per thread)
+constexpr int kGhostElems = 4096;  // elements per ghost-copy item
 
 __device__ __forceinline__ int ld_acquire(const int *p)
 {
@@ -170,9 +170,8 @@ __global__ void __launch_bounds__(kNT, 2) k_step_persistent(Launch L, PersistDes
             ion_faces_of<float>(I, tid, kNT);
             break;
         case kPhJInit: {
-            const long long r = local * kJInitCells + tid;
             const long long ncell = (long long)I.n[0] * I.n[1] * I.n[2];
-            if (r < ncell) {
+            for (long long r = local * kJInitCells + tid; r < min(ncell, (local + 1) * kJInitCells); r += kNT) {
                 const int rq = fast_div((int)r, I.div_n0);
                 const int i = (int)r - rq * I.n[0];
                 const int k = fast_div(rq, I.div_n1);
@@ -216,8 +215,8 @@ __global__ void __launch_bounds__(kNT, 2) k_step_persistent(Launch L, PersistDes
             break;
         default: {  // ghost copies
             const int axis = p - kPhGhostX;
-            const long long r = local * kGhostElems + tid;
-            if (r < ghost_elems(I, axis)) ghost_elem<float>(I, axis, r);
+            const long long ne = min(ghost_elems(I, axis), (local + 1) * kGhostElems);
+            for (long long r = local * kGhostElems + tid; r < ne; r += kNT) ghost_elem<float>(I, axis, r);
             break;
         }
         }
