@@ -99,6 +99,21 @@ def issue_roofline(kern_ms, particles, clocks):
             "frac": achieved / peak, "warp_instructions_per_particle": per, "sm_mhz": mhz}
 
 
+def smem_roofline(kern_ms, particles, clocks):
+    """The shared-memory pipe of the particle kernel (gather loads, deposit atomics, tile
+    folds): shared-memory wavefronts per launch (the capture's count per particle times
+    the particles) over the measured launch time, against one wavefront per SM-cycle on
+    152 SMs at the sampled SM clock.  None when the capture is stale or absent."""
+    per = profiled_value("shared_wavefronts_per_particle")
+    if per is None or not kern_ms or kern_ms <= 0:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    achieved = per * particles / (kern_ms * 1e-3) / 1e9
+    peak = 152 * mhz * 1e-3
+    return {"bound": "shared-memory wavefronts", "achieved": achieved, "peak": peak, "unit": "G wavefronts/s",
+            "frac": achieved / peak, "wavefronts_per_particle": per, "sm_mhz": mhz}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -385,6 +400,7 @@ def run_ours(args, rank, world):
             "profiled_pass_ms_per_step": ms_profiled / args.steps,
             "clocks": clk.summary()}
     line["issue_roofline"] = issue_roofline(kern_ms, 0.5 * (nb_p + na_p), line["clocks"])
+    line["smem_roofline"] = smem_roofline(kern_ms, 0.5 * (nb_p + na_p), line["clocks"])
     print(json.dumps(line), flush=True)
 
 
