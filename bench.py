@@ -288,7 +288,7 @@ def run_ours(args, rank, world):
     import paper_0909_5603_gb300 as pic
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
+    torch.cuda.set_device(local % max(torch.cuda.device_count(), 1))
     pic.build()
     w = workload(args.nz)
     ncell = w["n"][0] * w["n"][1] * w["n"][2]
@@ -307,7 +307,7 @@ def run_ours(args, rank, world):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk:
         e0.record(stream)
         sim.step(args.steps)
         e1.record(stream)
@@ -417,7 +417,7 @@ def run_slabs(args, rank, world):
     from paper_0909_5603_gb300 import slab as S
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
+    torch.cuda.set_device(local % max(torch.cuda.device_count(), 1))
     pic.build()
     w = workload(args.nz)
     n = w["n"]
@@ -441,7 +441,7 @@ def run_slabs(args, rank, world):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk:
         e0.record(sim.stream)
         run.step(args.steps)
         e1.record(sim.stream)
