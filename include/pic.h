@@ -318,6 +318,15 @@ pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx **batch);
  * on = 0 returns to the per-phase CUDA graph.  Not valid on a member (PIC_ERR_ARG). */
 pic_status pic_batch_set_persistent(pic_ctx *batch, int on, long long spin_limit, int test_stall);
 
+/* Online choice of the batch's launch form (the paper has no counterpart): runs one
+ * untimed and `steps` >= 1 timed steps with the per-phase CUDA graph, then the same with
+ * the persistent step when the batch admits it (pic_batch_set_persistent), and leaves
+ * the faster form on.  The 2 (steps + 1) steps are real steps of the run.  Reports the
+ * choice (*persistent, may be NULL) and the milliseconds per step of each form (-1 for
+ * a form not run; may be NULL).  Not valid on a member (PIC_ERR_ARG) or with profiling
+ * on (PIC_ERR_STATE); a device error of a step is returned as pic_step's would be. */
+pic_status pic_batch_autotune(pic_ctx *batch, int steps, int *persistent, double *ms_graph, double *ms_persistent);
+
 /* Lab-frame stations (Sec. 2: the results are recorded at planes immobile in the
  * laboratory frame and transformed back to it).  Replaces the stations with `count`
  * planes z = z_lab[i] (lab coordinates; lab and boosted frames share their origin at

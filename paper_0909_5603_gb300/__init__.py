@@ -36,7 +36,8 @@ EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error"
             "pic_get_timings", "pic_synchronize", "pic_batch_create", "pic_get_rho_noalloc", "pic_autotune",
             "pic_set_stations", "pic_get_station", "pic_set_injection", "pic_set_laser_antenna",
             "pic_get_fields", "pic_get_gauss_residual", "pic_get_planes", "pic_put_planes",
-            "pic_extract_particles", "pic_add_particles", "pic_adopt_slab", "pic_batch_set_persistent"]
+            "pic_extract_particles", "pic_add_particles", "pic_adopt_slab", "pic_batch_set_persistent",
+            "pic_batch_autotune"]
 PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
@@ -167,6 +168,8 @@ def lib():
                                             P(ctypes.c_int64)]
         L.pic_add_particles.restype = st
         L.pic_add_particles.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.pic_batch_autotune.restype = st
+        L.pic_batch_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_double)]
         L.pic_batch_set_persistent.restype = st
         L.pic_batch_set_persistent.argtypes = [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int]
         L.pic_adopt_slab.restype = st
@@ -491,6 +494,14 @@ class Batch:
 
     def step(self, n=1):
         _check(lib().pic_step(self.h, n), self.h)
+
+    def autotune(self, steps=3):
+        """pic_batch_autotune: times both launch forms on real steps and keeps the faster.
+        Returns (persistent chosen, ms per step graph, ms per step persistent)."""
+        pers, mg, mp = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().pic_batch_autotune(self.h, int(steps), ctypes.byref(pers), ctypes.byref(mg), ctypes.byref(mp)),
+               self.h)
+        return bool(pers.value), mg.value, mp.value
 
     def set_persistent(self, on=True, spin_limit=0, test_stall=-1):
         """pic_batch_set_persistent: each step() call as one persistent launch."""

@@ -1989,6 +1989,52 @@ extern "C" pic_status pic_batch_set_persistent(pic_ctx *batch, int on, long long
     return PIC_OK;
 }
 
+// Times `steps` steps of each launch form on the batch itself (real steps of the run,
+// CUDA events on its stream) and keeps the faster one on.
+extern "C" pic_status pic_batch_autotune(pic_ctx *batch, int steps, int *persistent, double *ms_graph,
+                                         double *ms_persistent)
+{
+    if (!batch) return PIC_ERR_ARG;
+    if (!batch->is_batch) return fail(batch, PIC_ERR_ARG, "pic_batch_autotune takes a batch");
+    if (steps < 1) return fail(batch, PIC_ERR_ARG, "steps must be >= 1");
+    if (batch->profiling) return fail(batch, PIC_ERR_STATE, "pic_batch_autotune with profiling on");
+    cudaSetDevice(batch->device);
+    const bool was = batch->persistent;
+    const long long spin = batch->spin_limit;
+    // the persistent form, when the batch admits it
+    pic_status st = pic_batch_set_persistent(batch, 1, spin, -1);
+    const bool can_persist = st == PIC_OK;
+    if (!can_persist) batch->err.clear();
+    double ms[2] = {-1.0, -1.0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_OR_FAIL(batch, cudaEventCreate(&e0));
+    CUDA_OR_FAIL(batch, cudaEventCreate(&e1));
+    for (int form = 0; form < 2 && st != PIC_ERR_CUDA; ++form) {
+        if (form == 1 && !can_persist) break;
+        batch->persistent = form == 1;
+        // one untimed step builds the graph or warms the persistent kernel
+        if ((st = pic_step(batch, 1)) != PIC_OK || (st = pic_synchronize(batch)) != PIC_OK) break;
+        cudaEventRecord(e0, batch->stream);
+        if ((st = pic_step(batch, steps)) != PIC_OK) break;
+        cudaEventRecord(e1, batch->stream);
+        if ((st = pic_synchronize(batch)) != PIC_OK) break;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[form] = t / steps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PIC_OK) {
+        batch->persistent = was;
+        return st;
+    }
+    batch->persistent = can_persist && ms[1] < ms[0];
+    if (persistent) *persistent = batch->persistent ? 1 : 0;
+    if (ms_graph) *ms_graph = ms[0];
+    if (ms_persistent) *ms_persistent = ms[1];
+    return PIC_OK;
+}
+
 extern "C" pic_status pic_batch_create(int n, pic_ctx *const *instances, pic_ctx **batch)
 {
     if (!batch) return fail(nullptr, PIC_ERR_ARG, "batch is NULL");

@@ -11,7 +11,8 @@ instance's previous phase, with bounded waits.
 * The timeout: an instance whose J set-up waits for an item that never runs (test_stall)
   ends the launch with PIC_ERR_TIMEOUT after the configured number of polls, and the
   device stays usable.
-* What the persistent step refuses (FP64 members, the low-dispersion solver).
+* What the persistent step refuses (FP64 members, the low-dispersion solver), and the
+  online choice between the two launch forms (pic_batch_autotune).
 """
 import numpy as np
 import pytest
@@ -138,3 +139,18 @@ def test_persistent_refuses_what_it_does_not_run():
     with pytest.raises(pic.PicError) as e:
         b2.set_persistent(True)
     assert e.value.status == pic.PIC_ERR_UNSUPPORTED
+
+
+def test_batch_autotune_times_both_forms_and_keeps_the_faster():
+    b = pic.Batch(scan_members(8))
+    chosen, ms_graph, ms_persistent = b.autotune(2)
+    print(f"batch autotune: graph {ms_graph:.3f} ms/step, persistent {ms_persistent:.3f} ms/step, "
+          f"persistent chosen: {chosen}")
+    assert ms_graph > 0 and ms_persistent > 0
+    assert chosen == (ms_persistent < ms_graph)
+    b.step(2)
+    b.synchronize()
+    # a batch the persistent step does not run: only the graph is timed
+    b64 = pic.Batch(scan_members(2, prec=FP64))
+    chosen, ms_graph, ms_persistent = b64.autotune(1)
+    assert not chosen and ms_graph > 0 and ms_persistent == -1.0
