@@ -434,8 +434,11 @@ pic_status pic_put_planes(pic_ctx *ctx, int comp, int k0, int nk, const double *
  * set and nothing removed).  pic_add_particles appends n particles (layout as
  * pic_load_particles; id may be NULL when ids are not tracked).  Unlike a load, both keep
  * the step count, the ion background, the antenna, the injection plane and the stations:
- * the particle set changes, the state of the run does not.  Both read the particles back
- * and lay the set out again on the host (O(particles) host work and copies per call). */
+ * the particle set changes, the state of the run does not.  Both read the particles out
+ * on the device, copy their cells to the host for the canonical order (a stable counting
+ * sort by tile) and place the set again on the device; only the particles taken out or
+ * added cross to the host in full.  Device memory: a read-out staging copy of the
+ * particles (kept for later read-outs) and a map of one int per particle. */
 pic_status pic_extract_particles(pic_ctx *ctx, int k_lo, int k_hi, int32_t *cell, double *off3, double *u3, double *w,
                                  int32_t *id, int64_t cap, int64_t *n_out);
 pic_status pic_add_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3, const double *u3,

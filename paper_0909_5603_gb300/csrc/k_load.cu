@@ -143,6 +143,28 @@ __global__ void __launch_bounds__(256) k_place(InstDev I, PlaceSrc s)
     store_particle<R>(I, s.slot[i], s.cell[i], off, u, s.w[i], s.id ? s.id[i] : (int)(s.id_base + i));
 }
 
+// Read-out staging (storage precision, canonical order) placed again: particle i goes to
+// slot map[i] of buffer 0, or, for map[i] < 0, to position -1 - map[i] of buffer 1 (the
+// particles taken out, packed).  No conversion: the values keep their bits.
+template <typename R>
+__global__ void __launch_bounds__(256) k_place_staged(InstDev I, StagedSrc s)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+    const int m = s.map[i];
+    const int b = m >= 0 ? 0 : 1;
+    const int d = m >= 0 ? m : -1 - m;
+    I.cell[b][d] = s.cell[i];
+    if (I.id[b]) I.id[b][d] = s.id[i];
+    const R *off = (const R *)s.off, *u = (const R *)s.u;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (I.off[b][a]) ((R *)I.off[b][a])[d] = off[3 * i + a];
+        ((R *)I.u[b][a])[d] = u[3 * i + a];
+    }
+    ((R *)I.w[b])[d] = ((const R *)s.w)[i];
+}
+
 // per cell: particles placed (low 16 bits) and ids used (high bits); count[ncell] is set
 // when a candidate lands in a cell other than the one that drew it (an offset rounding
 // to the next cell), which the layout by drawing cell does not cover
@@ -185,6 +207,15 @@ cudaError_t launch_place(int fp64, const InstDev &I, const PlaceSrc &s, cudaStre
     const unsigned blocks = (unsigned)((s.n + 255) / 256);
     if (fp64) k_place<double><<<blocks, 256, 0, st>>>(I, s);
     else k_place<float><<<blocks, 256, 0, st>>>(I, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_place_staged(int fp64, const InstDev &I, const StagedSrc &s, cudaStream_t st)
+{
+    if (s.n <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((s.n + 255) / 256);
+    if (fp64) k_place_staged<double><<<blocks, 256, 0, st>>>(I, s);
+    else k_place_staged<float><<<blocks, 256, 0, st>>>(I, s);
     return cudaGetLastError();
 }
 

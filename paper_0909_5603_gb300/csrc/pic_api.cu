@@ -1495,6 +1495,31 @@ extern "C" pic_status pic_num_particles(pic_ctx *ctx, int64_t *n_out)
     return PIC_OK;
 }
 
+// Device staging for the canonical read-out of every particle the buffers can hold.
+static pic_status ensure_staging(pic_ctx *ctx)
+{
+    InstDev &h = ctx->h;
+    if (ctx->stage_cap >= h.cap) return PIC_OK;
+    dfree(ctx, ctx->st_cell);
+    ctx->st_cell = nullptr;
+    const size_t per = (size_t)h.cap;
+    unsigned char *blk = (unsigned char *)dalloc(ctx, per * (2 * sizeof(int) + 7 * sizeof(double)) + 2048);
+    if (!blk) return fail(ctx, PIC_ERR_OOM, "read-out staging does not fit");
+    size_t o = 0;
+    auto take = [&](size_t b) {
+        void *p = blk + o;
+        o += (b + 255) & ~(size_t)255;
+        return p;
+    };
+    ctx->st_cell = (int *)take(per * sizeof(int));
+    ctx->st_id = (int *)take(per * sizeof(int));
+    ctx->st_off = (double *)take(per * 3 * sizeof(double));
+    ctx->st_u = (double *)take(per * 3 * sizeof(double));
+    ctx->st_w = (double *)take(per * sizeof(double));
+    ctx->stage_cap = h.cap;
+    return PIC_OK;
+}
+
 extern "C" pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off3, double *u3, double *w, int32_t *id,
                                         int64_t cap, int64_t *n_out)
 {
@@ -1509,26 +1534,7 @@ extern "C" pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off
     *n_out = live;
     if (live > cap) return fail(ctx, PIC_ERR_ARG, "cap %lld < %d live particles", (long long)cap, live);
     if (live == 0) return PIC_OK;
-    InstDev &h = ctx->h;
-    if (ctx->stage_cap < h.cap) {
-        dfree(ctx, ctx->st_cell);
-        ctx->st_cell = nullptr;
-        const size_t per = (size_t)h.cap;
-        unsigned char *blk = (unsigned char *)dalloc(ctx, per * (2 * sizeof(int) + 7 * sizeof(double)) + 2048);
-        if (!blk) return fail(ctx, PIC_ERR_OOM, "read-out staging does not fit");
-        size_t o = 0;
-        auto take = [&](size_t b) {
-            void *p = blk + o;
-            o += (b + 255) & ~(size_t)255;
-            return p;
-        };
-        ctx->st_cell = (int *)take(per * sizeof(int));
-        ctx->st_id = (int *)take(per * sizeof(int));
-        ctx->st_off = (double *)take(per * 3 * sizeof(double));
-        ctx->st_u = (double *)take(per * 3 * sizeof(double));
-        ctx->st_w = (double *)take(per * sizeof(double));
-        ctx->stage_cap = h.cap;
-    }
+    if ((st = ensure_staging(ctx)) != PIC_OK) return st;
     CUDA_OR_FAIL(ctx, launch_readout(ctx->fp64, ctx->L, ctx->d_start_ptr, ctx->st_cell, ctx->st_off, ctx->st_u, ctx->st_w,
                                      ctx->st_id, ctx->stream));
     // values copied in the storage precision (FP32: half the bytes) into the caller's
@@ -1586,28 +1592,77 @@ extern "C" pic_status pic_put_planes(pic_ctx *ctx, int comp, int k0, int nk, con
     return check_device_error(ctx);
 }
 
-// All live particles on the host in canonical order (ids only when tracked).
-struct HostParticles {
-    std::vector<int32_t> cell, id;
-    std::vector<double> off, u, w;
-    int64_t n = 0;
-};
-
-static pic_status read_particles(pic_ctx *c, HostParticles &P)
+// The live particles read out on the device into the staging arrays (storage precision,
+// canonical order); their cells copied to the host.
+static pic_status stage_particles(pic_ctx *c, std::vector<int32_t> &cells, int &live)
 {
-    int64_t n = 0;
-    pic_status st = pic_num_particles(c, &n);
+    pic_status st = pic_synchronize(c);
     if (st != PIC_OK) return st;
-    P.cell.resize((size_t)std::max<int64_t>(n, 1));
-    P.off.resize(3 * P.cell.size());
-    P.u.resize(3 * P.cell.size());
-    P.w.resize(P.cell.size());
-    if (c->opt.track_ids) P.id.resize(P.cell.size());
-    st = pic_get_particles(c, P.cell.data(), P.off.data(), P.u.data(), P.w.data(),
-                           c->opt.track_ids ? P.id.data() : nullptr, (int64_t)P.cell.size(), &P.n);
-    return st;
+    live = 0;
+    if ((st = count_live(c, 1, &live)) != PIC_OK) return st;
+    cells.resize((size_t)std::max(live, 1));
+    if (live == 0) return PIC_OK;
+    if ((st = ensure_staging(c)) != PIC_OK) return st;
+    CUDA_OR_FAIL(c, launch_readout(c->fp64, c->L, c->d_start_ptr, c->st_cell, c->st_off, c->st_u, c->st_w, c->st_id,
+                                   c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(cells.data(), c->st_cell, sizeof(int) * (size_t)live, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
 }
 
+// Stable counting sort by tile of n particles whose cells cell_at(q) gives: the slot of
+// each in the canonical order and the tile segments (host threads over contiguous ranges,
+// each range taking its slots in order, as the load does).
+template <typename F>
+static void canonical_slots(const pic_ctx *c, int64_t n, F cell_at, std::vector<int> &slot, std::vector<int> &seg)
+{
+    const int ntiles = c->h.ntiles;
+    const int T = host_workers(n);
+    std::vector<std::vector<int>> hist(T);
+    slot.assign((size_t)std::max<int64_t>(n, 1), 0);
+    seg.assign(ntiles + 1, 0);
+    parallel_ranges(n, T, [&](int t, int64_t b, int64_t e) {
+        std::vector<int> &hc = hist[t];
+        hc.assign(ntiles, 0);
+        for (int64_t q = b; q < e; ++q) {
+            slot[q] = tile_of_cell(c, cell_at(q));
+            hc[slot[q]]++;
+        }
+    });
+    for (int t = 0; t < T; ++t)
+        for (int k = 0; k < ntiles; ++k) seg[k + 1] += hist[t][k];
+    for (int k = 0; k < ntiles; ++k) seg[k + 1] += seg[k];
+    std::vector<int> fill(seg.begin(), seg.end() - 1);
+    for (int t = 0; t < T; ++t)
+        for (int k = 0; k < ntiles; ++k) {
+            const int m = hist[t][k];
+            hist[t][k] = fill[k];
+            fill[k] += m;
+        }
+    parallel_ranges(n, T, [&](int t, int64_t b, int64_t e) {
+        std::vector<int> &f = hist[t];
+        for (int64_t q = b; q < e; ++q) slot[q] = f[slot[q]]++;
+    });
+}
+
+// The first n values of an SoA device array in the storage precision, widened to FP64
+// into host_strided[i * stride + lane].
+static pic_status copy_out_widened(pic_ctx *c, const void *dev, size_t n, double *host_strided, int stride, int lane)
+{
+    std::vector<double> tmp(n);
+    if (c->fp64) {
+        CUDA_OR_FAIL(c, d2h(c, tmp.data(), dev, sizeof(double) * n));
+    } else {
+        std::vector<float> f(n);
+        CUDA_OR_FAIL(c, d2h(c, f.data(), dev, sizeof(float) * n));
+        for (size_t i = 0; i < n; ++i) tmp[i] = f[i];
+    }
+    for (size_t i = 0; i < n; ++i) host_strided[i * stride + lane] = tmp[i];
+    return PIC_OK;
+}
+
+// The particles are read out and laid out again on the device; only their cells (and the
+// particles taken out) cross to the host.
 extern "C" pic_status pic_extract_particles(pic_ctx *ctx, int k_lo, int k_hi, int32_t *cell, double *off3, double *u3,
                                             double *w, int32_t *id, int64_t cap, int64_t *n_out)
 {
@@ -1616,47 +1671,56 @@ extern "C" pic_status pic_extract_particles(pic_ctx *ctx, int k_lo, int k_hi, in
     if (!ctx->loaded) return fail(ctx, PIC_ERR_STATE, "pic_extract_particles before any load");
     if (k_lo > k_hi) return fail(ctx, PIC_ERR_ARG, "k_lo %d > k_hi %d", k_lo, k_hi);
     cudaSetDevice(ctx->device);
-    HostParticles P;
-    pic_status st = read_particles(ctx, P);
+    *n_out = 0;
+    std::vector<int32_t> cells;
+    int live = 0;
+    pic_status st = stage_particles(ctx, cells, live);
     if (st != PIC_OK) return st;
     const long long plane = (long long)ctx->n[0] * ctx->n[1];
-    std::vector<int64_t> go, keep;
-    for (int64_t p = 0; p < P.n; ++p) {
-        const int k = (int)(P.cell[p] / plane);
-        (k < k_lo || k >= k_hi ? go : keep).push_back(p);
+    std::vector<int> map((size_t)std::max(live, 1));
+    std::vector<int64_t> keep;
+    keep.reserve((size_t)live);
+    int ngo = 0;
+    for (int i = 0; i < live; ++i) {
+        const int k = (int)(cells[i] / plane);
+        if (k < k_lo || k >= k_hi) map[i] = -1 - ngo++;
+        else keep.push_back(i);
     }
-    *n_out = (int64_t)go.size();
-    if ((int64_t)go.size() > cap) return fail(ctx, PIC_ERR_ARG, "cap %lld < %zu particles to extract", (long long)cap, go.size());
-    if (go.empty()) return PIC_OK;
-    for (size_t q = 0; q < go.size(); ++q) {
-        const int64_t p = go[q];
-        if (cell) cell[q] = P.cell[p];
-        if (id) id[q] = P.id.empty() ? 0 : P.id[p];
-        for (int a = 0; a < 3; ++a) {
-            if (off3) off3[3 * q + a] = P.off[3 * p + a];
-            if (u3) u3[3 * q + a] = P.u[3 * p + a];
+    *n_out = ngo;
+    if (ngo > cap) return fail(ctx, PIC_ERR_ARG, "cap %lld < %d particles to extract", (long long)cap, ngo);
+    if (ngo == 0) return PIC_OK;
+    std::vector<int> slot, seg;
+    canonical_slots(ctx, (int64_t)keep.size(), [&](int64_t q) { return cells[keep[q]]; }, slot, seg);
+    for (size_t q = 0; q < keep.size(); ++q) map[keep[q]] = slot[q];
+    {
+        LoadScratch S{ctx, {}};
+        int *d_map = (int *)S.get(sizeof(int) * (size_t)live);
+        if (!d_map) return fail(ctx, PIC_ERR_OOM, "no device memory for the particle map");
+        CUDA_OR_FAIL(ctx, cudaMemcpyAsync(d_map, map.data(), sizeof(int) * (size_t)live, cudaMemcpyHostToDevice, ctx->stream));
+        StagedSrc src{ctx->st_cell, ctx->st_off, ctx->st_u, ctx->st_w, ctx->st_id, d_map, (long long)live};
+        CUDA_OR_FAIL(ctx, launch_place_staged(ctx->fp64, ctx->h, src, ctx->stream));
+        CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    // the particles taken out, packed at the start of buffer 1
+    const InstDev &h = ctx->h;
+    const size_t ng = (size_t)ngo;
+    if (cell) CUDA_OR_FAIL(ctx, d2h(ctx, cell, h.cell[1], sizeof(int) * ng));
+    if (id) {
+        if (h.id[1]) CUDA_OR_FAIL(ctx, d2h(ctx, id, h.id[1], sizeof(int) * ng));
+        else std::memset(id, 0, sizeof(int) * ng);
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (off3) {
+            if (h.off[1][a]) {
+                if ((st = copy_out_widened(ctx, h.off[1][a], ng, off3, 3, a)) != PIC_OK) return st;
+            } else {
+                for (size_t i = 0; i < ng; ++i) off3[3 * i + a] = 0.0;
+            }
         }
-        if (w) w[q] = P.w[p];
+        if (u3 && (st = copy_out_widened(ctx, h.u[1][a], ng, u3, 3, a)) != PIC_OK) return st;
     }
-    HostParticles K;
-    K.n = (int64_t)keep.size();
-    K.cell.resize(keep.size());
-    K.off.resize(3 * keep.size());
-    K.u.resize(3 * keep.size());
-    K.w.resize(keep.size());
-    if (!P.id.empty()) K.id.resize(keep.size());
-    for (size_t q = 0; q < keep.size(); ++q) {
-        const int64_t p = keep[q];
-        K.cell[q] = P.cell[p];
-        if (!P.id.empty()) K.id[q] = P.id[p];
-        for (int a = 0; a < 3; ++a) {
-            K.off[3 * q + a] = P.off[3 * p + a];
-            K.u[3 * q + a] = P.u[3 * p + a];
-        }
-        K.w[q] = P.w[p];
-    }
-    return load_internal(ctx, K.n, K.cell.data(), K.off.data(), K.u.data(), K.w.data(), K.id.empty() ? nullptr : K.id.data(),
-                         true);
+    if (w && (st = copy_out_widened(ctx, h.w[1], ng, w, 1, 0)) != PIC_OK) return st;
+    return finish_relayout(ctx, seg);
 }
 
 extern "C" pic_status pic_add_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3, const double *u3,
@@ -1668,23 +1732,42 @@ extern "C" pic_status pic_add_particles(pic_ctx *ctx, int64_t n, const int32_t *
     if (n < 0 || (n > 0 && (!cell || !off3 || !u3 || !w))) return fail(ctx, PIC_ERR_ARG, "particle arrays invalid");
     if (n == 0) return PIC_OK;
     cudaSetDevice(ctx->device);
-    HostParticles P;
-    pic_status st = read_particles(ctx, P);
-    if (st != PIC_OK) return st;
-    P.cell.resize((size_t)P.n);
-    P.off.resize(3 * (size_t)P.n);
-    P.u.resize(3 * (size_t)P.n);
-    P.w.resize((size_t)P.n);
-    P.cell.insert(P.cell.end(), cell, cell + n);
-    P.off.insert(P.off.end(), off3, off3 + 3 * n);
-    P.u.insert(P.u.end(), u3, u3 + 3 * n);
-    P.w.insert(P.w.end(), w, w + n);
-    if (ctx->opt.track_ids) {
-        P.id.resize((size_t)P.n);
-        for (int64_t p = 0; p < n; ++p) P.id.push_back(id ? id[p] : 0);
+    for (int64_t p = 0; p < n; ++p) {
+        if (cell[p] < 0 || cell[p] >= ctx->ncell) return fail(ctx, PIC_ERR_ARG, "particle %lld: cell %d outside the grid", (long long)p, cell[p]);
+        for (int a = 0; a < 3; ++a) {
+            const double o = off3[3 * p + a];
+            if (activeaxis(ctx->ndim, a) && !(o >= 0.0 && o < 1.0))
+                return fail(ctx, PIC_ERR_ARG, "particle %lld: offset %g outside [0,1)", (long long)p, o);
+        }
+        if (!finite3(u3 + 3 * p) || !std::isfinite(w[p])) return fail(ctx, PIC_ERR_NAN, "particle %lld: non-finite momentum or weight", (long long)p);
     }
-    return load_internal(ctx, P.n + n, P.cell.data(), P.off.data(), P.u.data(), P.w.data(),
-                         ctx->opt.track_ids ? P.id.data() : nullptr, true);
+    std::vector<int32_t> cells;
+    int live = 0;
+    pic_status st = stage_particles(ctx, cells, live);
+    if (st != PIC_OK) return st;
+    const int64_t total = (int64_t)live + n;
+    if (total >= (1LL << 31) - 1) return fail(ctx, PIC_ERR_ARG, "particle count %lld out of range", (long long)total);
+    std::vector<int> slot, seg;
+    canonical_slots(ctx, total, [&](int64_t q) { return q < live ? cells[q] : cell[q - live]; }, slot, seg);
+    if ((st = ensure_particle_capacity(ctx, total)) != PIC_OK) return st;
+    if (live > 0) {
+        LoadScratch S{ctx, {}};
+        int *d_map = (int *)S.get(sizeof(int) * (size_t)live);
+        if (!d_map) return fail(ctx, PIC_ERR_OOM, "no device memory for the particle map");
+        CUDA_OR_FAIL(ctx, cudaMemcpyAsync(d_map, slot.data(), sizeof(int) * (size_t)live, cudaMemcpyHostToDevice, ctx->stream));
+        StagedSrc src{ctx->st_cell, ctx->st_off, ctx->st_u, ctx->st_w, ctx->st_id, d_map, (long long)live};
+        CUDA_OR_FAIL(ctx, launch_place_staged(ctx->fp64, ctx->h, src, ctx->stream));
+        CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    std::vector<int> slot_new(slot.begin() + live, slot.begin() + total);
+    std::vector<int32_t> zero_ids;
+    const int32_t *ids = id;
+    if (!ids && ctx->opt.track_ids) {
+        zero_ids.assign((size_t)n, 0);
+        ids = zero_ids.data();
+    }
+    if ((st = place_from_host(ctx, n, cell, off3, u3, w, ids, 0, slot_new)) != PIC_OK) return st;
+    return finish_relayout(ctx, seg);
 }
 
 extern "C" pic_status pic_adopt_slab(pic_ctx *slab, pic_ctx *whole, int k_origin, int k_lo, int k_hi)

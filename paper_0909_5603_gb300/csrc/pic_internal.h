@@ -54,6 +54,16 @@ struct AntDev {
 // host-side launchers
 cudaError_t launch_stations(int fp64, const InstDev *d_inst, const StationDev &S, int nst, int plane, cudaStream_t s);
 cudaError_t launch_place(int fp64, const InstDev &I, const PlaceSrc &s, cudaStream_t st);
+// Read-out staging in the storage precision (off and u 3 values per particle) with a map:
+// map[i] >= 0 the slot in buffer 0, else -1 - map[i] the position in buffer 1
+struct StagedSrc {
+    const int *cell;
+    const void *off, *u, *w;
+    const int *id;
+    const int *map;
+    long long n;
+};
+cudaError_t launch_place_staged(int fp64, const InstDev &I, const StagedSrc &s, cudaStream_t st);
 cudaError_t launch_plasma_count(const PlasmaGen &G, int *count, cudaStream_t st);
 cudaError_t launch_plasma_write(int fp64, const InstDev &I, const PlasmaGen &G, const int *slot0, const int *id0,
                                 cudaStream_t st);

@@ -41,8 +41,9 @@ pic_put_planes, pic_extract_particles and pic_add_particles; a transport moves t
 host arrays between slabs: `InProcess` (every slab in this process, e.g. several
 contexts on one GPU) or `Distributed` (one slab per rank over a torch.distributed
 process group; gloo moves host tensors).  Moving particles reads the slab's particles
-back and lays them out again on the host, O(particles) per call: migrate_every > 1
-spreads that over several steps at the price of deeper ghosts.
+out and lays them out again on the device, with their cells (not the particles) copied
+to the host for the order, O(particles) device work per call: migrate_every > 1 spreads
+that over several steps at the price of deeper ghosts.
 """
 from __future__ import annotations
 
