@@ -437,7 +437,7 @@ def run_slabs(args, rank, world):
     run.step(args.warmup)
     sim.synchronize()
     nb = sim.num_particles()
-    calls0 = shard.plane_calls
+    calls0 = shard.plane_launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
@@ -451,7 +451,7 @@ def run_slabs(args, rank, world):
     psteps = 0.5 * (nb + sim.num_particles()) * args.steps
     ms_max = allreduce_max(ms, world)
     value = allreduce_sum(psteps, world) / (ms_max * 1e-3)
-    plane_launches = shard.plane_calls - calls0
+    plane_launches = shard.plane_launches - calls0
     # the step's own launches, counted by the library over one more (profiled) step
     sim.set_profiling(True, reset=True)
     run.step(1)

@@ -427,6 +427,12 @@ pic_status pic_autotune(const pic_grid *grid, const double dx[3], double dt, dou
  * memory: none beyond the context's. */
 pic_status pic_get_planes(pic_ctx *ctx, int comp, int k0, int nk, double *host_out, size_t count);
 pic_status pic_put_planes(pic_ctx *ctx, int comp, int k0, int nk, const double *host_in, size_t count, int add);
+/* The same for ncomp >= 1 components comps[i] at once, host arrays [ncomp][nk][n1][n0]
+ * (count >= ncomp nk n0 n1): one copy and one synchronisation per call (per group of
+ * components that fit the context's dense scratch of n0 n1 n2 values). */
+pic_status pic_get_planes_n(pic_ctx *ctx, const int *comps, int ncomp, int k0, int nk, double *host_out, size_t count);
+pic_status pic_put_planes_n(pic_ctx *ctx, const int *comps, int ncomp, int k0, int nk, const double *host_in,
+                            size_t count, int add);
 
 /* pic_extract_particles removes the live particles whose z cell index lies outside
  * [k_lo, k_hi) and copies them, in canonical order, into the caller's arrays (layout as

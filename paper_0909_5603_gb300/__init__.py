@@ -37,7 +37,7 @@ EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error"
             "pic_set_stations", "pic_get_station", "pic_set_injection", "pic_set_laser_antenna",
             "pic_get_fields", "pic_get_gauss_residual", "pic_get_planes", "pic_put_planes",
             "pic_extract_particles", "pic_add_particles", "pic_adopt_slab", "pic_batch_set_persistent",
-            "pic_batch_autotune"]
+            "pic_batch_autotune", "pic_get_planes_n", "pic_put_planes_n"]
 PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
@@ -172,6 +172,10 @@ def lib():
         L.pic_batch_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_double)]
         L.pic_batch_set_persistent.restype = st
         L.pic_batch_set_persistent.argtypes = [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int]
+        L.pic_get_planes_n.restype = st
+        L.pic_get_planes_n.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t]
+        L.pic_put_planes_n.restype = st
+        L.pic_put_planes_n.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int]
         L.pic_adopt_slab.restype = st
         L.pic_adopt_slab.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.pic_autotune.restype = st
@@ -441,6 +445,19 @@ class Simulation:
     def put_planes(self, comp, k0, values, add=False):
         v = np.ascontiguousarray(np.asarray(values, np.float64).reshape(-1, self.n[1], self.n[0]))
         _check(lib().pic_put_planes(self.h, comp, int(k0), v.shape[0], _ptr(v), v.size, 1 if add else 0), self.h)
+
+    def get_planes_n(self, comps, k0, nk):
+        """Planes k0 .. k0 + nk - 1 of several components, (len(comps), nk, n1, n0)."""
+        cs = np.ascontiguousarray(comps, dtype=np.int32)
+        out = np.empty((cs.size, nk, self.n[1], self.n[0]))
+        _check(lib().pic_get_planes_n(self.h, _ptr(cs), cs.size, int(k0), int(nk), _ptr(out), out.size), self.h)
+        return out
+
+    def put_planes_n(self, comps, k0, values, add=False):
+        cs = np.ascontiguousarray(comps, dtype=np.int32)
+        v = np.ascontiguousarray(np.asarray(values, np.float64).reshape(cs.size, -1, self.n[1], self.n[0]))
+        _check(lib().pic_put_planes_n(self.h, _ptr(cs), cs.size, int(k0), v.shape[1], _ptr(v), v.size, 1 if add else 0),
+               self.h)
 
     def extract_particles(self, k_lo, k_hi):
         """Removes and returns the particles whose z cell index is outside [k_lo, k_hi)."""

@@ -1592,6 +1592,63 @@ extern "C" pic_status pic_put_planes(pic_ctx *ctx, int comp, int k0, int nk, con
     return check_device_error(ctx);
 }
 
+// Several components' planes in one call: packed one component after the other into the
+// dense scratch (as many components at a time as it holds), one copy and one
+// synchronisation per batch.
+extern "C" pic_status pic_get_planes_n(pic_ctx *ctx, const int *comps, int ncomp, int k0, int nk, double *host_out,
+                                       size_t count)
+{
+    if (!ctx || !comps || !host_out || ncomp < 1) return PIC_ERR_ARG;
+    const size_t per = (size_t)nk * ctx->n[0] * ctx->n[1];
+    for (int i = 0; i < ncomp; ++i) {
+        pic_status st = check_planes(ctx, comps[i], k0, nk, per);
+        if (st != PIC_OK) return st;
+    }
+    if (count < per * ncomp) return fail(ctx, PIC_ERR_ARG, "need room for %zu values", per * ncomp);
+    pic_status st = pic_synchronize(ctx);
+    if (st != PIC_OK) return st;
+    const int fit = (int)std::max<size_t>(1, (size_t)ctx->ncell / std::max<size_t>(per, 1));
+    for (int i0 = 0; i0 < ncomp; i0 += fit) {
+        const int m = std::min(fit, ncomp - i0);
+        for (int i = 0; i < m; ++i)
+            CUDA_OR_FAIL(ctx, launch_pack_planes(ctx->fp64, ctx->h, comps[i0 + i], ctx->last_filtered, ctx->d_dense + per * i,
+                                                 k0, nk, ctx->stream));
+        CUDA_OR_FAIL(ctx, cudaMemcpyAsync(host_out + per * i0, ctx->d_dense, sizeof(double) * per * m, cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+        CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return check_device_error(ctx);
+}
+
+extern "C" pic_status pic_put_planes_n(pic_ctx *ctx, const int *comps, int ncomp, int k0, int nk, const double *host_in,
+                                       size_t count, int add)
+{
+    if (!ctx || !comps || !host_in || ncomp < 1) return PIC_ERR_ARG;
+    const size_t per = (size_t)nk * ctx->n[0] * ctx->n[1];
+    bool eb = false;
+    for (int i = 0; i < ncomp; ++i) {
+        pic_status st = check_planes(ctx, comps[i], k0, nk, per);
+        if (st != PIC_OK) return st;
+        eb = eb || comps[i] < PIC_JX;
+    }
+    if (count < per * ncomp) return fail(ctx, PIC_ERR_ARG, "need room for %zu values", per * ncomp);
+    pic_status st = pic_synchronize(ctx);
+    if (st != PIC_OK) return st;
+    const int fit = (int)std::max<size_t>(1, (size_t)ctx->ncell / std::max<size_t>(per, 1));
+    for (int i0 = 0; i0 < ncomp; i0 += fit) {
+        const int m = std::min(fit, ncomp - i0);
+        CUDA_OR_FAIL(ctx, cudaMemcpyAsync(ctx->d_dense, host_in + per * i0, sizeof(double) * per * m, cudaMemcpyHostToDevice,
+                                          ctx->stream));
+        for (int i = 0; i < m; ++i)
+            CUDA_OR_FAIL(ctx, launch_unpack_planes(ctx->fp64, ctx->h, comps[i0 + i], ctx->d_dense + per * i, k0, nk,
+                                                   add ? 1 : 0, ctx->stream));
+        CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));  // before the scratch is reused
+    }
+    if (eb && (st = ghost_fill_now(ctx)) != PIC_OK) return st;
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
+}
+
 // The live particles read out on the device into the staging arrays (storage precision,
 // canonical order); their cells copied to the host.
 static pic_status stage_particles(pic_ctx *c, std::vector<int32_t> &cells, int &live)

@@ -36,8 +36,9 @@ when a slab's set is laid out again; in FP32 the block scale of the deposit depe
 which particles share a chunk, so FP32 results agree with the unsplit run to FP32
 rounding, FP64 ones to FP64 rounding.
 
-The exchange is staged through host memory with the C-ABI calls pic_get_planes,
-pic_put_planes, pic_extract_particles and pic_add_particles; a transport moves the
+The exchange is staged through host memory with the C-ABI calls pic_get_planes_n,
+pic_put_planes_n (all components of an exchange in one call), pic_extract_particles and
+pic_add_particles; a transport moves the
 host arrays between slabs: `InProcess` (every slab in this process, e.g. several
 contexts on one GPU) or `Distributed` (one slab per rank over a torch.distributed
 process group; gloo moves host tensors).  Moving particles reads the slab's particles
@@ -199,7 +200,7 @@ class GpuShard:
 
     def __init__(self, sim: Simulation):
         self.sim = sim
-        self.plane_calls = 0  # pic_get_planes / pic_put_planes calls (one pack or unpack launch each)
+        self.plane_launches = 0  # pack / unpack launches of the plane calls (one per component)
 
     def particle_phase(self):
         self.sim.run_phases(PIC_PHASE_PARTICLES)
@@ -207,13 +208,14 @@ class GpuShard:
     def field_phases(self):
         self.sim.run_phases(PIC_PHASE_FILTER | PIC_PHASE_MAXWELL)
 
-    def get_planes(self, comp, k0, nk):
-        self.plane_calls += 1
-        return self.sim.get_planes(comp, k0, nk)
+    def get_planes(self, comps, k0, nk):
+        """Planes of several components, (len(comps), nk, n1, n0), in one call."""
+        self.plane_launches += len(comps)
+        return self.sim.get_planes_n(comps, k0, nk)
 
-    def put_planes(self, comp, k0, values, add):
-        self.plane_calls += 1
-        self.sim.put_planes(comp, k0, values, add=add)
+    def put_planes(self, comps, k0, values, add):
+        self.plane_launches += len(comps)
+        self.sim.put_planes_n(comps, k0, values, add=add)
 
     def extract(self, k_lo, k_hi):
         return self.sim.extract_particles(k_lo, k_hi)
@@ -258,12 +260,11 @@ class SlabRun:
     def _exchange_j(self):
         def make_partial(s, side):
             a, b = s.ghost_range(side)
-            return np.stack([self.shards[s.rank].get_planes(c, a, b - a) for c in J_COMPS])
+            return self.shards[s.rank].get_planes(J_COMPS, a, b - a)
 
         def add_partial(s, face, arr):
             a, _ = s.edge_range(face)
-            for i, c in enumerate(J_COMPS):
-                self.shards[s.rank].put_planes(c, a, arr[i], True)
+            self.shards[s.rank].put_planes(J_COMPS, a, arr, True)
 
         self._swap(make_partial, add_partial)
         self._refresh(J_COMPS)
@@ -271,12 +272,11 @@ class SlabRun:
     def _refresh(self, comps):
         def make_edge(s, side):
             a, b = s.edge_range(side)
-            return np.stack([self.shards[s.rank].get_planes(c, a, b - a) for c in comps])
+            return self.shards[s.rank].get_planes(comps, a, b - a)
 
         def put_ghost(s, face, arr):
             a, _ = s.ghost_range(face)
-            for i, c in enumerate(comps):
-                self.shards[s.rank].put_planes(c, a, arr[i], False)
+            self.shards[s.rank].put_planes(comps, a, arr, False)
 
         self._swap(make_edge, put_ghost)
 
@@ -325,7 +325,7 @@ class SlabRun:
     # -- read-out of the whole grid's owned planes (for checks)
     def owned_field(self, rank, comp):
         s = self.slabs[rank]
-        return self.shards[rank].get_planes(comp, s.own_lo, s.k1 - s.k0)
+        return self.shards[rank].get_planes((comp,), s.own_lo, s.k1 - s.k0)[0]
 
 
 # ---- the GPU split of a whole-grid context ----------------------------------------------

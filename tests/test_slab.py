@@ -68,13 +68,14 @@ class OracleShard:
         self.sim.filter()
         self.sim.maxwell()
 
-    def get_planes(self, comp, k0, nk):
-        return self.sim.get_field(comp)[k0:k0 + nk].copy()
+    def get_planes(self, comps, k0, nk):
+        return np.stack([self.sim.get_field(c)[k0:k0 + nk].copy() for c in comps])
 
-    def put_planes(self, comp, k0, values, add):
-        f = self.sim.get_field(comp)
-        f[k0:k0 + values.shape[0]] = f[k0:k0 + values.shape[0]] + values if add else values
-        self.sim.set_field(comp, f)
+    def put_planes(self, comps, k0, values, add):
+        for c, v in zip(comps, values):
+            f = self.sim.get_field(c)
+            f[k0:k0 + v.shape[0]] = f[k0:k0 + v.shape[0]] + v if add else v
+            self.sim.set_field(c, f)
 
     def extract(self, k_lo, k_hi):
         p = self.sim.get_particles()
