@@ -1213,7 +1213,9 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
         tm.end(0);
         launches += 3;
     }
-    int filtered = 0;
+    // whether J holds the filtered current when the Yee update reads it: filtered in this
+    // call, or by an earlier filter-only call since the last particle phase
+    int filtered = (mask & PIC_PHASE_PARTICLES) ? 0 : c->last_filtered;
     if ((mask & PIC_PHASE_FILTER) && c->max_sweeps > 0) {
         const int nin = c->is_batch ? (int)c->members.size() : 1;
         const long long *starts[3] = {c->d_pencil, c->d_pencil + (nin + 1), c->d_pencil + 2 * (nin + 1)};
