@@ -400,3 +400,21 @@ def test_errors_surface_as_status():
     with pytest.raises(pic.PicError) as e:
         g.load_particles(np.array([0], np.int32), np.array([[0.5, 0.0, 0.0]]), np.array([[np.nan, 0, 0]]), np.ones(1))
     assert e.value.status == pic.PIC_ERR_NAN
+
+
+@pytest.mark.parametrize("ndim", [3, 2])
+def test_phases_one_call_each_equal_the_oracle_step(ndim):
+    """The three phases run as three pic_run_phases calls (particles, filter, Yee) make
+    the oracle's step: the Yee call reads the current the filter call left (FP64, 1e-12)."""
+    c = dict(CASES_3D if ndim == 3 else CASES_2D)
+    bc = (0, 0, 0)
+    g, o = pair(ndim, c["n"], bc, c["dx"], c["dt"], 2, FP64, passes=2)
+    parts = synth.random_particles(c["n"], ndim, 6000, 0.2, seed=91)
+    load_both(g, o, parts)
+    set_fields_both(g, o, synth.smooth_fields(c["n"], ndim, 0.2, seed=92))
+    for _ in range(3):
+        g.run_phases(pic.PIC_PHASE_PARTICLES)
+        g.run_phases(pic.PIC_PHASE_FILTER)
+        g.run_phases(pic.PIC_PHASE_MAXWELL)
+        o.step(1)
+    compare_fields(g, o, COMPS + [pic.PIC_JX, pic.PIC_JY, pic.PIC_JZ], 1e-12)
