@@ -267,57 +267,56 @@ __global__ void __launch_bounds__(256) k_ghost(Launch L, int axis, long long per
     if (r < ghost_elems(I, axis)) ghost_elem<R>(I, axis, r);
 }
 
-// FP64 field energy sums (1/2) sum (E^2 + B^2) dV per instance.
+// FP64 field energy sums (1/2) sum (E^2 + B^2) dV per instance.  Each block takes a
+// contiguous range of kEnergyCells cells of the flattened cell space and, for every
+// instance the range meets, sums its part (each cell's E^2 + B^2 in the storage
+// precision, then FP64) and adds it with one atomic: a few thousand atomics per call
+// instead of one per 256 cells, all on the same address.
+constexpr long long kEnergyCells = 8192;
+
+// sum of v over the block (every thread gets it)
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();  // red is free
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_field_energy(Launch L, double *sums)
 {
-    __shared__ double s_e[8];
-    __shared__ int s_ii[8];
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    CellPos c;
-    const InstDev *Ip;
-    double e = 0.0;
-    int ii = -1;
-    if (cell_of(L, g, c, Ip)) {
-        const InstDev &I = *Ip;
-        ii = c.ii;
-        R s2 = R(0);  // the cell's E^2 + B^2 in the storage precision, then FP64
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const R x = ((const R *)eb_field(I, a))[c.p], y = ((const R *)eb_field(I, 3 + a))[c.p];
-            s2 += x * x + y * y;
+    __shared__ double red[8];
+    const long long b0 = (long long)blockIdx.x * kEnergyCells;
+    const long long b1 = min(b0 + kEnergyCells, L.total_cells);
+    if (b0 >= b1) return;
+    int ii = find_instance_ll(L.cell_start, L.ninst, b0);
+    for (long long lo = b0; lo < b1; ++ii) {
+        const long long hi = min(b1, L.cell_start[ii + 1]);
+        const InstDev &I = L.inst[ii];
+        const R *Ex = (const R *)eb_field(I, 0), *Ey = (const R *)eb_field(I, 1), *Ez = (const R *)eb_field(I, 2);
+        const R *Bx = (const R *)eb_field(I, 3), *By = (const R *)eb_field(I, 4), *Bz = (const R *)eb_field(I, 5);
+        double e = 0.0;
+        for (long long g = lo + threadIdx.x; g < hi; g += blockDim.x) {
+            const int r = (int)(g - L.cell_start[ii]);
+            const int rq = fast_div(r, I.div_n0);
+            const int i = r - rq * I.n[0];
+            const int k = fast_div(rq, I.div_n1);
+            const int j = rq - k * I.n[1];
+            const long long p = (i + I.gh[0]) + I.sy * (j + I.gh[1]) + I.sz * (k + I.gh[2]);
+            // the cell's E^2 + B^2 in the storage precision, then FP64
+            R s2 = Ex[p] * Ex[p] + Bx[p] * Bx[p];
+            s2 += Ey[p] * Ey[p] + By[p] * By[p];
+            s2 += Ez[p] * Ez[p] + Bz[p] * Bz[p];
+            e += (double)s2;
         }
-        e = (double)s2 * (0.5 * I.dx[0] * I.dx[1] * I.dx[2]);
-    }
-    // instances are contiguous in g: reduce per warp when the whole warp shares one, then
-    // per block (one atomic per instance present in the block)
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ii0 = __shfl_sync(0xffffffffu, ii, 0);
-    const bool same = __all_sync(0xffffffffu, ii == ii0 || ii < 0);
-    if (same) {
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-        if (lane == 0) {
-            s_e[warp] = e;
-            s_ii[warp] = ii0;
-        }
-    } else {
-        if (ii >= 0) atomicAdd(sums + 2 * L.ninst + ii, e);
-        if (lane == 0) s_ii[warp] = -1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int cur = -1;
-        double acc = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            if (s_ii[w] < 0) continue;
-            if (s_ii[w] != cur) {
-                if (cur >= 0) atomicAdd(sums + 2 * L.ninst + cur, acc);
-                cur = s_ii[w];
-                acc = 0.0;
-            }
-            acc += s_e[w];
-        }
-        if (cur >= 0) atomicAdd(sums + 2 * L.ninst + cur, acc);
+        const double t = block_sum(e, red);
+        if (threadIdx.x == 0 && t != 0.0) atomicAdd(sums + 2 * L.ninst + ii, t * (0.5 * I.dx[0] * I.dx[1] * I.dx[2]));
+        lo = hi;
     }
 }
 
@@ -503,10 +502,11 @@ cudaError_t launch_ghost(int fp64, const Launch &L, int axis, long long per_inst
 
 cudaError_t launch_field_energy(int fp64, const Launch &L, double *sums, cudaStream_t s)
 {
+    const unsigned nb = (unsigned)((L.total_cells + kEnergyCells - 1) / kEnergyCells);
     if (fp64)
-        k_field_energy<double><<<blocks_for(L.total_cells, 256), 256, 0, s>>>(L, sums);
+        k_field_energy<double><<<nb, 256, 0, s>>>(L, sums);
     else
-        k_field_energy<float><<<blocks_for(L.total_cells, 256), 256, 0, s>>>(L, sums);
+        k_field_energy<float><<<nb, 256, 0, s>>>(L, sums);
     return cudaGetLastError();
 }
 

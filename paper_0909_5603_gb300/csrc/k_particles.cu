@@ -77,56 +77,68 @@ __device__ __forceinline__ void load_particle(const InstDev &I, int lay, int pos
     w = ((const R *)I.w[lay])[pos];
 }
 
+// FP64 kinetic energy and charge sums per instance.  Each block takes kSumTiles
+// consecutive tiles of the launch and adds, for every instance they belong to, its part
+// with one pair of atomics (one pair per tile before: tens of thousands on two addresses).
+constexpr int kSumTiles = 16;
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_particle_sums(Launch L, double *sums /* 2 per instance */)
 {
-    const int g = blockIdx.x;
-    const int ii = find_instance(L.tile_start, L.ninst, g);
-    const InstDev &I = L.inst[ii];
-    const int t = g - L.tile_start[ii];
-    const int cur = *I.cur;
-    const int s0 = I.seg[cur][t];
-    const int c0 = I.chunk_base[cur][t], c1 = I.chunk_base[cur][t + 1];
-    double ke = 0.0, q = 0.0;
-    for (int c = c0; c < c1; ++c) {
-        const int live = I.chunk_pre[cur][(long long)c * kPre + kDead];
-        const int start = s0 + (c - c0) * I.R;
-        for (int p = threadIdx.x; p < live; p += blockDim.x) {
-            const int pos = start + p;  // momenta and weight only: half the particle's bytes
-            R u[3];
-            for (int a = 0; a < 3; ++a) u[a] = ((const R *)I.u[cur][a])[pos];
-            const R w = ((const R *)I.w[cur])[pos];
-            if (sizeof(R) == 8) {
-                const double g2 = 1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
-                ke += (double)w * I.m * (sqrt(g2) - 1.0);
-            } else {
-                // FP32 storage: gamma - 1 = u^2 / (1 + gamma) in FP32 (no cancellation; the
-                // stored momenta carry FP32 precision anyway), summed in FP64
-                const float uu = (float)u[0] * (float)u[0] + (float)u[1] * (float)u[1] + (float)u[2] * (float)u[2];
-                ke += (double)((float)w * (uu / (1.f + sqrtf(1.f + uu)))) * I.m;
-            }
-            q += I.q * (double)w;
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        ke += __shfl_down_sync(0xffffffffu, ke, o);
-        q += __shfl_down_sync(0xffffffffu, q, o);
-    }
-    // one pair of atomics per block (the tile's instance), not per warp
     __shared__ double s_ke[8], s_q[8];
-    if ((threadIdx.x & 31) == 0) {
-        s_ke[threadIdx.x >> 5] = ke;
-        s_q[threadIdx.x >> 5] = q;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            a += s_ke[w];
-            b += s_q[w];
+    const int g0 = blockIdx.x * kSumTiles, g1 = min(g0 + kSumTiles, L.total_tiles);
+    if (g0 >= g1) return;
+    int ii = find_instance(L.tile_start, L.ninst, g0);
+    for (int lo = g0; lo < g1; ++ii) {
+        const int hi = min(g1, L.tile_start[ii + 1]);
+        const InstDev &I = L.inst[ii];
+        const int cur = *I.cur;
+        double ke = 0.0, q = 0.0;
+        for (int g = lo; g < hi; ++g) {
+            const int t = g - L.tile_start[ii];
+            const int s0 = I.seg[cur][t];
+            const int c0 = I.chunk_base[cur][t], c1 = I.chunk_base[cur][t + 1];
+            for (int c = c0; c < c1; ++c) {
+                const int live = I.chunk_pre[cur][(long long)c * kPre + kDead];
+                const int start = s0 + (c - c0) * I.R;
+                for (int p = threadIdx.x; p < live; p += blockDim.x) {
+                    const int pos = start + p;  // momenta and weight only: half the particle's bytes
+                    R u[3];
+                    for (int a = 0; a < 3; ++a) u[a] = ((const R *)I.u[cur][a])[pos];
+                    const R w = ((const R *)I.w[cur])[pos];
+                    if (sizeof(R) == 8) {
+                        const double g2 = 1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
+                        ke += (double)w * I.m * (sqrt(g2) - 1.0);
+                    } else {
+                        // FP32 storage: gamma - 1 = u^2 / (1 + gamma) in FP32 (no cancellation;
+                        // the stored momenta carry FP32 precision anyway), summed in FP64
+                        const float uu = (float)u[0] * (float)u[0] + (float)u[1] * (float)u[1] + (float)u[2] * (float)u[2];
+                        ke += (double)((float)w * (uu / (1.f + sqrtf(1.f + uu)))) * I.m;
+                    }
+                    q += I.q * (double)w;
+                }
+            }
         }
-        if (a != 0.0) atomicAdd(sums + 2 * ii + 0, a);
-        if (b != 0.0) atomicAdd(sums + 2 * ii + 1, b);
+        for (int o = 16; o > 0; o >>= 1) {
+            ke += __shfl_down_sync(0xffffffffu, ke, o);
+            q += __shfl_down_sync(0xffffffffu, q, o);
+        }
+        __syncthreads();  // the shared sums of the previous instance are read
+        if ((threadIdx.x & 31) == 0) {
+            s_ke[threadIdx.x >> 5] = ke;
+            s_q[threadIdx.x >> 5] = q;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                a += s_ke[w];
+                b += s_q[w];
+            }
+            if (a != 0.0) atomicAdd(sums + 2 * ii + 0, a);
+            if (b != 0.0) atomicAdd(sums + 2 * ii + 1, b);
+        }
+        lo = hi;
     }
 }
 
@@ -240,10 +252,11 @@ cudaError_t launch_readout(int fp64, const Launch &L, const int *const *start, i
 
 cudaError_t launch_particle_sums(int fp64, const Launch &L, double *sums, cudaStream_t s)
 {
+    const unsigned nb = (unsigned)((L.total_tiles + kSumTiles - 1) / kSumTiles);
     if (fp64)
-        k_particle_sums<double><<<L.total_tiles, 256, 0, s>>>(L, sums);
+        k_particle_sums<double><<<nb, 256, 0, s>>>(L, sums);
     else
-        k_particle_sums<float><<<L.total_tiles, 256, 0, s>>>(L, sums);
+        k_particle_sums<float><<<nb, 256, 0, s>>>(L, sums);
     return cudaGetLastError();
 }
 
