@@ -225,6 +225,16 @@ pic_status pic_load_lab_frame(pic_ctx *ctx, const pic_laser_lab *laser, const pi
 pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t *cell, const double *off3,
                               const double *u3, const double *w, const int32_t *id);
 
+/* pic_load_particles with the values in the context's storage precision: off3, u3 and w
+ * are float arrays for a PIC_PREC_FP32 context and double arrays for PIC_PREC_FP64 (then
+ * the call is pic_load_particles).  The particles of Sec. 2 as the step stores them, so
+ * an FP32 run moves and checks half the bytes on the host and places the values as they
+ * are (an offset must lie in [0,1) as a float).  Same layout, validation and errors as
+ * pic_load_particles; the arrays stay the caller's (page-locked host memory, e.g. from
+ * cudaHostAlloc, copies at the link's full rate). */
+pic_status pic_load_particles_stored(pic_ctx *ctx, int64_t n, const int32_t *cell, const void *off3,
+                                     const void *u3, const void *w, const int32_t *id);
+
 /* Overwrites one field component (PIC_EX .. PIC_JZ) with count = n0 n1 n2 host values. */
 pic_status pic_set_field(pic_ctx *ctx, int comp, const double *host, size_t count);
 
@@ -276,6 +286,15 @@ pic_status pic_num_particles(pic_ctx *ctx, int64_t *n_out);
  * context keeps. */
 pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off3, double *u3, double *w,
                              int32_t *id, int64_t cap, int64_t *n_out);
+
+/* pic_get_particles (the Sec. 2 macro-particles, canonical order) with the values in the
+ * storage precision: off3, u3 and w receive floats for a PIC_PREC_FP32 context (no
+ * widening on the host; the FP64 values pic_get_particles returns are exactly these
+ * widened) and doubles for PIC_PREC_FP64.  Same layout, cap rule, errors and staging
+ * buffer as pic_get_particles; into page-locked host memory the copies run at the
+ * link's full rate. */
+pic_status pic_get_particles_stored(pic_ctx *ctx, int32_t *cell, void *off3, void *u3, void *w, int32_t *id,
+                                    int64_t cap, int64_t *n_out);
 
 /* FP64 global diagnostics of the boosted frame, computed on the device and copied to
  * *out: field energy sum (E^2 + B^2) dV / 2, particles' kinetic energy sum w (gamma - 1)

@@ -37,7 +37,8 @@ EXPORTED = ["pic_default_options", "pic_create", "pic_destroy", "pic_last_error"
             "pic_set_stations", "pic_get_station", "pic_set_injection", "pic_set_laser_antenna",
             "pic_get_fields", "pic_get_gauss_residual", "pic_get_planes", "pic_put_planes",
             "pic_extract_particles", "pic_add_particles", "pic_adopt_slab", "pic_batch_set_persistent",
-            "pic_batch_autotune", "pic_get_planes_n", "pic_put_planes_n"]
+            "pic_batch_autotune", "pic_get_planes_n", "pic_put_planes_n", "pic_load_particles_stored",
+            "pic_get_particles_stored"]
 PIC_NOALLOC_RHO_MAX_CELLS = 1 << 20
 
 
@@ -135,6 +136,10 @@ def lib():
         L.pic_num_particles.argtypes = [vp, P(ctypes.c_int64)]
         L.pic_get_particles.restype = st
         L.pic_get_particles.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int64, P(ctypes.c_int64)]
+        L.pic_get_particles_stored.restype = st
+        L.pic_get_particles_stored.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int64, P(ctypes.c_int64)]
+        L.pic_load_particles_stored.restype = st
+        L.pic_load_particles_stored.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp]
         L.pic_get_diagnostics.restype = st
         L.pic_get_diagnostics.argtypes = [vp, P(pic_diag)]
         L.pic_set_profiling.restype = st
@@ -297,6 +302,7 @@ class Simulation:
         self.ndim = ndim
         self.n = tuple(int(v) for v in n)
         self.ncell = self.n[0] * self.n[1] * self.n[2]
+        self.precision = int(precision)
         self.device = torch.cuda.current_device() if device is None else int(device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         opt = pic_default_options()
@@ -346,13 +352,29 @@ class Simulation:
             pass
 
     # -- loading
+    @property
+    def stored_dtype(self):
+        """numpy type of the particle values as the device stores them."""
+        return np.float32 if self.precision == PIC_PREC_FP32 else np.float64
+
     def load_particles(self, cell, off, u, w, ids=None):
+        """Replaces the particles.  float32 off, u and w on an FP32 context go in as they
+        are (pic_load_particles_stored: no FP64 copy, half the bytes); anything else is
+        taken as FP64 (pic_load_particles)."""
         cell = np.ascontiguousarray(cell, dtype=np.int32)
         npart = cell.size
+        ids = None if ids is None else np.ascontiguousarray(ids, dtype=np.int32)
+        arrs = [np.asarray(a) for a in (off, u, w)]
+        if self.precision == PIC_PREC_FP32 and all(a.dtype == np.float32 for a in arrs):
+            off, u, w = (np.ascontiguousarray(a) for a in arrs)
+            if off.size != 3 * npart or u.size != 3 * npart or w.size != npart:
+                raise ValueError("off and u need 3 values per particle, w one")
+            _check(lib().pic_load_particles_stored(self.h, npart, _ptr(cell), _ptr(off), _ptr(u), _ptr(w), _ptr(ids)),
+                   self.h)
+            return
         off = np.ascontiguousarray(np.asarray(off, np.float64).reshape(npart, 3))
         u = np.ascontiguousarray(np.asarray(u, np.float64).reshape(npart, 3))
         w = np.ascontiguousarray(w, dtype=np.float64)
-        ids = None if ids is None else np.ascontiguousarray(ids, dtype=np.int32)
         _check(lib().pic_load_particles(self.h, npart, _ptr(cell), _ptr(off), _ptr(u), _ptr(w), _ptr(ids)), self.h)
 
     def load_lab_frame(self, laser=None, plasma=None, beam=None):
@@ -424,17 +446,29 @@ class Simulation:
         _check(lib().pic_num_particles(self.h, ctypes.byref(v)), self.h)
         return int(v.value)
 
-    def get_particles(self):
+    def get_particles(self, stored=False, out=None):
+        """The live particles in canonical order: dict of cell (n,), off (n, 3), u (n, 3), w
+        (n,), id (n,).  stored: values in the storage precision (float32 for an FP32
+        context; pic_get_particles_stored), else FP64.  out: a dict of such arrays with room
+        for at least n particles (any of the five keys; e.g. page-locked buffers reused
+        across calls), filled in place and returned cut to n."""
         n = self.num_particles()
-        cell = np.empty(n, np.int32)
-        off = np.empty((n, 3))
-        u = np.empty((n, 3))
-        w = np.empty(n)
-        ids = np.empty(n, np.int32)
+        vt = self.stored_dtype if stored else np.float64
+        shapes = dict(cell=((n,), np.int32), off=((n, 3), vt), u=((n, 3), vt), w=((n,), vt), id=((n,), np.int32))
+        arrs = {}
+        for k, (shape, dt) in shapes.items():
+            if out is None or k not in out:
+                arrs[k] = np.empty(shape, dt)
+                continue
+            a = out[k]
+            per = int(np.prod(shape[1:])) if len(shape) > 1 else 1
+            if a.dtype != dt or not a.flags.c_contiguous or a.size < n * per:
+                raise ValueError(f"out[{k!r}] must be a C-contiguous {np.dtype(dt).name} array of >= {n * per} values")
+            arrs[k] = a.reshape(-1)[:n * per].reshape(shape)
         got = ctypes.c_int64()
-        _check(lib().pic_get_particles(self.h, _ptr(cell), _ptr(off), _ptr(u), _ptr(w), _ptr(ids), n,
-                                       ctypes.byref(got)), self.h)
-        return dict(cell=cell, off=off, u=u, w=w, id=ids)
+        fn = lib().pic_get_particles_stored if stored else lib().pic_get_particles
+        _check(fn(self.h, *(_ptr(arrs[k]) for k in ("cell", "off", "u", "w", "id")), n, ctypes.byref(got)), self.h)
+        return arrs
 
     # -- z-slab exchange
     def get_planes(self, comp, k0, nk):

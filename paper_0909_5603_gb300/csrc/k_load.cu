@@ -1,8 +1,9 @@
 // k_load.cu -- device side of the particle loads.
 //
-// k_place: particles arrive in FP64 in any order together with their slot in the
-// canonical (tile-sorted) order, which the host computed with a stable counting sort;
-// each thread converts one particle to the storage precision and writes it to its slot.
+// k_place: particles arrive in FP64 (or, for an FP32 context, in FP32) in any order
+// together with their slot in the canonical (tile-sorted) order, which the host computed
+// with a stable counting sort; each thread converts one particle to the storage precision
+// and writes it to its slot.
 //
 // k_plasma_count / k_plasma_write: the lab-frame plasma of pic_load_lab_frame generated
 // on the device instead of on the host.  Every cell draws `ppc` candidates from the
@@ -133,14 +134,16 @@ __device__ int plasma_candidate(const PlasmaGen &G, long long cidx, int p, int &
 
 }  // namespace
 
-template <typename R>
+// S: the source precision (an FP32 source widens exactly and narrows back to itself)
+template <typename R, typename S>
 __global__ void __launch_bounds__(256) k_place(InstDev I, PlaceSrc s)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
-    const double off[3] = {s.off[3 * i], s.off[3 * i + 1], s.off[3 * i + 2]};
-    const double u[3] = {s.u[3 * i], s.u[3 * i + 1], s.u[3 * i + 2]};
-    store_particle<R>(I, s.slot[i], s.cell[i], off, u, s.w[i], s.id ? s.id[i] : (int)(s.id_base + i));
+    const S *so = (const S *)s.off, *su = (const S *)s.u, *sw = (const S *)s.w;
+    const double off[3] = {(double)so[3 * i], (double)so[3 * i + 1], (double)so[3 * i + 2]};
+    const double u[3] = {(double)su[3 * i], (double)su[3 * i + 1], (double)su[3 * i + 2]};
+    store_particle<R>(I, s.slot[i], s.cell[i], off, u, (double)sw[i], s.id ? s.id[i] : (int)(s.id_base + i));
 }
 
 // Read-out staging (storage precision, canonical order) placed again: particle i goes to
@@ -205,8 +208,9 @@ cudaError_t launch_place(int fp64, const InstDev &I, const PlaceSrc &s, cudaStre
 {
     if (s.n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((s.n + 255) / 256);
-    if (fp64) k_place<double><<<blocks, 256, 0, st>>>(I, s);
-    else k_place<float><<<blocks, 256, 0, st>>>(I, s);
+    if (fp64) k_place<double, double><<<blocks, 256, 0, st>>>(I, s);
+    else if (s.f32) k_place<float, float><<<blocks, 256, 0, st>>>(I, s);
+    else k_place<float, double><<<blocks, 256, 0, st>>>(I, s);
     return cudaGetLastError();
 }
 

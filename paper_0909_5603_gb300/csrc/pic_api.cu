@@ -50,6 +50,7 @@ struct pic_ctx {
     Launch L{};
     size_t smem = 0;
     long long ncell = 0;
+    FastDiv fd_ts[3] = {};  // host division by the tile extents (cell -> tile on loads)
     long long ghost_max = 0;
     bool any_periodic[3] = {false, false, false};
     int max_sweeps = 0;
@@ -428,6 +429,7 @@ extern "C" pic_status pic_create(const pic_grid *grid, const double dx[3], doubl
     }
     h.div_n0 = make_fastdiv(c->n[0]);
     h.div_n1 = make_fastdiv(c->n[1]);
+    for (int a = 0; a < 3; ++a) c->fd_ts[a] = make_fastdiv(h.ts[a]);
     h.jlo = -shape_order;
     for (int a = 0; a < 3; ++a) h.jdim[a] = activeaxis(c->ndim, a) ? ts[a] + (shape_order == 2 ? 5 : 3) : 1;
     const size_t boxb = ((size_t)h.box[0] * h.box[1] * h.box[2] * c->es + 127) / 128 * 128;
@@ -689,11 +691,16 @@ static void widen_in_place(double *d, size_t n)
     }
 }
 
+// Tile of a valid cell index (0 <= cell < ncell), by multiply-shift divisions: the loads
+// and read-outs map tens of millions of particles with it.
 static int tile_of_cell(const pic_ctx *c, int cell)
 {
     const InstDev &h = c->h;
-    const int ci = cell % c->n[0], cj = (cell / c->n[0]) % c->n[1], ck = cell / (c->n[0] * c->n[1]);
-    return ci / h.ts[0] + h.nt[0] * (cj / h.ts[1] + h.nt[1] * (ck / h.ts[2]));
+    const int cyz = fast_div(cell, h.div_n0);
+    const int ci = cell - cyz * c->n[0];
+    const int ck = fast_div(cyz, h.div_n1);
+    const int cj = cyz - ck * c->n[1];
+    return fast_div(ci, c->fd_ts[0]) + h.nt[0] * (fast_div(cj, c->fd_ts[1]) + h.nt[1] * fast_div(ck, c->fd_ts[2]));
 }
 
 // Device scratch for a load, released when it goes out of scope.
@@ -712,26 +719,27 @@ struct LoadScratch {
     }
 };
 
-// Uploads n FP64 particles (host arrays, any order) with their canonical slots and places
-// them on the device in the storage precision (k_place).
-static pic_status place_from_host(pic_ctx *c, int64_t n, const int32_t *cell, const double *off, const double *u,
-                                  const double *w, const int32_t *id, long long id_base, const std::vector<int> &slot)
+// Uploads n particles (host arrays, any order; values FP64, or FP32 when f32 is set) with
+// their canonical slots and places them on the device in the storage precision (k_place).
+static pic_status place_from_host(pic_ctx *c, int64_t n, const int32_t *cell, const void *off, const void *u,
+                                  const void *w, const int32_t *id, long long id_base, const std::vector<int> &slot,
+                                  bool f32 = false)
 {
     if (n <= 0) return PIC_OK;
+    const size_t vs = f32 ? sizeof(float) : sizeof(double);
     LoadScratch S{c, {}};
     int *d_cell = (int *)S.get(sizeof(int) * n), *d_slot = (int *)S.get(sizeof(int) * n);
-    double *d_off = (double *)S.get(sizeof(double) * 3 * n), *d_u = (double *)S.get(sizeof(double) * 3 * n);
-    double *d_w = (double *)S.get(sizeof(double) * n);
+    void *d_off = S.get(vs * 3 * n), *d_u = S.get(vs * 3 * n), *d_w = S.get(vs * n);
     int *d_id = id ? (int *)S.get(sizeof(int) * n) : nullptr;
     if (!d_cell || !d_slot || !d_off || !d_u || !d_w || (id && !d_id))
         return fail(c, PIC_ERR_OOM, "no device memory to stage %lld particles", (long long)n);
     CUDA_OR_FAIL(c, cudaMemcpyAsync(d_cell, cell, sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(d_slot, slot.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_off, off, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_u, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_w, w, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_off, off, vs * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_u, u, vs * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(d_w, w, vs * n, cudaMemcpyHostToDevice, c->stream));
     if (id) CUDA_OR_FAIL(c, cudaMemcpyAsync(d_id, id, sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
-    PlaceSrc src{d_cell, d_off, d_u, d_w, d_id, d_slot, (long long)n, id_base};
+    PlaceSrc src{d_cell, d_off, d_u, d_w, d_id, d_slot, (long long)n, id_base, f32 ? 1 : 0};
     CUDA_OR_FAIL(c, launch_place(c->fp64, c->h, src, c->stream));
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));  // before the scratch is released
     return PIC_OK;
@@ -824,12 +832,34 @@ static pic_status finish_relayout(pic_ctx *c, const std::vector<int> &seg)
     return PIC_OK;
 }
 
-static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, const double *off, const double *u,
-                                const double *w, const int32_t *id, bool keep_state = false)
+// The first invalid particle of [b, e) (kind 1: cell, 2: offset, 3: momentum or weight),
+// or -1; values of type V.
+template <typename V>
+static int64_t first_invalid(const pic_ctx *c, const int32_t *cell, const V *off, const V *u, const V *w, int64_t b,
+                             int64_t e, int &kind)
+{
+    for (int64_t p = b; p < e; ++p) {
+        kind = 0;
+        if (cell[p] < 0 || cell[p] >= c->ncell) kind = 1;
+        for (int a = 0; a < 3 && !kind; ++a) {
+            if (!activeaxis(c->ndim, a)) continue;
+            const V o = off[3 * p + a];
+            if (!(o >= V(0) && o < V(1))) kind = 2;
+        }
+        if (!kind && !(std::isfinite(u[3 * p]) && std::isfinite(u[3 * p + 1]) && std::isfinite(u[3 * p + 2]) &&
+                       std::isfinite(w[p])))
+            kind = 3;
+        if (kind) return p;
+    }
+    return -1;
+}
+
+static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, const void *offv, const void *uv,
+                                const void *wv, const int32_t *id, bool keep_state = false, bool f32 = false)
 {
     InstDev &h = c->h;
     if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", (long long)n);
-    if (n > 0 && (!cell || !off || !u || !w)) return fail(c, PIC_ERR_ARG, "particle arrays must not be NULL");
+    if (n > 0 && (!cell || !offv || !uv || !wv)) return fail(c, PIC_ERR_ARG, "particle arrays must not be NULL");
     // validation and a stable counting sort by tile id, on T host threads over contiguous
     // ranges: each range finds its first invalid particle (the lowest over the ranges is
     // the one reported) and its tile histogram; slots are then assigned
@@ -840,26 +870,24 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
     std::vector<std::vector<int>> hist(T);
     std::vector<int> seg(h.ntiles + 1, 0), slot(n > 0 ? n : 1);
     parallel_ranges(n, T, [&](int t, int64_t b, int64_t e) {
-        for (int64_t p = b; p < e; ++p) {
+        std::vector<int> &hc = hist[t];
+        hc.assign(h.ntiles, 0);
+        // blocks of particles: checked, then their tiles counted while still in cache
+        constexpr int64_t kBlock = 4096;
+        for (int64_t b0 = b; b0 < e; b0 += kBlock) {
+            const int64_t e0 = std::min(e, b0 + kBlock);
             int kind = 0;
-            if (cell[p] < 0 || cell[p] >= c->ncell) kind = 1;
-            for (int a = 0; a < 3 && !kind; ++a) {
-                if (!activeaxis(c->ndim, a)) continue;
-                const double o = off[3 * p + a];
-                if (!(o >= 0.0 && o < 1.0)) kind = 2;
-            }
-            if (!kind && (!finite3(u + 3 * p) || !std::isfinite(w[p]))) kind = 3;
-            if (kind) {
+            const int64_t p = f32 ? first_invalid(c, cell, (const float *)offv, (const float *)uv, (const float *)wv, b0, e0, kind)
+                                  : first_invalid(c, cell, (const double *)offv, (const double *)uv, (const double *)wv, b0, e0, kind);
+            if (p >= 0) {
                 bad[t] = p;
                 bad_kind[t] = kind;
                 return;
             }
-        }
-        std::vector<int> &hc = hist[t];
-        hc.assign(h.ntiles, 0);
-        for (int64_t p = b; p < e; ++p) {
-            slot[p] = tile_of_cell(c, cell[p]);
-            hc[slot[p]]++;
+            for (int64_t q = b0; q < e0; ++q) {
+                slot[q] = tile_of_cell(c, cell[q]);
+                hc[slot[q]]++;
+            }
         }
     });
     int first = 0;
@@ -870,7 +898,7 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
         if (bad_kind[first] == 1) return fail(c, PIC_ERR_ARG, "particle %lld: cell %d outside the grid", (long long)p, cell[p]);
         if (bad_kind[first] == 2) {
             for (int a = 0; a < 3; ++a) {
-                const double o = off[3 * p + a];
+                const double o = f32 ? (double)((const float *)offv)[3 * p + a] : ((const double *)offv)[3 * p + a];
                 if (activeaxis(c->ndim, a) && !(o >= 0.0 && o < 1.0))
                     return fail(c, PIC_ERR_ARG, "particle %lld: offset %g outside [0,1)", (long long)p, o);
             }
@@ -896,7 +924,7 @@ static pic_status load_internal(pic_ctx *c, int64_t n, const int32_t *cell, cons
     });
     pic_status st = ensure_particle_capacity(c, n);
     if (st != PIC_OK) return st;
-    if ((st = place_from_host(c, n, cell, off, u, w, id, 0, slot)) != PIC_OK) return st;
+    if ((st = place_from_host(c, n, cell, offv, uv, wv, id, 0, slot, f32)) != PIC_OK) return st;
     return keep_state ? finish_relayout(c, seg) : finish_load(c, seg);
 }
 
@@ -910,6 +938,18 @@ extern "C" pic_status pic_load_particles(pic_ctx *ctx, int64_t n, const int32_t 
     ctx->h.ion = 0;  // particles loaded directly carry no ion background
     ctx->beam_first_id = INT_MAX;
     return load_internal(ctx, n, cell, off3, u3, w, id);
+}
+
+extern "C" pic_status pic_load_particles_stored(pic_ctx *ctx, int64_t n, const int32_t *cell, const void *off3,
+                                                const void *u3, const void *w, const int32_t *id)
+{
+    if (!ctx) return PIC_ERR_ARG;
+    if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_load_particles_stored on a batch");
+    cudaSetDevice(ctx->device);
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->h.ion = 0;
+    ctx->beam_first_id = INT_MAX;
+    return load_internal(ctx, n, cell, off3, u3, w, id, false, !ctx->fp64);
 }
 
 extern "C" pic_status pic_set_laser_antenna(pic_ctx *ctx, const pic_laser_lab *laser, double z_lab)
@@ -1020,8 +1060,19 @@ extern "C" pic_status pic_set_field(pic_ctx *ctx, int comp, const double *host, 
     if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "pic_set_field on a batch");
     if (comp < PIC_EX || comp > PIC_JZ) return fail(ctx, PIC_ERR_ARG, "component %d cannot be set", comp);
     if (!host || count < (size_t)ctx->ncell) return fail(ctx, PIC_ERR_ARG, "need %lld values", ctx->ncell);
-    for (long long i = 0; i < ctx->ncell; ++i)
-        if (!std::isfinite(host[i])) return fail(ctx, PIC_ERR_NAN, "non-finite field value at %lld", i);
+    {
+        const int T = host_workers(ctx->ncell);
+        std::vector<long long> bad(T, -1);
+        parallel_ranges(ctx->ncell, T, [&](int t, int64_t b, int64_t e) {
+            for (int64_t i = b; i < e; ++i)
+                if (!std::isfinite(host[i])) {
+                    bad[t] = i;
+                    return;
+                }
+        });
+        for (int t = 0; t < T; ++t)  // the first one over the ranges
+            if (bad[t] >= 0) return fail(ctx, PIC_ERR_NAN, "non-finite field value at %lld", bad[t]);
+    }
     cudaSetDevice(ctx->device);
     return set_field_internal(ctx, comp, host);
 }
@@ -1522,8 +1573,8 @@ static pic_status ensure_staging(pic_ctx *ctx)
     return PIC_OK;
 }
 
-extern "C" pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off3, double *u3, double *w, int32_t *id,
-                                        int64_t cap, int64_t *n_out)
+static pic_status get_particles_internal(pic_ctx *ctx, int32_t *cell, void *off3v, void *u3v, void *wv, int32_t *id,
+                                         int64_t cap, int64_t *n_out, bool widen)
 {
     if (!ctx || !n_out) return PIC_ERR_ARG;
     if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "getters take a member, not a batch");
@@ -1540,7 +1591,8 @@ extern "C" pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off
     CUDA_OR_FAIL(ctx, launch_readout(ctx->fp64, ctx->L, ctx->d_start_ptr, ctx->st_cell, ctx->st_off, ctx->st_u, ctx->st_w,
                                      ctx->st_id, ctx->stream));
     // values copied in the storage precision (FP32: half the bytes) into the caller's
-    // arrays, then widened there in place
+    // arrays, then widened there in place when FP64 values are asked for
+    double *off3 = (double *)off3v, *u3 = (double *)u3v, *w = (double *)wv;
     const size_t n = (size_t)live, es = ctx->es;
     if (cell) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(cell, ctx->st_cell, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     if (id) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(id, ctx->st_id, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1548,12 +1600,24 @@ extern "C" pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off
     if (u3) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(u3, ctx->st_u, 3 * n * es, cudaMemcpyDeviceToHost, ctx->stream));
     if (w) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(w, ctx->st_w, n * es, cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
-    if (!ctx->fp64) {
+    if (widen && !ctx->fp64) {
         if (off3) widen_in_place(off3, 3 * n);
         if (u3) widen_in_place(u3, 3 * n);
         if (w) widen_in_place(w, n);
     }
     return check_device_error(ctx);
+}
+
+extern "C" pic_status pic_get_particles(pic_ctx *ctx, int32_t *cell, double *off3, double *u3, double *w, int32_t *id,
+                                        int64_t cap, int64_t *n_out)
+{
+    return get_particles_internal(ctx, cell, off3, u3, w, id, cap, n_out, true);
+}
+
+extern "C" pic_status pic_get_particles_stored(pic_ctx *ctx, int32_t *cell, void *off3, void *u3, void *w, int32_t *id,
+                                               int64_t cap, int64_t *n_out)
+{
+    return get_particles_internal(ctx, cell, off3, u3, w, id, cap, n_out, false);
 }
 
 // ---- z-slab exchange (domain decomposition along z) -----------------------------------

@@ -12,11 +12,12 @@ namespace pic {
 // for off and u); slot[i] is particle i's position in the sorted buffer.
 struct PlaceSrc {
     const int *cell;
-    const double *off, *u, *w;
+    const void *off, *u, *w;  // FP64, or FP32 when f32 is set
     const int *id;  // null: ids id_base + i
     const int *slot;
     long long n;
     long long id_base;
+    int f32;
 };
 
 // Lab-frame plasma drawn on the device (see k_load.cu)
