@@ -457,11 +457,12 @@ __device__ __forceinline__ void filter_col_block(const Launch &L, int axis, cons
     }
 }
 
-// x axis: warp w takes rows w, w + 8, w + 16, w + 24 of the pencil; per row it loads the
-// kPencil + 2P window of all three components with coalesced loads into its own slice of
-// shared memory (warp-synchronous, no block barrier) and each lane forms two outputs
-// from it.  Cells within P of an end convolve the wrapped window (periodic) or run the
-// passes (absorbing).
+// x axis: warp w takes rows w, w + 8, w + 16, w + 24 of the pencil.  It first loads the
+// kPencil + 2P window of all three components of all four rows into registers
+// (coalesced, all in flight together), then per row stores the window into its own
+// slice of shared memory (warp-synchronous, no block barrier) and each lane forms two
+// outputs from it.  Cells within P of an end convolve the wrapped window (periodic) or
+// run the passes (absorbing).
 // sw: shared memory for the windows, 8 x 3 x (kPencil + 2P) values
 template <typename R, int P>
 __device__ __forceinline__ void filter_row_block(const Launch &L, const long long *pencil_start, int src_is_jt,
@@ -483,26 +484,45 @@ __device__ __forceinline__ void filter_row_block(const Launch &L, const long lon
     void *const *src = src_is_jt ? I.Jt : I.J;
     void *const *dst = src_is_jt ? I.J : I.Jt;
     R(*win)[W] = reinterpret_cast<R(*)[W]>(sw + warp * 3 * W);
-#pragma unroll 1
-    for (int rr = warp; rr < 32; rr += 8) {
-        const long long row = r * 32 + rr;
-        if (row >= (long long)I.n[1] * I.n[2]) break;
-        const int y = (int)(row % I.n[1]), z = (int)(row / I.n[1]);
-        const long long lo = I.gh[0] + I.sy * (long long)(y + I.gh[1]) + I.sz * (long long)(z + I.gh[2]);
+    constexpr int NR = 4, NC = (W + 31) / 32;  // rows per warp, window chunks of 32
+    const long long nrows = (long long)I.n[1] * I.n[2];
+    long long lo[NR];
+    R pre[NR][3][NC];
+    // this lane's window cells (the same in every row)
+    int qi[NC];
+    bool qok[NC];
 #pragma unroll
-        for (int i0 = 0; i0 < W; i0 += 32) {
-            const int i = i0 + lane;
-            if (i < W) {
-                int q = q0 - P + i;
-                bool ok = true;
-                if (!inside && (q < 0 || q >= n)) {
-                    if (per) q = ((q % n) + n) % n;
-                    else ok = false;
-                }
-#pragma unroll
-                for (int comp = 0; comp < 3; ++comp) win[comp][i] = ok ? ((const R *)src[comp])[lo + q] : R(0);
-            }
+    for (int c = 0; c < NC; ++c) {
+        const int i = 32 * c + lane;
+        int q = q0 - P + i;
+        bool ok = i < W;
+        if (ok && !inside && (q < 0 || q >= n)) {
+            if (per) q = ((q % n) + n) % n;
+            else ok = false;
         }
+        qi[c] = q;
+        qok[c] = ok;
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const long long row = r * 32 + warp + 8 * j;
+        const bool rok = row < nrows;
+        const int y = rok ? (int)(row % I.n[1]) : 0, z = rok ? (int)(row / I.n[1]) : 0;
+        lo[j] = I.gh[0] + I.sy * (long long)(y + I.gh[1]) + I.sz * (long long)(z + I.gh[2]);
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                pre[j][comp][c] = (rok && qok[c]) ? ((const R *)src[comp])[lo[j] + qi[c]] : R(0);
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        if (r * 32 + warp + 8 * j >= nrows) break;
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (32 * c + lane < W) win[comp][32 * c + lane] = pre[j][comp][c];
         __syncwarp();
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -535,10 +555,10 @@ __device__ __forceinline__ void filter_row_block(const Launch &L, const long lon
                     }
                     v = w[P];
                 }
-                ((R *)dst[comp])[lo + q] = v;
+                ((R *)dst[comp])[lo[j] + q] = v;
             }
         }
-        __syncwarp();  // the window is reloaded for the next row
+        __syncwarp();  // the window is rewritten for the next row
     }
 }
 
