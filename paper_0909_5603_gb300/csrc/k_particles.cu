@@ -195,31 +195,35 @@ __global__ void __launch_bounds__(256) k_rho(Launch L, double *rho /* dense n0*n
 // -------------------------------------------------------------------------------------
 // Host-side launchers (called from pic_api.cu).
 // -------------------------------------------------------------------------------------
-cudaError_t dispatch_particles_f32(int ndim, int order, int pusher, const Launch *L, size_t smem, cudaStream_t s);
-cudaError_t dispatch_particles_f64(int ndim, int order, int pusher, const Launch *L, size_t smem, cudaStream_t s);
-cudaError_t dispatch_particles_f32_inj(int ndim, int order, int pusher, const Launch *L, size_t smem, cudaStream_t s);
-cudaError_t dispatch_particles_f64_inj(int ndim, int order, int pusher, const Launch *L, size_t smem, cudaStream_t s);
+cudaError_t dispatch_particles_f32(int ndim, int order, int pusher, const Launch *L, const InstDev *one, size_t smem,
+                                   cudaStream_t s);
+cudaError_t dispatch_particles_f64(int ndim, int order, int pusher, const Launch *L, const InstDev *one, size_t smem,
+                                   cudaStream_t s);
+cudaError_t dispatch_particles_f32_inj(int ndim, int order, int pusher, const Launch *L, const InstDev *one, size_t smem,
+                                   cudaStream_t s);
+cudaError_t dispatch_particles_f64_inj(int ndim, int order, int pusher, const Launch *L, const InstDev *one, size_t smem,
+                                   cudaStream_t s);
 
-static cudaError_t dispatch_particles(int ndim, int order, int fp64, int pusher, bool inj, const Launch *L, size_t smem,
-                                      cudaStream_t s)
+static cudaError_t dispatch_particles(int ndim, int order, int fp64, int pusher, bool inj, const Launch *L,
+                                      const InstDev *one, size_t smem, cudaStream_t s)
 {
     if (fp64)
-        return inj ? dispatch_particles_f64_inj(ndim, order, pusher, L, smem, s)
-                   : dispatch_particles_f64(ndim, order, pusher, L, smem, s);
-    return inj ? dispatch_particles_f32_inj(ndim, order, pusher, L, smem, s)
-               : dispatch_particles_f32(ndim, order, pusher, L, smem, s);
+        return inj ? dispatch_particles_f64_inj(ndim, order, pusher, L, one, smem, s)
+                   : dispatch_particles_f64(ndim, order, pusher, L, one, smem, s);
+    return inj ? dispatch_particles_f32_inj(ndim, order, pusher, L, one, smem, s)
+               : dispatch_particles_f32(ndim, order, pusher, L, one, smem, s);
 }
 
-cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, bool inj, const Launch &L, size_t smem,
-                             cudaStream_t s)
+cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, bool inj, const Launch &L, const InstDev *one,
+                             size_t smem, cudaStream_t s)
 {
-    return dispatch_particles(ndim, order, fp64, pusher, inj, &L, smem, s);
+    return dispatch_particles(ndim, order, fp64, pusher, inj, &L, one, smem, s);
 }
 
 cudaError_t prepare_particles(int ndim, int order, int fp64, int pusher, size_t smem)
 {
-    cudaError_t e = dispatch_particles(ndim, order, fp64, pusher, false, nullptr, smem, 0);
-    return e == cudaSuccess ? dispatch_particles(ndim, order, fp64, pusher, true, nullptr, smem, 0) : e;
+    cudaError_t e = dispatch_particles(ndim, order, fp64, pusher, false, nullptr, nullptr, smem, 0);
+    return e == cudaSuccess ? dispatch_particles(ndim, order, fp64, pusher, true, nullptr, nullptr, smem, 0) : e;
 }
 
 int particle_chunk() { return kChunk; }

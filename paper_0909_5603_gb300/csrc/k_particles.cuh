@@ -575,11 +575,14 @@ __device__ __forceinline__ void scan_instance(const Launch &L, int ii, int mode,
     }
 }
 
-// The particle phase of tile g of the launch (its global index over the instances), by
-// one CTA of kNT threads.  INJ: instances with a beam injection plane (a separate
-// instantiation, so that the kernel without a plane carries none of its code).
+// The particle phase of tile t of instance I, by one CTA of kNT threads.  INJ: instances
+// with a beam injection plane (a separate instantiation, so that the kernel without a
+// plane carries none of its code).  I is the instance's entry of the launch's device
+// array, or, for a launch of one instance, a kernel parameter: its fields are then
+// operands from the constant bank, which no store of the kernel can alias, so they are
+// never reloaded after the particle write-out.
 template <int ND, int ORD, typename R, int PUSHER, bool INJ>
-__device__ __forceinline__ void particle_tile(const Launch &L, const int g)
+__device__ __forceinline__ void particle_tile(const InstDev &I, const int t)
 {
     constexpr bool kFixed = sizeof(R) == 4;  // FP32: fixed-point chunk accumulator + FP32 tile
     extern __shared__ __align__(128) unsigned char smem[];
@@ -593,9 +596,6 @@ __device__ __forceinline__ void particle_tile(const Launch &L, const int g)
     __shared__ int s_cnt[2][kNW][kBuckets];  // per-warp bucket counts, double-buffered per chunk
     __shared__ __align__(16) unsigned s_bmax[3][kNW];  // FP32: per-warp contribution bounds of the chunk
 
-    const int ii = find_instance(L.tile_start, L.ninst, g);
-    const InstDev &I = L.inst[ii];
-    const int t = g - L.tile_start[ii];
     const int out = *I.cur;  // the scan of this step already flipped the parity
     const int in = 1 - out;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1007,10 +1007,25 @@ __device__ __forceinline__ void particle_tile(const Launch &L, const int g)
         flush_j_double(I, T0, ND, sJD, jvol, jst, tid, kNT);
 }
 
+// the particle phase of tile g of the launch (its global index over the instances)
+template <int ND, int ORD, typename R, int PUSHER, bool INJ>
+__device__ __forceinline__ void particle_tile_of_launch(const Launch &L, const int g)
+{
+    const int ii = find_instance(L.tile_start, L.ninst, g);
+    particle_tile<ND, ORD, R, PUSHER, INJ>(L.inst[ii], g - L.tile_start[ii]);
+}
+
 template <int ND, int ORD, typename R, int PUSHER, bool INJ>
 __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launch L)
 {
-    particle_tile<ND, ORD, R, PUSHER, INJ>(L, blockIdx.x);
+    particle_tile_of_launch<ND, ORD, R, PUSHER, INJ>(L, blockIdx.x);
+}
+
+// a launch of one instance: the instance by value (tile = block)
+template <int ND, int ORD, typename R, int PUSHER, bool INJ>
+__global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles_one(const __grid_constant__ InstDev I)
+{
+    particle_tile<ND, ORD, R, PUSHER, INJ>(I, blockIdx.x);
 }
 
 }  // namespace pic

@@ -90,7 +90,7 @@ __device__ __forceinline__ void filter_item(const Launch &L, const long long *pe
 template <int ND, int ORD>
 __device__ __noinline__ void particle_item(const Launch &L, int g)
 {
-    particle_tile<ND, ORD, float, 0, false>(L, g);
+    particle_tile_of_launch<ND, ORD, float, 0, false>(L, g);
 }
 
 template <int ND>

@@ -3,9 +3,10 @@
 
 namespace pic {
 
-cudaError_t dispatch_particles_f64(int ndim, int order, int pusher, const Launch *L, size_t smem, cudaStream_t s)
+cudaError_t dispatch_particles_f64(int ndim, int order, int pusher, const Launch *L, const InstDev *one, size_t smem,
+                                     cudaStream_t s)
 {
-    return dispatch_particles_t<double, false>(ndim, order, pusher, L, smem, s);
+    return dispatch_particles_t<double, false>(ndim, order, pusher, L, one, smem, s);
 }
 
 }  // namespace pic

@@ -1260,7 +1260,8 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
         tm.begin(0);
         bool inj = c->h.inj_id0 != INT_MAX;
         for (auto m : c->members) inj = inj || m->h.inj_id0 != INT_MAX;
-        CUDA_OR_FAIL(c, launch_particles(c->ndim, c->order, fp64, c->opt.pusher, inj, L, c->smem, c->stream));
+        CUDA_OR_FAIL(c, launch_particles(c->ndim, c->order, fp64, c->opt.pusher, inj, L, c->is_batch ? nullptr : &c->h,
+                                         c->smem, c->stream));
         tm.end(0);
         launches += 3;
     }

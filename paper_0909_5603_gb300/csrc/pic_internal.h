@@ -71,8 +71,10 @@ cudaError_t launch_plasma_write(int fp64, const InstDev &I, const PlasmaGen &G, 
 cudaError_t launch_ion_current(int fp64, const Launch &L, cudaStream_t s);
 cudaError_t launch_rho_ion(const Launch &L, long long ncell, double *rho, cudaStream_t s);
 // inj: some instance of the launch has a beam injection plane
-cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, bool inj, const Launch &L, size_t smem,
-                             cudaStream_t s);
+// one: for a launch of one instance, its host copy (passed to the kernel by value); null
+// for a batch
+cudaError_t launch_particles(int ndim, int order, int fp64, int pusher, bool inj, const Launch &L, const InstDev *one,
+                             size_t smem, cudaStream_t s);
 int particle_chunk();
 int particle_threads();
 cudaError_t launch_scan(const Launch &L, int mode, int *const *dst, cudaStream_t s);
