@@ -343,7 +343,7 @@ def run_ours(args, rank, world):
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(0.5 * (nb_p + na_p)), "peak_kind": peak_kind,
-            "kernel": "k_particles<3,2,float,Vay>", "kernel_ms": kern_ms,
+            "kernel": "k_particles_one<3,2,float,Vay>", "kernel_ms": kern_ms,
             "bytes_per_launch": algo_bytes,
             "kernel_timing": "CUDA events around each launch in a second pass of the same K steps (direct launches)"}
 
