@@ -1439,6 +1439,15 @@ static cudaError_t d2h(pic_ctx *c, void *dst, const void *src, size_t bytes)
     return e == cudaSuccess ? cudaStreamSynchronize(c->stream) : e;
 }
 
+// The status of a sticky device error word (PIC_OK when it is 0).
+static pic_status device_error_status(pic_ctx *c, int err)
+{
+    if (err & kErrTimeout) return fail(c, PIC_ERR_TIMEOUT, "a bounded device wait timed out (error word 0x%x)", err);
+    if (err & kErrSpeed) return fail(c, PIC_ERR_PARTICLE_SPEED, "a particle moved a cell or more in one step, or is not finite (0x%x)", err);
+    if (err & (kErrInternal | kErrCapacity)) return fail(c, PIC_ERR_INTERNAL, "device consistency check failed (0x%x)", err);
+    return PIC_OK;
+}
+
 static pic_status check_device_error(pic_ctx *c)
 {
     int err = 0;
@@ -1940,22 +1949,27 @@ extern "C" pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out)
 {
     if (!ctx || !out) return PIC_ERR_ARG;
     if (ctx->is_batch) return fail(ctx, PIC_ERR_ARG, "getters take a member, not a batch");
-    pic_status st = pic_synchronize(ctx);
-    int err = 0;
-    d2h(ctx, &err, ctx->h.err, sizeof(int));
+    cudaSetDevice(ctx->device);
     std::memset(out, 0, sizeof(*out));
-    out->error_flags = err;
-    if (st != PIC_OK) return st;
-    CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_sums, 0, 3 * sizeof(double), ctx->stream));
-    if (ctx->loaded) CUDA_OR_FAIL(ctx, launch_particle_sums(ctx->fp64, ctx->L, ctx->d_sums, ctx->stream));
-    CUDA_OR_FAIL(ctx, launch_field_energy(ctx->fp64, ctx->L, ctx->d_sums, ctx->stream));
+    // the reductions, the live count and the read-back queued behind the work in flight,
+    // with one synchronisation
+    cudaStream_t s = ctx->stream;
+    CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_sums, 0, 3 * sizeof(double), s));
+    if (ctx->loaded) CUDA_OR_FAIL(ctx, launch_particle_sums(ctx->fp64, ctx->L, ctx->d_sums, s));
+    CUDA_OR_FAIL(ctx, launch_field_energy(ctx->fp64, ctx->L, ctx->d_sums, s));
+    if (ctx->loaded) CUDA_OR_FAIL(ctx, launch_scan(ctx->L, 1, ctx->d_start_ptr, s));
     double sums[3];
     unsigned long long lost = 0;
-    int live = 0;
-    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(sums, ctx->d_sums, sizeof(sums), cudaMemcpyDeviceToHost, ctx->stream));
-    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(&lost, ctx->h.lost, sizeof(lost), cudaMemcpyDeviceToHost, ctx->stream));
-    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
-    if (ctx->loaded && (st = count_live(ctx, 0, &live)) != PIC_OK) return st;
+    int live = 0, err = 0;
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(sums, ctx->d_sums, sizeof(sums), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(&lost, ctx->h.lost, sizeof(lost), cudaMemcpyDeviceToHost, s));
+    if (ctx->loaded) CUDA_OR_FAIL(ctx, cudaMemcpyAsync(&live, ctx->h.live, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(&err, ctx->h.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(s));
+    CUDA_OR_FAIL(ctx, cudaGetLastError());
+    out->error_flags = err;
+    pic_status st = device_error_status(ctx, err);
+    if (st != PIC_OK) return st;
     out->step = ctx->step;
     out->t = ctx->step * ctx->dt;
     out->kinetic_energy = sums[0];
@@ -1963,7 +1977,7 @@ extern "C" pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out)
     out->field_energy = sums[2];
     out->n_particles = live;
     out->n_lost = (int64_t)lost;
-    return check_device_error(ctx);
+    return PIC_OK;
 }
 
 // ------------------------------------------------------------------------------------
