@@ -93,8 +93,11 @@ __global__ void __launch_bounds__(256) k_particle_sums(Launch L, double *sums /*
         const int hi = min(g1, L.tile_start[ii + 1]);
         const InstDev &I = L.inst[ii];
         const int cur = *I.cur;
+        // an instance with a device error may hold a step's layout half written: its
+        // chunk records are not read (the read-out reports the error instead)
+        const bool skip = *(volatile const int *)I.err != 0;
         double ke = 0.0, q = 0.0;
-        for (int g = lo; g < hi; ++g) {
+        for (int g = skip ? hi : lo; g < hi; ++g) {
             const int t = g - L.tile_start[ii];
             const int s0 = I.seg[cur][t];
             const int c0 = I.chunk_base[cur][t], c1 = I.chunk_base[cur][t + 1];

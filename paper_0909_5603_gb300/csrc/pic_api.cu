@@ -1952,7 +1952,8 @@ extern "C" pic_status pic_get_diagnostics(pic_ctx *ctx, pic_diag *out)
     cudaSetDevice(ctx->device);
     std::memset(out, 0, sizeof(*out));
     // the reductions, the live count and the read-back queued behind the work in flight,
-    // with one synchronisation
+    // with one synchronisation; the particle sums skip an instance whose error word is set
+    // (its layout may be half written), and that error is what the call returns
     cudaStream_t s = ctx->stream;
     CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_sums, 0, 3 * sizeof(double), s));
     if (ctx->loaded) CUDA_OR_FAIL(ctx, launch_particle_sums(ctx->fp64, ctx->L, ctx->d_sums, s));
