@@ -1243,14 +1243,15 @@ static pic_status enqueue_step(pic_ctx *c, int mask)
         if (c->is_batch) {
             for (auto m : c->members)
                 CUDA_OR_FAIL(c, cudaMemsetAsync(m->h.J[0], 0, 3 * (size_t)m->h.cstride * m->es, c->stream));
+            bool ions = false;
+            for (auto m : c->members) ions = ions || m->h.ion != 0;
+            if (ions) {
+                CUDA_OR_FAIL(c, launch_ion_current(fp64, L, c->stream));
+                launches += 2;
+            }
         } else {
-            CUDA_OR_FAIL(c, cudaMemsetAsync(c->h.J[0], 0, 3 * (size_t)c->h.cstride * c->es, c->stream));
-        }
-        bool ions = c->h.ion != 0;
-        for (auto m : c->members) ions = ions || m->h.ion != 0;
-        if (ions) {
-            CUDA_OR_FAIL(c, launch_ion_current(fp64, L, c->stream));
-            launches += 2;
+            CUDA_OR_FAIL(c, launch_j_init_one(fp64, L, c->h, c->stream));
+            launches += c->h.ion ? 2 : 1;
         }
         tm.end(4);
         tm.begin(1);

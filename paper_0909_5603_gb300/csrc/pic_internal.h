@@ -68,6 +68,9 @@ cudaError_t launch_place_staged(int fp64, const InstDev &I, const StagedSrc &s, 
 cudaError_t launch_plasma_count(const PlasmaGen &G, int *count, cudaStream_t st);
 cudaError_t launch_plasma_write(int fp64, const InstDev &I, const PlasmaGen &G, const int *slot0, const int *id0,
                                 cudaStream_t st);
+// J of a step's start for a launch of one instance (h: its host copy): the ion faces
+// (when it has ions), then Jx = Jy = 0, Jz = the ion current, in one pass
+cudaError_t launch_j_init_one(int fp64, const Launch &L, const InstDev &h, cudaStream_t s);
 cudaError_t launch_ion_current(int fp64, const Launch &L, cudaStream_t s);
 cudaError_t launch_rho_ion(const Launch &L, long long ncell, double *rho, cudaStream_t s);
 // inj: some instance of the launch has a beam injection plane
