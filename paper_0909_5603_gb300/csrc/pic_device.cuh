@@ -218,8 +218,8 @@ __device__ __forceinline__ void acc_put(const Acc &acc, int idx, R a, R b)
 //
 // WX, WY, WZ: window extents covered (each ORD + 1 or ORD + 2).  A particle that keeps
 // its nodes along an axis has ORD + 1 non-zero entries there (the entry beyond is zero
-// and so is the running sum at the window's last entry), so a warp whose particles all
-// keep their x and y nodes can cover ORD + 1 entries along x and y and lose nothing.
+// and so is the running sum at the window's last entry), so a particle that keeps its x
+// and y nodes can be covered with ORD + 1 entries along x and y and lose nothing.
 // ------------------------------------------------------------------------------------
 template <int WX, int WY, int WZ, typename R, typename Acc>
 __device__ __forceinline__ void esirkepov3d(const R *S0x, const R *DSx, const R *S0y, const R *DSy, const R *S0z,
@@ -291,13 +291,95 @@ __device__ __forceinline__ void esirkepov3d(const R *S0x, const R *DSx, const R 
     }
 }
 
+// The entries of the W x W x W window outside the N x N x W one (N = ORD + 1 along x and
+// y): what a particle that changes its x or y nodes adds beyond the narrow window that
+// esirkepov3d<N, N, W> covers.  The values are those esirkepov3d<W, W, W> forms at the
+// same entries, so the narrow call plus this one is the wide deposit.  Called only by the
+// lanes that change their x or y nodes: for the others these entries are exactly zero
+// (their shape beyond entry N - 1 is zero and the running sums end at exactly zero), and
+// leaving them out keeps the extra atomics of a warp to the lanes that need them instead
+// of every lane.
+template <int N, int W, typename R, typename Acc>
+__device__ __forceinline__ void esirkepov3d_extra(const R *S0x, const R *DSx, const R *S0y, const R *DSy, const R *S0z,
+                                                  const R *DSz, R fx, R fy, R fz, int base, int jd0, int jd01, int jvol,
+                                                  const Acc &acc)
+{
+    const R half = R(0.5), third = R(1.0 / 3.0);
+    R Ay[W], Cy[W], Az[W], Cz[W];
+#pragma unroll
+    for (int m = 0; m < W; ++m) {
+        Ay[m] = S0y[m] + half * DSy[m];
+        Cy[m] = half * S0y[m] + third * DSy[m];
+        Az[m] = S0z[m] + half * DSz[m];
+        Cz[m] = half * S0z[m] + third * DSz[m];
+    }
+    R rx[W - 1], ry[W - 1];
+    {
+        R run = R(0);
+#pragma unroll
+        for (int i = 0; i < W - 1; ++i) {
+            run += DSx[i];
+            rx[i] = fx * run;
+        }
+        run = R(0);
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) {
+            run += DSy[j];
+            ry[j] = fy * run;
+        }
+    }
+    R rz[W - 1];
+    {
+        R run = R(0);
+#pragma unroll
+        for (int k = 0; k < W - 1; ++k) {
+            run += DSz[k];
+            rz[k] = fz * run;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const R Y = S0y[j] * Az[k] + DSy[j] * Cz[k];
+            const int row = base + jd0 * j + jd01 * k;
+#pragma unroll
+            for (int i = 0; i < W - 1; ++i)
+                if (i >= N - 1 || j >= N) acc_put<R>(acc, row + i, Y, rx[i]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const R X = S0x[i] * Az[k] + DSx[i] * Cz[k];
+            const int col = jvol + base + i + jd01 * k;
+#pragma unroll
+            for (int j = 0; j < W - 1; ++j)
+                if (i >= N || j >= N - 1) acc_put<R>(acc, col + jd0 * j, X, ry[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            if (i < N && j < N) continue;
+            const R X = S0x[i] * Ay[j] + DSx[i] * Cy[j];
+            const int col = 2 * jvol + base + i + jd0 * j;
+#pragma unroll
+            for (int k = 0; k < W - 1; ++k) acc_put<R>(acc, col + jd01 * k, X, rz[k]);
+        }
+    }
+}
+
 // The deposit of one particle; every lane of the warp calls it (a lane without a particle
 // passes f = 0 and a position inside the tile).  In 2D3V (x-z plane) Wx = DSx (S0z +
 // DSz/2), Wz = DSz (S0x + DSx/2) and the out-of-plane Jy = f_y' (S0x S0z + DSx S0z / 2 +
 // S0x DSz / 2 + DSx DSz / 3) with f_y' = (q w / dV) v_y; the 2D3V loops skip zero
-// contributions (up to 16 particles per cell contend there).  kNarrow (3D): the warp
-// covers ORD + 1 entries along x and y when none of its particles changes its x or y
-// nodes (one vote per warp), ORD + 2 otherwise.
+// contributions (up to 16 particles per cell contend there).  kNarrow (3D): every lane
+// covers ORD + 1 entries along x and y, and a lane whose particle changes its x or y nodes
+// adds the entries of the ORD + 2 window beyond them (esirkepov3d_extra), so the other
+// lanes of its warp add none of that window's zeros.
 template <int ND, int ORD, bool kDisp, bool kNarrow, typename R, typename Acc>
 __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3], const int l1[3], const R o1[3],
                                                   const R disp[3], R fx, R fy, R fz, int jlo, int jlo_y, int jd0,
@@ -312,10 +394,13 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
     if (ND == 3) {
         const int wsy = shape_window<ORD, kDisp>(l0[1], o0[1], l1[1], o1[1], disp[1], S0y, DSy, nwy) - jlo_y;
         const int base = wsx + jd0 * wsy + jd01 * wsz;
-        if (kNarrow && !__any_sync(0xffffffffu, nwx > ORD + 1 || nwy > ORD + 1))
+        if (kNarrow) {
             esirkepov3d<ORD + 1, ORD + 1, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
-        else
+            if (nwx > ORD + 1 || nwy > ORD + 1)
+                esirkepov3d_extra<ORD + 1, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
+        } else {
             esirkepov3d<W, W, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
+        }
     } else {
         // fy carries the out-of-plane factor (q w / dV) v_y here
         const int base = wsx + jd01 * wsz;
