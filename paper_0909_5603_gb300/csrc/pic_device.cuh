@@ -291,6 +291,68 @@ __device__ __forceinline__ void esirkepov3d(const R *S0x, const R *DSx, const R 
     }
 }
 
+// The entries of the N x N x W window outside the N x N x N one: what a particle that
+// changes its z nodes adds beyond the window narrow along z as well (Jx and Jy at the
+// last z entry, Jz at the last z face), with the values esirkepov3d<N, N, W> forms
+// there.  Called only by the lanes that change their z nodes: for the others these
+// entries are exactly zero (their z shape beyond entry N - 1 is zero and the running sum
+// along z ends at exactly zero).
+template <int N, int W, typename R, typename Acc>
+__device__ __forceinline__ void esirkepov3d_zextra(const R *S0x, const R *DSx, const R *S0y, const R *DSy, const R *S0z,
+                                                   const R *DSz, R fx, R fy, R fz, int base, int jd0, int jd01, int jvol,
+                                                   const Acc &acc)
+{
+    const R half = R(0.5), third = R(1.0 / 3.0);
+    constexpr int K = W - 1;  // the last z entry (Jx, Jy) and, less one, the last z face (Jz)
+    const R Azk = S0z[K] + half * DSz[K];
+    const R Czk = half * S0z[K] + third * DSz[K];
+    R rx[N - 1], ry[N - 1];
+    {
+        R run = R(0);
+#pragma unroll
+        for (int i = 0; i < N - 1; ++i) {
+            run += DSx[i];
+            rx[i] = fx * run;
+        }
+        run = R(0);
+#pragma unroll
+        for (int j = 0; j < N - 1; ++j) {
+            run += DSy[j];
+            ry[j] = fy * run;
+        }
+    }
+    R rzk;
+    {
+        R run = R(0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) run += DSz[k];
+        rzk = fz * run;
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const R Y = S0y[j] * Azk + DSy[j] * Czk;
+        const int row = base + jd0 * j + jd01 * K;
+#pragma unroll
+        for (int i = 0; i < N - 1; ++i) acc_put<R>(acc, row + i, Y, rx[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const R X = S0x[i] * Azk + DSx[i] * Czk;
+        const int col = jvol + base + i + jd01 * K;
+#pragma unroll
+        for (int j = 0; j < N - 1; ++j) acc_put<R>(acc, col + jd0 * j, X, ry[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const R Ay = S0y[j] + half * DSy[j], Cy = half * S0y[j] + third * DSy[j];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const R X = S0x[i] * Ay + DSx[i] * Cy;
+            acc_put<R>(acc, 2 * jvol + base + i + jd0 * j + jd01 * (K - 1), X, rzk);
+        }
+    }
+}
+
 // The entries of the W x W x W window outside the N x N x W one (N = ORD + 1 along x and
 // y): what a particle that changes its x or y nodes adds beyond the narrow window that
 // esirkepov3d<N, N, W> covers.  The values are those esirkepov3d<W, W, W> forms at the
@@ -377,9 +439,10 @@ __device__ __forceinline__ void esirkepov3d_extra(const R *S0x, const R *DSx, co
 // DSz/2), Wz = DSz (S0x + DSx/2) and the out-of-plane Jy = f_y' (S0x S0z + DSx S0z / 2 +
 // S0x DSz / 2 + DSx DSz / 3) with f_y' = (q w / dV) v_y; the 2D3V loops skip zero
 // contributions (up to 16 particles per cell contend there).  kNarrow (3D): every lane
-// covers ORD + 1 entries along x and y, and a lane whose particle changes its x or y nodes
-// adds the entries of the ORD + 2 window beyond them (esirkepov3d_extra), so the other
-// lanes of its warp add none of that window's zeros.
+// covers ORD + 1 entries along each axis; a lane whose particle changes its z nodes adds
+// the entries beyond them along z (esirkepov3d_zextra) and one that changes its x or y
+// nodes those of the ORD + 2 window beyond them along x and y (esirkepov3d_extra), so the
+// other lanes of its warp add none of those zeros.
 template <int ND, int ORD, bool kDisp, bool kNarrow, typename R, typename Acc>
 __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3], const int l1[3], const R o1[3],
                                                   const R disp[3], R fx, R fy, R fz, int jlo, int jlo_y, int jd0,
@@ -395,7 +458,9 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
         const int wsy = shape_window<ORD, kDisp>(l0[1], o0[1], l1[1], o1[1], disp[1], S0y, DSy, nwy) - jlo_y;
         const int base = wsx + jd0 * wsy + jd01 * wsz;
         if (kNarrow) {
-            esirkepov3d<ORD + 1, ORD + 1, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
+            esirkepov3d<ORD + 1, ORD + 1, ORD + 1, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
+            if (nwz > ORD + 1)
+                esirkepov3d_zextra<ORD + 1, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
             if (nwx > ORD + 1 || nwy > ORD + 1)
                 esirkepov3d_extra<ORD + 1, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
         } else {
