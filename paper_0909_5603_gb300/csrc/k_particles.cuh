@@ -580,8 +580,10 @@ __device__ __forceinline__ void scan_instance(const Launch &L, int ii, int mode,
 // plane carries none of its code).  I is the instance's entry of the launch's device
 // array, or, for a launch of one instance, a kernel parameter: its fields are then
 // operands from the constant bank, which no store of the kernel can alias, so they are
-// never reloaded after the particle write-out.
-template <int ND, int ORD, typename R, int PUSHER, bool INJ>
+// never reloaded after the particle write-out.  LANEWIN: the deposit window per lane
+// (deposit_esirkepov's kLane), taken where the registers allow it (the one-instance
+// kernel).
+template <int ND, int ORD, typename R, int PUSHER, bool INJ, bool LANEWIN>
 __device__ __forceinline__ void particle_tile(const InstDev &I, const int t)
 {
     constexpr bool kFixed = sizeof(R) == 4;  // FP32: fixed-point chunk accumulator + FP32 tile
@@ -918,10 +920,10 @@ __device__ __forceinline__ void particle_tile(const InstDev &I, const int t)
                 sc[a] = __frcp_rn(inv[a]);
             }
             // the current follows the computed displacement (see shape_window)
-            deposit_esirkepov<ND, ORD, true, true, R>(l, o, l1, o1, disp, fx * sc[0], fy * sc[1], fz * sc[2], I.jlo,
+            deposit_esirkepov<ND, ORD, true, true, LANEWIN, R>(l, o, l1, o1, disp, fx * sc[0], fy * sc[1], fz * sc[2], I.jlo,
                                                       jlo_y, jd0, jd01, jst, ChunkAcc{sJA});
         } else {
-            deposit_esirkepov<ND, ORD, false, false, R>(l, o, l1, o1, disp, fx, fy, fz, I.jlo, jlo_y, jd0, jd01,
+            deposit_esirkepov<ND, ORD, false, false, false, R>(l, o, l1, o1, disp, fx, fy, fz, I.jlo, jlo_y, jd0, jd01,
                                                         jst, DoubleAcc{sJD});
         }
 
@@ -1012,7 +1014,7 @@ template <int ND, int ORD, typename R, int PUSHER, bool INJ>
 __device__ __forceinline__ void particle_tile_of_launch(const Launch &L, const int g)
 {
     const int ii = find_instance(L.tile_start, L.ninst, g);
-    particle_tile<ND, ORD, R, PUSHER, INJ>(L.inst[ii], g - L.tile_start[ii]);
+    particle_tile<ND, ORD, R, PUSHER, INJ, false>(L.inst[ii], g - L.tile_start[ii]);
 }
 
 template <int ND, int ORD, typename R, int PUSHER, bool INJ>
@@ -1025,7 +1027,7 @@ __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles(Launc
 template <int ND, int ORD, typename R, int PUSHER, bool INJ>
 __global__ void __launch_bounds__(kNT, sizeof(R) == 4 ? 2 : 1) k_particles_one(const __grid_constant__ InstDev I)
 {
-    particle_tile<ND, ORD, R, PUSHER, INJ>(I, blockIdx.x);
+    particle_tile<ND, ORD, R, PUSHER, INJ, true>(I, blockIdx.x);
 }
 
 }  // namespace pic

@@ -438,12 +438,15 @@ __device__ __forceinline__ void esirkepov3d_extra(const R *S0x, const R *DSx, co
 // passes f = 0 and a position inside the tile).  In 2D3V (x-z plane) Wx = DSx (S0z +
 // DSz/2), Wz = DSz (S0x + DSx/2) and the out-of-plane Jy = f_y' (S0x S0z + DSx S0z / 2 +
 // S0x DSz / 2 + DSx DSz / 3) with f_y' = (q w / dV) v_y; the 2D3V loops skip zero
-// contributions (up to 16 particles per cell contend there).  kNarrow (3D): every lane
-// covers ORD + 1 entries along each axis; a lane whose particle changes its z nodes adds
-// the entries beyond them along z (esirkepov3d_zextra) and one that changes its x or y
-// nodes those of the ORD + 2 window beyond them along x and y (esirkepov3d_extra), so the
-// other lanes of its warp add none of those zeros.
-template <int ND, int ORD, bool kDisp, bool kNarrow, typename R, typename Acc>
+// contributions (up to 16 particles per cell contend there).  kNarrow (3D): the window
+// adapts to the particles.  With kLane every lane covers ORD + 1 entries along each axis;
+// a lane whose particle changes its z nodes adds the entries beyond them along z
+// (esirkepov3d_zextra) and one that changes its x or y nodes those of the ORD + 2 window
+// beyond them along x and y (esirkepov3d_extra), so the other lanes of its warp add none
+// of those zeros.  Without kLane (fewer registers: the launches over many instances) the
+// warp covers ORD + 1 entries along x and y when none of its particles changes its x or y
+// nodes (one vote per warp), ORD + 2 otherwise, and ORD + 2 along z.
+template <int ND, int ORD, bool kDisp, bool kNarrow, bool kLane, typename R, typename Acc>
 __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3], const int l1[3], const R o1[3],
                                                   const R disp[3], R fx, R fy, R fz, int jlo, int jlo_y, int jd0,
                                                   int jd01, int jvol, const Acc &acc)
@@ -457,12 +460,14 @@ __device__ __forceinline__ void deposit_esirkepov(const int l0[3], const R o0[3]
     if (ND == 3) {
         const int wsy = shape_window<ORD, kDisp>(l0[1], o0[1], l1[1], o1[1], disp[1], S0y, DSy, nwy) - jlo_y;
         const int base = wsx + jd0 * wsy + jd01 * wsz;
-        if (kNarrow) {
+        if (kNarrow && kLane) {
             esirkepov3d<ORD + 1, ORD + 1, ORD + 1, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
             if (nwz > ORD + 1)
                 esirkepov3d_zextra<ORD + 1, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
             if (nwx > ORD + 1 || nwy > ORD + 1)
                 esirkepov3d_extra<ORD + 1, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
+        } else if (kNarrow && !__any_sync(0xffffffffu, nwx > ORD + 1 || nwy > ORD + 1)) {
+            esirkepov3d<ORD + 1, ORD + 1, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
         } else {
             esirkepov3d<W, W, W, R>(S0x, DSx, S0y, DSy, S0z, DSz, fx, fy, fz, base, jd0, jd01, jvol, acc);
         }
