@@ -111,7 +111,18 @@ def test_null_handles(L):
                  lambda: L.pic_set_stations(N, 0, N, 0),
                  lambda: L.pic_get_station(N, 0, N, N, 0, N, 0),
                  lambda: L.pic_get_rho_noalloc(N, N, 0),
-                 lambda: L.pic_autotune(N, N, ctypes.c_double(0.1), ctypes.c_double(1.0), 1, N, N, N, N, 1, N, N)):
+                 lambda: L.pic_autotune(N, N, ctypes.c_double(0.1), ctypes.c_double(1.0), 1, N, N, N, N, 1, N, N),
+                 lambda: L.pic_load_particles_stored(N, 0, N, N, N, N, N),
+                 lambda: L.pic_get_particles_stored(N, N, N, N, N, N, 0, N),
+                 lambda: L.pic_get_planes(N, 0, 0, 1, N, 0),
+                 lambda: L.pic_put_planes(N, 0, 0, 1, N, 0, 0),
+                 lambda: L.pic_get_planes_n(N, N, 1, 0, 1, N, 0),
+                 lambda: L.pic_put_planes_n(N, N, 1, 0, 1, N, 0, 0),
+                 lambda: L.pic_extract_particles(N, 0, 1, N, N, N, N, N, 0, N),
+                 lambda: L.pic_add_particles(N, 0, N, N, N, N, N),
+                 lambda: L.pic_adopt_slab(N, N, 0, 0, 1),
+                 lambda: L.pic_batch_set_persistent(N, 1, 0, -1),
+                 lambda: L.pic_batch_autotune(N, 1, N, N, N)):
         assert call() == pic.PIC_ERR_ARG
 
 
